@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the plotting path on GB300: one JSON line on stdout.
+
+Default workload: plain single plot K=31 (2^31 uint32 nonces, 32-byte key
+from seed 31): keyed-BLAKE3 Table 1, two-level bucketing scatter, partition
+sort, match and pair hashing into Table 2, both tables resident in HBM.  A
+step is one whole plot (vx_table1 + vx_match); `value` is nonces/s over the
+timed steps (max over ranks; weak scaling: every rank plots its own keys).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--K 31] [--impl ours|reference]
+
+`--impl reference` times the CPU oracle (the test oracle, as it stands) on
+the host cores on a bounded sample of the same workload (one K=22 plot per
+step) and reports the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Blake3 nonces/s and K=31 plot seconds on 1 GB300; % INT/HBM roofline; batched vs plain"
+UNIT = "nonces/s"
+SMS = 152
+SMSP_PER_SM = 4
+LANES = 32
+# Algorithmic 32-bit integer operations of one keyed BLAKE3 compression as
+# the plotter needs it: 53 message-dependent G functions x 12 ops (4 adds,
+# 4 xors, 4 rotates), minus 14 ops of the last round that do not reach
+# output words 0..1, plus the 2 output xors.
+INT_OPS_PER_COMPRESSION = 53 * 12 - 14 + 2
+KERNELS = ["key_setup", "hash_scatter", "scatter2", "scan_counts", "sort", "scan_pairs", "match"]
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            m = json.load(f)
+        return {"hbm_gbs": float(m["hbm_gbs"]), "sm_max_mhz": float(m.get("sm_max_mhz", 2070.0)),
+                "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def int_peak_ops(sm_mhz: float) -> float:
+    """Integer-issue peak: every SM sub-partition issues one 32-lane warp
+    instruction per clock (152 SMs x 4 x 32 lanes x clock)."""
+    return SMS * SMSP_PER_SM * LANES * sm_mhz * 1e6
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="vx_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def source_digest(files) -> str:
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {
+    "hash_scatter": ["paper_2606_14007_gb300/csrc/k_hash.cu", "paper_2606_14007_gb300/csrc/vx_internal.cuh"],
+    "scatter2": ["paper_2606_14007_gb300/csrc/k_sort.cu", "paper_2606_14007_gb300/csrc/vx_internal.cuh"],
+    "sort": ["paper_2606_14007_gb300/csrc/k_sort.cu", "paper_2606_14007_gb300/csrc/vx_internal.cuh"],
+    "match": ["paper_2606_14007_gb300/csrc/k_match.cu", "paper_2606_14007_gb300/csrc/vx_internal.cuh"],
+}
+
+
+def ncu_traffic(kernel: str, K: int):
+    """DRAM bytes per launch of `kernel` at this workload from the committed
+    ncu summary, or None if absent or taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        e = t[kernel]
+        if e.get("source_digest") != source_digest(KERNEL_SOURCES[kernel]) or int(e["K"]) != K:
+            return None
+        return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def cpu_baseline(K_sample: int = 24):
+    """The CPU oracle, as it stands, on one plot of 2^K_sample nonces: hash on
+    all host cores, sort and match on one core."""
+    from oracle import oracle as orc
+    from paper_2606_14007_gb300.inputs import plot_key
+    orc.build()
+    key = plot_key(1000 + K_sample)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    recs = orc.hash_range(key, 0, 1 << K_sample, threads=threads)
+    t1 = orc.sort_table1(recs)
+    n2 = orc.match_count(key, t1, orc.default_distance(K_sample))
+    t2 = orc.match(key, t1, orc.default_distance(K_sample))
+    dt = time.perf_counter() - t0
+    assert t2.shape[0] == n2
+    return {"value": (1 << K_sample) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "one K=%d plot (2^%d nonces): keyed BLAKE3 on %d threads, qsort and match "
+                      "(incl. pair hashing) on 1 thread; %.1f s" % (K_sample, K_sample, threads, dt)}
+
+
+def run_reference(args):
+    """CPU oracle as the reference arm: one K=22 plot per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as orc
+    from paper_2606_14007_gb300.inputs import plot_key
+    orc.build()
+    Ks = 22
+    threads = os.cpu_count() or 1
+
+    def step(i):
+        key = plot_key(2000 + i)
+        recs = orc.hash_range(key, 0, 1 << Ks, threads=threads)
+        t1 = orc.sort_table1(recs)
+        orc.match(key, t1, orc.default_distance(Ks))
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    dt = time.perf_counter() - t0
+    value = (1 << Ks) * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic",
+        "config": {"workload": "plain plot, bounded sample: one K=22 plot per step on the CPU oracle",
+                   "K": Ks, "key_seeds": "2000+i"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": "one K=22 plot per step: hash on %d threads, sort + match on 1" % threads},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--K", type=int, default=31)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    import __graft_entry__
+    if local == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2606_14007_gb300 import vaultx as vx
+    from paper_2606_14007_gb300.inputs import plot_key
+    vx.lib()
+
+    K = args.K
+    N = 1 << K
+    key = plot_key(K + 1000 * rank)
+    stream = torch.cuda.current_stream()
+    plot = vx.Plot(K, key)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        plot.run(stream)
+    n2 = plot.sync()
+
+    vx.vx_plot_profile(plot.handle, args.steps)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        vx.vx_table1(plot.handle, stream)
+        vx.vx_match(plot.handle, stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    n2 = plot.sync()          # raises on any device-side status error
+    per_kernel, runs = vx.vx_plot_profile_read(plot.handle)
+    vx.vx_plot_profile(plot.handle, 0)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = N * args.steps * world / (ms_total / 1000.0)
+
+    # Per-kernel figures (CUDA events on the launching stream, timed region).
+    pk = {}
+    pk_peak = peaks()
+    hbm_peak = pk_peak["hbm_gbs"]
+    int_peak = int_peak_ops(pk_peak["sm_max_mhz"])
+    algo_bytes = {"scatter2": 24 * N, "sort": 24 * N, "match": 12 * N + 16 * n2}
+    algo_ops = {"hash_scatter": INT_OPS_PER_COMPRESSION * N, "match": INT_OPS_PER_COMPRESSION * n2}
+    for k in KERNELS:
+        ms = per_kernel[k] / max(1, runs)
+        e = {"ms_per_launch": ms}
+        if k in algo_ops and ms > 0:
+            e["int_tops"] = algo_ops[k] / (ms / 1e3) / 1e12
+            e["int_frac"] = e["int_tops"] * 1e12 / int_peak
+        if k in algo_bytes and ms > 0:
+            e["gbs"] = algo_bytes[k] / (ms / 1e3) / 1e9
+            e["hbm_frac"] = e["gbs"] / hbm_peak
+        pk[k] = e
+    dom = max(KERNELS, key=lambda k: pk[k]["ms_per_launch"])
+    if dom in algo_ops:
+        ach = pk[dom]["int_tops"] * 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach / 1e12, "peak": int_peak / 1e12,
+                "unit": "Tops/s (32-bit integer)", "frac": ach / int_peak,
+                "peak_basis": "152 SMs x 4 sub-partitions x 32 lanes x %.0f MHz (max SM clock, %s)"
+                              % (pk_peak["sm_max_mhz"], pk_peak["source"]),
+                "work_per_launch": algo_ops[dom],
+                "traffic": ncu_traffic(dom, K)}
+    else:
+        ach = pk[dom]["gbs"]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "work_per_launch": algo_bytes[dom],
+                "traffic": ncu_traffic(dom, K)}
+
+    # End to end through the C ABI with host buffers: per step the key goes
+    # host -> device (plot descriptor upload from pinned memory) and Table 2
+    # comes back device -> host (pinned), all inside the timed region.
+    e2e = None
+    if args.e2e_steps > 0:
+        t2_bytes = 16 * n2
+        chunk = 1 << 30
+        ring = torch.empty(2 * chunk, dtype=torch.uint8).pin_memory()
+        handles = []
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.e2e_steps):
+            h = vx.vx_plot_create(K, plot_key(K + 1000 * rank + 1 + i))
+            vx.vx_plot_bind(h, plot._t1.data_ptr(), plot._t2.data_ptr(), plot._scratch.data_ptr(), 0)
+            vx.vx_table1(h, stream)
+            vx.vx_match(h, stream)
+            vx.vx_sync(h)
+            _, m, _, _ = vx.vx_table_info(h, vx.VX_TABLE2)
+            off, k = 0, 0
+            while off < 16 * m:
+                nb = min(chunk, 16 * m - off)
+                vx.vx_table_copy(h, vx.VX_TABLE2, ring.data_ptr() + (k % 2) * chunk, nb, stream, offset=off)
+                off += nb
+                k += 1
+            stream.synchronize()
+            handles.append(h)
+        dt = time.perf_counter() - t0
+        barrier()
+        for h in handles:
+            vx.vx_plot_destroy(h)
+        desc_bytes = 512
+        e2e = {"value": N * args.e2e_steps * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": desc_bytes, "d2h_bytes_per_step": t2_bytes + 12,
+               "steps": args.e2e_steps,
+               "note": "vx_plot_create from a host key, vx_table1, vx_match, vx_sync, then Table 2 "
+                       "copied to pinned host memory through a 2 x 1 GiB ring"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    launches_per_step = 7 if plot_two_level(vx, K) else 6
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "plain single plot K=%d (2^%d uint32 nonces, key from seed %d), "
+                               "Table 1 + Table 2 resident in HBM" % (K, K, K),
+                   "K": K, "table2_records": n2,
+                   "l2": "inputs larger than L2: Table 1 %.1f GB, Table 2 %.1f GB per plot"
+                         % (12 * N / 1e9, 16 * n2 / 1e9)},
+        "plot_seconds": ms_step / 1000.0,
+        "roofline": roof,
+        "kernels": pk,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+    }
+    plot.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def plot_two_level(vx, K):
+    """True when the plan of K uses the second scatter level (7 kernels)."""
+    # The planner keeps one level up to 10 partition bits (K <= 22 at the
+    # default 4096-record partitions).
+    return K - 12 > 10
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,251 @@
+/*
+ * vaultx.h -- C ABI of the GB300 (sm_103a) VaultxGPU plotting path.
+ *
+ * A plot is the paper's unit of work (Sec. III-A): for a K and a 256-bit
+ * plot key, hash every nonce 0 .. 2^K-1 with keyed BLAKE3 into Table 1,
+ * bucket and sort Table 1 by hash prefix, pair its entries under the match
+ * threshold and hash every pair into Table 2.  All compute runs in this
+ * library's CUDA kernels; the Python binding only marshals arguments.
+ *
+ * Layouts (readings of the paper, which leaves them unstated):
+ *   Table 1 record, 12 bytes: LE u32 nonce, then hash bytes 0..7 of
+ *     BLAKE3-keyed(key, LE32(nonce)).  Sorted by key64 = big-endian u64 of
+ *     the 8 hash bytes, ties by nonce; logical bucket = key64 >> 40, so the
+ *     2^24 buckets of Sec. I-A / III-B come out concatenated in order.
+ *   Table 2 record, 16 bytes: LE u32 a, LE u32 b, then hash bytes 0..7 of
+ *     BLAKE3-keyed(key, LE32(a) || LE32(b)); (a, b) ranges over pairs of
+ *     Table-1 records i < j in the same logical bucket with
+ *     key64_j - key64_i < D (Sec. II-B "matching factor threshold",
+ *     Sec. III-A "expected distance threshold"); D = 2^(64-K) by default.
+ *     Order: bucket, then i, then j.
+ *
+ * Conventions.
+ *   - Every call returns an int status: VX_OK (0) or a negative VX_E* code.
+ *     No call aborts the process, and no kernel traps: device-side failures
+ *     set bits in a per-plot status word that vx_sync() reads and maps.
+ *   - Streams are cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Compute calls are asynchronous on that stream.
+ *   - Device pointers are plain CUDA device addresses (e.g. a torch
+ *     tensor's data_ptr()).  Buffers given to vx_plot_bind stay owned by
+ *     the caller; the library never frees them.
+ *   - A vx_plot is owned by the caller from vx_plot_create until
+ *     vx_plot_destroy; it may be used from one host thread at a time.
+ */
+#ifndef VAULTX_H
+#define VAULTX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status */
+enum {
+    VX_OK = 0,
+    VX_EINVAL = -1,     /* bad argument (K, key, opts, pointer, alignment, size)   */
+    VX_ENOMEM = -2,     /* allocation failed, or Table 2 exceeds its capacity      */
+    VX_ECUDA = -3,      /* a CUDA runtime call failed (detail in vx_last_error)    */
+    VX_ETIMEDOUT = -4,  /* a bounded device-side wait gave up                      */
+    VX_EBUSY = -5,      /* server full / resource in use                           */
+    VX_ENOTREADY = -6,  /* result not produced yet (call order, or still running)  */
+    VX_EOVERFLOW = -7   /* a partition slot overflowed its capacity: the tables are
+                           incomplete; re-run with a larger opts.slack_sigma       */
+};
+
+/* Table selectors. */
+enum { VX_TABLE1 = 1, VX_TABLE2 = 2 };
+
+/* Plot states reported by the server. */
+enum { VX_QUEUED = 0, VX_RUNNING = 1, VX_DONE = 2, VX_FAILED = 3 };
+
+/* Tuning and semantics options.  Zero-initialised fields take defaults;
+ * always set .size = sizeof(vx_opts) (vx_opts_default does). */
+typedef struct vx_opts {
+    uint32_t size;              /* sizeof(vx_opts)                                   */
+    uint32_t reserved0;
+    uint64_t match_distance;    /* D of the match predicate; 0 = 2^(64-K)            */
+    int32_t partition_log2;     /* log2 of the mean records per physical partition
+                                   (6..13); 0 = default (12).  Partitions are runs
+                                   of whole logical buckets; at most 2^24 of them.  */
+    int32_t coarse_bits;        /* bits of the first scatter level (0..10);
+                                   -1 = automatic                                     */
+    uint32_t slack_sigma;       /* partition-slot slack in standard deviations of a
+                                   Poisson count; 0 = default (12)                   */
+    uint32_t hash_block;        /* threads per block of the hash kernel (64..1024,
+                                   multiple of 32); 0 = default                      */
+    uint32_t nonces_per_thread; /* nonces each hash thread handles (2..64, even);
+                                   0 = default                                        */
+    uint32_t reserved1;
+    uint64_t t2_capacity;       /* Table-2 capacity in records; 0 = default bound    */
+} vx_opts;
+
+typedef struct vx_plot vx_plot;
+
+/* Fills *opts with the defaults.  Returns VX_EINVAL on NULL. */
+int vx_opts_default(vx_opts *opts);
+
+/* Short static description of a status code. */
+const char *vx_strerror(int status);
+
+/* Detail of the last failure on this plot (static empty string if none or
+ * plot is NULL).  Valid until the next call on the plot. */
+const char *vx_last_error(const vx_plot *plot);
+
+/* Library version, (major << 16) | minor. */
+int vx_version(void);
+
+/* Device memory one plot needs (Sec. I-A: Table 1 stays resident in VRAM).
+ *   t1_bytes:      Table-1 buffer (>= 12 * 2^K; the first scatter level also
+ *                  uses it as its staging area, so it may be a little larger)
+ *   t2_bytes:      Table-2 buffer (>= 16 * Table-2 capacity; the second
+ *                  scatter level stages in it before vx_match runs)
+ *   scratch_bytes: counters, offsets and the plot descriptor
+ * Any output pointer may be NULL.  1 <= K <= 32.  No allocation. */
+int vx_plot_required_bytes(int K, const vx_opts *opts, uint64_t *t1_bytes,
+                           uint64_t *t2_bytes, uint64_t *scratch_bytes);
+
+/* Creates a plot for (K, key) (Sec. III-B: the 256-bit plot key).  key is 32
+ * host bytes, copied.  opts may be NULL.  Allocates host state only. */
+int vx_plot_create(int K, const uint8_t key[32], const vx_opts *opts, vx_plot **out);
+
+/* Gives the plot caller-owned device buffers of at least the sizes
+ * vx_plot_required_bytes reports, each 256-byte aligned.  t2_capacity is the
+ * number of 16-byte Table-2 records d_t2 can hold (0 = t2_bytes / 16 of the
+ * default plan).  Replaces any earlier binding; frees library-owned memory. */
+int vx_plot_bind(vx_plot *plot, void *d_t1, void *d_t2, void *d_scratch, uint64_t t2_capacity);
+
+/* Allocates library-owned device buffers (cudaMalloc) if none are bound. */
+int vx_plot_alloc(vx_plot *plot);
+
+/* Table 1 (Sec. III-A hash stage; sort half of the fused Sort+Match kernel):
+ * key setup, keyed BLAKE3 of every nonce, two-level bucketing scatter by
+ * hash prefix, in-partition shared-memory sort.  Allocates (vx_plot_alloc)
+ * if nothing is bound.  Asynchronous on stream. */
+int vx_table1(vx_plot *plot, void *stream);
+
+/* Table 2 (Sec. III-A match half of the fused Sort+Match kernel): pair
+ * counting, deterministic placement by prefix sums, pair hashing.  Requires
+ * vx_table1 earlier on the same stream.  If the pairs exceed the Table-2
+ * capacity nothing is written and vx_sync returns VX_ENOMEM; the needed
+ * count is then in vx_table_info(VX_TABLE2).nrec.  Asynchronous. */
+int vx_match(vx_plot *plot, void *stream);
+
+/* Waits for the plot's last stream, reads its device status word and the
+ * Table-2 count, and maps the status to VX_OK / VX_EOVERFLOW / VX_ENOMEM /
+ * VX_ETIMEDOUT.  Synchronous. */
+int vx_sync(vx_plot *plot);
+
+/* Zero-copy view of a table: device pointer, record count, record size.
+ * Table-2 counts are known after vx_sync following vx_match (VX_ENOTREADY
+ * before). */
+int vx_table_info(const vx_plot *plot, int which, const void **dptr, uint64_t *nrec,
+                  uint32_t *rec_bytes);
+
+/* Writes the 2^24 + 1 logical-bucket offsets of Table 1 (u64, offsets[b] =
+ * records in buckets < b) to d_out (device, 8-byte aligned).  Asynchronous. */
+int vx_table1_offsets(vx_plot *plot, void *d_out, void *stream);
+
+/* Copies bytes [offset, offset + bytes) of a table to host memory (pinned
+ * memory makes it asynchronous on stream).  The range must lie within
+ * nrec * rec_bytes. */
+int vx_table_copy(vx_plot *plot, int which, uint64_t offset, void *host_dst, uint64_t bytes,
+                  void *stream);
+
+/* Writes Table 2 as a flat binary file (Sec. III-A / III-B: D2H through a
+ * pinned staging buffer, sequential 4 MB chunks; no header).  Returns after
+ * the file is written.  Synchronous. */
+int vx_plot_write(vx_plot *plot, const char *path, double *seconds_d2h, double *seconds_total);
+
+/* Runs vx_table1 + vx_match for n plots as one batch: every stage is one
+ * grouped launch over all plots' work (mixed K and keys), recorded once into
+ * a CUDA graph per batch shape and replayed.  Each plot must be bound or
+ * allocatable.  Per-plot status via vx_sync on each plot (the batch records
+ * the stream on every plot).  Asynchronous. */
+int vx_plot_batch(vx_plot *const *plots, int n, void *stream);
+
+/* Frees library-owned memory and the handle.  NULL is a no-op. */
+void vx_plot_destroy(vx_plot *plot);
+
+/* ------------------------------------------------------------ tracing */
+
+/* Records CUDA events around every kernel of this plot's next `runs`
+ * vx_table1 + vx_match pairs (single-plot path; the paper's per-stage
+ * timing of Sec. IV-C at kernel granularity).  runs = 0 turns tracing off
+ * and frees the events.  Adds one event record per kernel, no sync. */
+int vx_plot_profile(vx_plot *plot, int runs);
+
+/* Sums the traced runs: ms[k] = total milliseconds of kernel k, k <
+ * *nkernels (cap must be >= 7); *nruns = runs recorded.  Waits for them. */
+int vx_plot_profile_read(vx_plot *plot, double *ms, int cap, int *nkernels, int *nruns);
+
+/* Name of traced kernel k ("key_setup", "hash_scatter", "scatter2",
+ * "scan_counts", "sort", "scan_pairs", "match"), or "" if out of range. */
+const char *vx_kernel_name(int k);
+
+/* ------------------------------------------------ stand-alone stages */
+
+/* Keyed BLAKE3 of nonces nonce0 .. nonce0+count-1 into 12-byte Table-1
+ * records in nonce order (no bucketing), at d_out (device, 4-byte aligned,
+ * 12*count bytes).  The hash row of the path on its own.  Asynchronous. */
+int vx_hash_nonces(const uint8_t key[32], uint64_t nonce0, uint64_t count, void *d_out,
+                   void *stream);
+
+/* Pair hash of Table 2 on its own: for each of `count` pairs (a, b) at
+ * d_pairs (device, 2 LE u32 each, 8-byte aligned) writes the 16-byte
+ * Table-2 record {a, b, hash2[0..7]} to d_out (16-byte aligned).
+ * Asynchronous. */
+int vx_pair_hash(const uint8_t key[32], const void *d_pairs, uint64_t count, void *d_out,
+                 void *stream);
+
+/* Test hook (host-side fault injection, no GPU fault): the next `count`
+ * device allocations the library makes fail as if cudaMalloc had returned
+ * cudaErrorMemoryAllocation, so callers' VX_ENOMEM paths can be exercised.
+ * The paper has no counterpart.  count <= 0 clears it. */
+int vx_test_fail_next_allocs(int count);
+
+/* ------------------------------------------------------------ server */
+
+typedef struct vx_server vx_server;
+
+typedef struct vx_serve_opts {
+    uint32_t size;           /* sizeof(vx_serve_opts)                                  */
+    uint32_t max_inflight;   /* plots on the device at once (running or waiting to be
+                                fetched); 0 = 64                                        */
+    uint64_t memory_budget;  /* bytes of device memory the server may hold; 0 = 80% of
+                                free memory at creation                                 */
+    uint32_t streams;        /* concurrent waves in flight; 0 = 2                      */
+    uint32_t max_wave;       /* plots per wave (one batch launch); 0 = 32              */
+    vx_opts plot_opts;       /* options for every plot (size 0 = defaults)            */
+} vx_serve_opts;
+
+/* Creates a continuous-batching plot server on the current device. */
+int vx_serve_create(const vx_serve_opts *opts, vx_server **out);
+
+/* Queues a plot request; *ticket identifies it.  VX_EINVAL for a bad K or a
+ * plot larger than the memory budget.  Never blocks. */
+int vx_serve_submit(vx_server *srv, int K, const uint8_t key[32], uint64_t *ticket);
+
+/* Advances the server (admits queued requests whose footprint fits the free
+ * budget, launches waves, retires finished ones) and reports the ticket's
+ * state.  When *state == VX_DONE and out != NULL, the plot handle is handed
+ * to the caller (tables on the device, count synced), who must
+ * vx_plot_destroy it; that frees its share of the budget.  VX_EINVAL for an
+ * unknown ticket. */
+int vx_serve_poll(vx_server *srv, uint64_t ticket, int *state, vx_plot **out);
+
+/* Advances the server without asking about a ticket; returns the number of
+ * requests not yet handed out. */
+int vx_serve_step(vx_server *srv);
+
+/* Submit-to-done latency of a finished ticket in seconds. */
+int vx_serve_latency(vx_server *srv, uint64_t ticket, double *seconds);
+
+/* Waits for all waves, frees every plot not handed out, frees the server. */
+void vx_serve_destroy(vx_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VAULTX_H */

@@ -1,0 +1,263 @@
+// k_hash.cu -- key setup, Table-1 hashing fused with the first bucketing
+// scatter, and the stand-alone hash / pair-hash kernels.
+//
+// Paper: Sec. III-A/III-B (one keyed BLAKE3 per nonce, little-endian nonce,
+// bucket index from the hash prefix).  The paper's kernel claims one bucket
+// slot per nonce with a global atomicAdd; here a CTA hashes a tile of
+// nonces, histograms them by the leading hash bits in shared memory
+// (warp-aggregated with __match_any_sync where bins are few), claims one
+// contiguous run per (CTA, bin) with a single global atomic, and writes the
+// records partition-ordered so that consecutive threads store consecutive
+// addresses.  Order inside a partition is irrelevant: the partition sort
+// orders records by (key64, nonce), a total order.
+#include "vx_internal.cuh"
+
+namespace vx {
+
+// ------------------------------------------------------------ key setup
+// One CTA row per plot: thread 0 of block x == 0 derives the per-key hash
+// states; every CTA zeroes a share of the plot's fill counters and the
+// status word.
+__global__ void k_key_setup(Desc *descs)
+{
+    Desc &d = descs[blockIdx.y];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        uint32_t pre[16];
+        b3_key_setup(d.key, 4u, pre);
+        for (int i = 0; i < 16; ++i) d.pre1[i] = pre[i];
+        b3_key_setup(d.key, 8u, pre);
+        for (int i = 0; i < 16; ++i) d.pre2[i] = pre[i];
+        *d.status = 0u;
+    }
+    const uint64_t n1 = d.p2 > 0 ? (1ull << d.p1) : 0ull;
+    const uint64_t n2 = 1ull << d.p;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+        d.cnt2[i] = 0u;
+        if (i < n1) d.cnt1[i] = 0u;
+    }
+}
+
+cudaError_t launch_key_setup(Desc *descs, int nplots, cudaStream_t s)
+{
+    dim3 grid(64, nplots);
+    k_key_setup<<<grid, 256, 0, s>>>(descs);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------- hash + first-level scatter
+// Shared layout of one tile: staged key64[T], nonce[T], then per-bin
+// histogram, local offset and claimed global base (kMaxCoarseBits bins).
+template <int NT, int NPT>
+struct HashSmem {
+    static constexpr int T = NT * NPT;
+    uint64_t keys[T];
+    uint32_t nonces[T];
+    uint32_t hist[1 << kMaxCoarseBits];
+    uint32_t loff[1 << kMaxCoarseBits];
+    uint32_t gbase[1 << kMaxCoarseBits];
+    uint32_t ws[NT / 32 + 1];
+};
+
+// Rank of this lane's record within its bin's run of the tile.
+template <bool AGG>
+__device__ __forceinline__ uint32_t bin_rank(uint32_t *hist, uint32_t bin, bool valid)
+{
+    if (AGG) {
+        const uint32_t peers = __match_any_sync(0xffffffffu, valid ? bin : 0xffffffffu);
+        const int leader = __ffs(peers) - 1;
+        const int lane = threadIdx.x & 31;
+        uint32_t base = 0;
+        if (lane == leader && valid) base = atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        return base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    } else {
+        return valid ? atomicAdd(&hist[bin], 1u) : 0u;
+    }
+}
+
+// Exclusive scan of hist[0..nbins) into loff, and one global claim per
+// non-empty bin: gbase[b] = atomicAdd(&cnt[bin_base + b], hist[b]).
+template <int NT>
+__device__ __forceinline__ void scan_and_claim(uint32_t *hist, uint32_t *loff, uint32_t *gbase,
+                                               uint32_t *ws, int nbins, uint32_t *cnt,
+                                               uint32_t bin_base)
+{
+    const int per = (nbins + NT - 1) / NT;  // <= 4 for 1024 bins and 256 threads
+    const int b0 = threadIdx.x * per;
+    uint32_t local = 0;
+    for (int k = 0; k < per; ++k)
+        if (b0 + k < nbins) local += hist[b0 + k];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan_u32<NT>(local, ws, &total);
+    for (int k = 0; k < per; ++k) {
+        const int b = b0 + k;
+        if (b < nbins) {
+            const uint32_t h = hist[b];
+            loff[b] = run;
+            run += h;
+            gbase[b] = h ? atomicAdd(&cnt[bin_base + b], h) : 0u;
+        }
+    }
+}
+
+template <int NT, int NPT, bool AGG>
+__global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ descs, int nplots,
+                                                     const uint32_t *__restrict__ tile_start)
+{
+    using S = HashSmem<NT, NPT>;
+    constexpr int T = S::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S &sm = *reinterpret_cast<S *>(smem_raw);
+
+    const int plot = find_plot(tile_start, nplots, blockIdx.x);
+    const Desc &d = descs[plot];
+    const uint64_t N = d.N;
+    const uint64_t base = (uint64_t)(blockIdx.x - tile_start[plot]) * T;
+    const bool two_level = d.p2 > 0;
+    const int bits = two_level ? d.p1 : d.p;
+    const int nbins = 1 << bits;
+    const uint32_t cap = two_level ? d.cap1 : d.cap2;
+    uint64_t *__restrict__ okeys = two_level ? d.a_keys : d.b_keys;
+    uint32_t *__restrict__ ononces = two_level ? d.a_nonces : d.b_nonces;
+    uint32_t *cnt = two_level ? d.cnt1 : d.cnt2;
+
+    uint32_t pre[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) pre[i] = d.pre1[i];
+
+    for (int b = threadIdx.x; b < nbins; b += NT) sm.hist[b] = 0u;
+    __syncthreads();
+
+    uint64_t key[NPT];
+    uint32_t rank[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
+        const bool valid = nonce < N;
+        uint32_t h0, h1;
+        b3_finish<false>(pre, (uint32_t)nonce, 0u, h0, h1);
+        key[j] = key64_of(h0, h1);
+        const uint32_t bin = bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u;
+        rank[j] = bin_rank<AGG>(sm.hist, bin, valid);
+    }
+    __syncthreads();
+    scan_and_claim<NT>(sm.hist, sm.loff, sm.gbase, sm.ws, nbins, cnt, 0u);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
+        if (nonce < N) {
+            const uint32_t bin = bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u;
+            const uint32_t pos = sm.loff[bin] + rank[j];
+            sm.keys[pos] = key[j];
+            sm.nonces[pos] = (uint32_t)nonce;
+        }
+    }
+    __syncthreads();
+    const uint32_t count = (uint32_t)((N - base) < (uint64_t)T ? (N - base) : (uint64_t)T);
+    bool overflow = false;
+    for (uint32_t i = threadIdx.x; i < count; i += NT) {
+        const uint64_t k = sm.keys[i];
+        const uint32_t bin = bits ? (uint32_t)(k >> (64 - bits)) : 0u;
+        const uint32_t g = sm.gbase[bin] + (i - sm.loff[bin]);
+        if (g < cap) {
+            const uint64_t at = (uint64_t)bin * cap + g;
+            okeys[at] = k;
+            ononces[at] = sm.nonces[i];
+        } else {
+            overflow = true;
+        }
+    }
+    if (overflow) atomicOr(d.status, two_level ? kStSlot1Overflow : kStSlot2Overflow);
+}
+
+template <int NT, int NPT, bool AGG>
+static cudaError_t launch_hs(const Desc *descs, int nplots, const uint32_t *tile_start,
+                             uint32_t total_tiles, cudaStream_t s)
+{
+    const size_t smem = sizeof(HashSmem<NT, NPT>);
+    auto fn = k_hash_scatter<NT, NPT, AGG>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<total_tiles, NT, smem, s>>>(descs, nplots, tile_start);
+    return cudaGetLastError();
+}
+
+// AGG (warp-aggregated ranks) pays off when a warp's 32 records fall into
+// few bins; the host picks it from the smallest bin count in the launch.
+cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *tile_start,
+                                uint32_t total_tiles, HashCfg cfg, cudaStream_t s)
+{
+    if (cfg.agg)
+        return launch_hs<kHashThreads, kHashNoncesPerThread, true>(descs, nplots, tile_start,
+                                                                   total_tiles, s);
+    return launch_hs<kHashThreads, kHashNoncesPerThread, false>(descs, nplots, tile_start,
+                                                                total_tiles, s);
+}
+
+// --------------------------------------------------- stand-alone hashing
+// Records {nonce, h0, h1} of nonces nonce0 .. nonce0+count-1, nonce order.
+__global__ void __launch_bounds__(256) k_hash_records(uint32_t k0, uint32_t k1, uint32_t k2,
+                                                      uint32_t k3, uint32_t k4, uint32_t k5,
+                                                      uint32_t k6, uint32_t k7, uint64_t nonce0,
+                                                      uint64_t count, uint32_t *__restrict__ out)
+{
+    const uint32_t key[8] = {k0, k1, k2, k3, k4, k5, k6, k7};
+    uint32_t pre[16];
+    b3_key_setup(key, 4u, pre);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const uint32_t nonce = (uint32_t)(nonce0 + i);
+        uint32_t h0, h1;
+        b3_finish<false>(pre, nonce, 0u, h0, h1);
+        out[3 * i] = nonce;
+        out[3 * i + 1] = h0;
+        out[3 * i + 2] = h1;
+    }
+}
+
+cudaError_t launch_hash_records(const uint32_t key[8], uint64_t nonce0, uint64_t count,
+                                uint32_t *out, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    uint64_t blocks = (count + 255) / 256;
+    if (blocks > 152ull * 64) blocks = 152ull * 64;
+    k_hash_records<<<(unsigned)blocks, 256, 0, s>>>(key[0], key[1], key[2], key[3], key[4],
+                                                      key[5], key[6], key[7], nonce0, count, out);
+    return cudaGetLastError();
+}
+
+// Table-2 records {a, b, g0, g1} of the pairs (a, b).
+__global__ void __launch_bounds__(256) k_pair_hash(uint32_t k0, uint32_t k1, uint32_t k2,
+                                                   uint32_t k3, uint32_t k4, uint32_t k5,
+                                                   uint32_t k6, uint32_t k7,
+                                                   const uint2 *__restrict__ pairs, uint64_t count,
+                                                   uint4 *__restrict__ out)
+{
+    const uint32_t key[8] = {k0, k1, k2, k3, k4, k5, k6, k7};
+    uint32_t pre[16];
+    b3_key_setup(key, 8u, pre);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+        const uint2 ab = pairs[i];
+        uint32_t g0, g1;
+        b3_finish<true>(pre, ab.x, ab.y, g0, g1);
+        out[i] = make_uint4(ab.x, ab.y, g0, g1);
+    }
+}
+
+cudaError_t launch_pair_hash(const uint32_t key[8], const uint32_t *pairs, uint64_t count,
+                             uint4 *out, cudaStream_t s)
+{
+    if (count == 0) return cudaSuccess;
+    uint64_t blocks = (count + 255) / 256;
+    if (blocks > 152ull * 64) blocks = 152ull * 64;
+    k_pair_hash<<<(unsigned)blocks, 256, 0, s>>>(key[0], key[1], key[2], key[3], key[4], key[5],
+                                                   key[6], key[7],
+                                                   reinterpret_cast<const uint2 *>(pairs), count,
+                                                   out);
+    return cudaGetLastError();
+}
+
+}  // namespace vx

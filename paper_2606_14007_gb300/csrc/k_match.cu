@@ -1,0 +1,131 @@
+// k_match.cu -- the match stage and Table 2.
+//
+// Paper: Sec. II-B (pairwise match against a matching-factor threshold ->
+// Table 2) and Sec. III-A (match half of the fused Sort+Match kernel, one
+// bucket per block, data kept in shared memory).  Here one CTA takes one
+// physical partition (a run of whole logical buckets) of the sorted Table 1
+// into shared memory, counts for every record i the later records j of its
+// logical bucket with key64_j - key64_i < D, turns the counts into
+// positions with a block prefix sum, lists the pairs in shared memory in
+// (i, j) order, and then every lane hashes list entries back to back, so
+// the one-compression-per-pair work never idles lanes on records without a
+// partner.  Table-2 placement comes from the per-partition pair counts of
+// the sort kernel and an exclusive scan: deterministic, no atomics.
+#include "vx_internal.cuh"
+
+namespace vx {
+
+constexpr uint32_t kPairList = 4096;  // pair-list window (entries of 2 x u16)
+
+struct MatchLayout {
+    size_t nonces, start, list, ws, bytes;
+    __host__ __device__ MatchLayout(uint32_t cap)
+    {
+        nonces = (size_t)cap * 8;
+        start = nonces + (size_t)cap * 4;
+        list = start + (size_t)cap * 4;
+        ws = list + (size_t)kPairList * 4;
+        bytes = ws + (kMatchThreads / 32 + 1) * 4;
+    }
+};
+
+__global__ void __launch_bounds__(kMatchThreads) k_match(const Desc *__restrict__ descs, int nplots,
+                                                         const uint32_t *__restrict__ tile_start)
+{
+    constexpr int NT = kMatchThreads;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int plot = find_plot(tile_start, nplots, blockIdx.x);
+    const Desc &d = descs[plot];
+    const uint32_t f = blockIdx.x - tile_start[plot];
+    const uint64_t np = 1ull << d.p;
+    if (d.t2off[np] > d.t2cap) return;  // capacity exceeded: the scan flagged it
+    const uint64_t pbase = d.t2off[f];
+    const uint32_t P = (uint32_t)(d.t2off[f + 1] - pbase);
+    if (P == 0) return;
+    const uint64_t off = d.t1off[f];
+    const uint32_t n = (uint32_t)(d.t1off[f + 1] - off);
+    const MatchLayout L(d.cap2);
+    uint64_t *keys = reinterpret_cast<uint64_t *>(smem_raw);
+    uint32_t *nonces = reinterpret_cast<uint32_t *>(smem_raw + L.nonces);
+    uint32_t *start = reinterpret_cast<uint32_t *>(smem_raw + L.start);
+    uint32_t *list = reinterpret_cast<uint32_t *>(smem_raw + L.list);
+    uint32_t *ws = reinterpret_cast<uint32_t *>(smem_raw + L.ws);
+
+    // Table-1 words {nonce, h0, h1} -> nonce[], key64[] (key64 = BE of h).
+    const uint32_t *__restrict__ t1w = reinterpret_cast<const uint32_t *>(d.t1) + 3 * off;
+    uint32_t *khalf = reinterpret_cast<uint32_t *>(keys);
+    for (uint32_t w = threadIdx.x; w < 3 * n; w += NT) {
+        const uint32_t r = w / 3, q = w - 3 * r;
+        const uint32_t v = t1w[w];
+        if (q == 0) nonces[r] = v;
+        else khalf[2 * r + (q == 1 ? 1 : 0)] = bswap32(v);
+    }
+    __syncthreads();
+
+    // Per-record pair counts over a contiguous chunk of records per thread.
+    const uint64_t D = d.D;
+    const uint32_t per = (n + NT - 1) / NT;
+    const uint32_t r0 = min(n, threadIdx.x * per), r1 = min(n, r0 + per);
+    uint32_t mine = 0;
+    for (uint32_t r = r0; r < r1; ++r) {
+        const uint64_t k = keys[r];
+        const uint64_t bucket = k >> 40;
+        uint32_t c = 0;
+        for (uint32_t r2 = r + 1; r2 < n; ++r2) {
+            const uint64_t k2 = keys[r2];
+            if ((k2 >> 40) != bucket || k2 - k >= D) break;
+            ++c;
+        }
+        start[r] = c;
+        mine += c;
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive_scan_u32<NT>(mine, ws, &total);
+    for (uint32_t r = r0; r < r1; ++r) {
+        const uint32_t c = start[r];
+        start[r] = run;
+        run += c;
+    }
+    if (total != P && threadIdx.x == 0) atomicOr(d.status, kStCountMismatch);
+    __syncthreads();
+
+    uint32_t g[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) g[i] = d.pre2[i];
+    uint4 *__restrict__ out = reinterpret_cast<uint4 *>(d.t2) + pbase;
+    const uint32_t limit = min(total, P);
+    for (uint32_t w0 = 0; w0 < limit; w0 += kPairList) {
+        const uint32_t w1 = min(limit, w0 + kPairList);
+        // List the pairs whose Table-2 position falls in [w0, w1).
+        for (uint32_t r = r0; r < r1; ++r) {
+            const uint32_t s = start[r];
+            const uint32_t e = r + 1 < n ? start[r + 1] : total;
+            const uint32_t lo = max(s, w0), hi = min(e, w1);
+            for (uint32_t k = lo; k < hi; ++k) list[k - w0] = r | ((r + 1 + (k - s)) << 16);
+        }
+        __syncthreads();
+        for (uint32_t q = threadIdx.x; q < w1 - w0; q += NT) {
+            const uint32_t e = list[q];
+            const uint32_t a = nonces[e & 0xffffu], b = nonces[e >> 16];
+            uint32_t h0, h1;
+            b3_finish<true>(g, a, b, h0, h1);
+            out[w0 + q] = make_uint4(a, b, h0, h1);
+        }
+        __syncthreads();
+    }
+}
+
+size_t match_smem_bytes(uint32_t cap) { return MatchLayout(cap).bytes; }
+
+cudaError_t launch_match(const Desc *descs, int nplots, const uint32_t *tile_start,
+                         uint32_t total_tiles, cudaStream_t s, uint32_t max_cap)
+{
+    const size_t smem = match_smem_bytes(max_cap);
+    cudaError_t e = cudaFuncSetAttribute(k_match, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_match<<<total_tiles, kMatchThreads, smem, s>>>(descs, nplots, tile_start);
+    return cudaGetLastError();
+}
+
+}  // namespace vx

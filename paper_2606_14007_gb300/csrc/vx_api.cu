@@ -1,0 +1,842 @@
+// vx_api.cu -- host engine behind include/vaultx.h: the plot planner (how
+// many physical partitions, slot capacities, buffer sizes), device-memory
+// binding, the launch sequences of vx_table1 / vx_match, the batch path
+// (grouped launches recorded into a CUDA graph), status mapping and the
+// Table-2 file writer.
+//
+// Paper: Sec. III-A (pipeline: Table 1 in VRAM -> sort+match -> Table 2 ->
+// D2H -> flat binary file in 4 MB chunks), Sec. III-B (pinned 256 MB
+// staging buffer), Sec. III-C (allocation-size admission check).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstddef>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <fcntl.h>
+#include <unistd.h>
+
+#include "../../include/vaultx.h"
+#include "vx_internal.cuh"
+#include "vx_plan.h"
+#include "vx_engine.h"
+
+using vx::Desc;
+using vx::LaunchSet;
+
+namespace vx {
+static_assert(kPlanHashTile == (uint64_t)kHashTile, "planner and hash kernel tiles differ");
+static_assert(sizeof(Desc) + 64 <= kStageTilesOffset, "descriptor overlaps staged tiles");
+inline int make_plan(int K, const vx_opts *o, Plan *pl, std::string *why)
+{
+    int rc = make_plan_sized(K, o, pl, why, sizeof(Desc));
+    if (rc != VX_OK) return rc;
+    if (sort_smem_bytes(pl->cap2, pl->dbits) > kMaxSmemPerCta ||
+        match_smem_bytes(pl->cap2) > kMaxSmemPerCta) {
+        *why = "partition slot too large for shared memory";
+        return VX_EINVAL;
+    }
+    return VX_OK;
+}
+}  // namespace vx
+
+namespace {
+
+void forget_batches(vx_plot *p);  // drops cached batch graphs that use p
+std::mutex g_mu;
+int g_fail_allocs = 0;  // test hook: the next N device allocations fail
+
+void set_err(vx_plot *p, const std::string &s)
+{
+    if (p) p->err = s;
+}
+
+int cuda_fail(vx_plot *p, const char *what, cudaError_t e)
+{
+    set_err(p, std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return VX_ECUDA;
+}
+
+#define VX_TRY(p, call)                                \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(p, #call, e_); \
+    } while (0)
+
+bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+void key_words(const uint8_t key[32], uint32_t w[8])
+{
+    for (int i = 0; i < 8; ++i)
+        w[i] = (uint32_t)key[4 * i] | ((uint32_t)key[4 * i + 1] << 8) |
+               ((uint32_t)key[4 * i + 2] << 16) | ((uint32_t)key[4 * i + 3] << 24);
+}
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (g_fail_allocs > 0) {
+            --g_fail_allocs;
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
+void free_owned(vx_plot *p)
+{
+    if (p->owned) {
+        cudaFree(p->d_t1);
+        cudaFree(p->d_t2);
+        cudaFree(p->d_scratch);
+    }
+    p->d_t1 = p->d_t2 = p->d_scratch = nullptr;
+    p->owned = false;
+    p->desc_dirty = true;
+    p->stage = 0;
+    p->t2_known = false;
+}
+
+// Descriptor of a bound plot (host copy).
+void fill_desc(const vx_plot *p, Desc *d)
+{
+    const vx::Plan &pl = p->plan;
+    memset(d, 0, sizeof(*d));
+    d->N = pl.N;
+    d->D = pl.D;
+    d->t2cap = p->t2cap;
+    d->K = pl.K;
+    d->p = pl.p;
+    d->p1 = pl.p1;
+    d->p2 = pl.p2;
+    d->dbits = pl.dbits;
+    d->cap1 = pl.cap1;
+    d->cap2 = pl.cap2;
+    d->chunks1 = pl.chunks1;
+    if (pl.p2 > 0) {
+        d->a_keys = reinterpret_cast<uint64_t *>(p->d_t1);
+        d->a_nonces = reinterpret_cast<uint32_t *>(p->d_t1 + pl.regionA_keys);
+    }
+    d->b_keys = reinterpret_cast<uint64_t *>(p->d_t2);
+    d->b_nonces = reinterpret_cast<uint32_t *>(p->d_t2 + pl.regionB_keys);
+    uint8_t *s = p->d_scratch;
+    d->status = reinterpret_cast<uint32_t *>(s + pl.o_status);
+    d->cnt1 = reinterpret_cast<uint32_t *>(s + pl.o_cnt1);
+    d->cnt2 = reinterpret_cast<uint32_t *>(s + pl.o_cnt2);
+    d->t1off = reinterpret_cast<uint64_t *>(s + pl.o_t1off);
+    d->pairs = reinterpret_cast<uint64_t *>(s + pl.o_pairs);
+    d->t2off = reinterpret_cast<uint64_t *>(s + pl.o_t2off);
+    d->t1 = p->d_t1;
+    d->t2 = p->d_t2;
+    key_words(p->key, d->key);
+}
+
+Desc *dev_desc(vx_plot *p) { return reinterpret_cast<Desc *>(p->d_scratch + p->plan.o_desc); }
+uint32_t *dev_tiles(vx_plot *p) { return reinterpret_cast<uint32_t *>(p->d_scratch + p->plan.o_tiles); }
+
+// Uploads the descriptor and the single-plot tile prefixes if they changed.
+int upload_desc(vx_plot *p, cudaStream_t s)
+{
+    if (!p->desc_dirty) return VX_OK;
+    if (!p->h_stage) {
+        void *h = nullptr;
+        VX_TRY(p, cudaMallocHost(&h, vx::kStageBytes));
+        p->h_stage = reinterpret_cast<Desc *>(h);
+        VX_TRY(p, cudaEventCreateWithFlags(&p->ev_stage, cudaEventDisableTiming));
+    }
+    if (p->ev_pending) VX_TRY(p, cudaEventSynchronize(p->ev_stage));
+    fill_desc(p, p->h_stage);
+    uint32_t *t = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(p->h_stage) +
+                                               vx::kStageTilesOffset);
+    t[0] = 0; t[1] = p->plan.tiles_hash;   // hash + first scatter
+    t[2] = 0; t[3] = p->plan.tiles_s2;     // second scatter
+    t[4] = 0; t[5] = p->plan.tiles_part;   // sort and match
+    // Only the host-filled part: pre1/pre2 are derived on the device by the
+    // key-setup kernel and must survive a re-upload after vx_plot_bind.
+    VX_TRY(p, cudaMemcpyAsync(dev_desc(p), p->h_stage, offsetof(Desc, pre1), cudaMemcpyHostToDevice, s));
+    VX_TRY(p, cudaMemcpyAsync(dev_tiles(p), t, 6 * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    VX_TRY(p, cudaEventRecord(p->ev_stage, s));
+    p->ev_pending = true;
+    p->desc_dirty = false;
+    return VX_OK;
+}
+
+int ensure_memory(vx_plot *p)
+{
+    if (p->d_t1) return VX_OK;
+    return vx_plot_alloc(p);
+}
+
+int map_status(uint32_t st)
+{
+    if (st & vx::kStTimeout) return VX_ETIMEDOUT;
+    if (st & (vx::kStSlot1Overflow | vx::kStSlot2Overflow | vx::kStCountMismatch |
+              vx::kStPartitionTooBig))
+        return VX_EOVERFLOW;
+    if (st & vx::kStT2Capacity) return VX_ENOMEM;
+    return VX_OK;
+}
+
+std::string status_text(uint32_t st)
+{
+    std::string s;
+    if (st & vx::kStSlot1Overflow) s += "first-level partition slot overflow; ";
+    if (st & vx::kStSlot2Overflow) s += "second-level partition slot overflow; ";
+    if (st & vx::kStCountMismatch) s += "records lost before the sort (count mismatch); ";
+    if (st & vx::kStPartitionTooBig) s += "partition larger than shared memory; ";
+    if (st & vx::kStT2Capacity) s += "Table 2 exceeds its capacity; ";
+    if (st & vx::kStTimeout) s += "device wait timed out; ";
+    return s;
+}
+
+// Kernel sequences.  ev (nullable) receives an event before the first
+// kernel and after each one (tracing); skipped kernels still record.
+cudaError_t launch_table1(const LaunchSet &L, cudaStream_t s, cudaEvent_t *ev = nullptr)
+{
+    cudaError_t e;
+    if (ev) cudaEventRecord(ev[0], s);
+    if ((e = vx::launch_key_setup(L.descs, L.n, s)) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], s);
+    if ((e = vx::launch_hash_scatter(L.descs, L.n, L.t_hash, L.n_hash, vx::HashCfg{L.agg}, s)) !=
+        cudaSuccess)
+        return e;
+    if (ev) cudaEventRecord(ev[2], s);
+    if (L.n_s2 && (e = vx::launch_scatter2(L.descs, L.n, L.t_s2, L.n_s2, s)) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[3], s);
+    if ((e = vx::launch_scan_counts(L.descs, L.n, s)) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[4], s);
+    e = vx::launch_sort(L.descs, L.n, L.t_part, L.n_part, s, L.max_cap2, L.max_dbits);
+    if (ev) cudaEventRecord(ev[5], s);
+    return e;
+}
+
+cudaError_t launch_match_seq(const LaunchSet &L, cudaStream_t s, cudaEvent_t *ev = nullptr)
+{
+    cudaError_t e;
+    if ((e = vx::launch_scan_pairs(L.descs, L.n, s)) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[6], s);
+    e = vx::launch_match(L.descs, L.n, L.t_part, L.n_part, s, L.max_cap2);
+    if (ev) cudaEventRecord(ev[7], s);
+    return e;
+}
+
+LaunchSet single_set(vx_plot *p)
+{
+    LaunchSet L;
+    L.descs = dev_desc(p);
+    L.n = 1;
+    uint32_t *t = dev_tiles(p);
+    L.t_hash = t;
+    L.t_s2 = t + 2;
+    L.t_part = t + 4;
+    L.n_hash = p->plan.tiles_hash;
+    L.n_s2 = p->plan.tiles_s2;
+    L.n_part = p->plan.tiles_part;
+    L.agg = p->plan.agg;
+    L.max_cap2 = p->plan.cap2;
+    L.max_dbits = p->plan.dbits;
+    return L;
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+int vx_version(void) { return (1 << 16) | 0; }
+
+int vx_opts_default(vx_opts *o)
+{
+    if (!o) return VX_EINVAL;
+    memset(o, 0, sizeof(*o));
+    o->size = sizeof(vx_opts);
+    o->coarse_bits = -1;
+    return VX_OK;
+}
+
+const char *vx_strerror(int st)
+{
+    switch (st) {
+    case VX_OK: return "ok";
+    case VX_EINVAL: return "invalid argument";
+    case VX_ENOMEM: return "out of memory or Table-2 capacity exceeded";
+    case VX_ECUDA: return "CUDA runtime error";
+    case VX_ETIMEDOUT: return "device wait timed out";
+    case VX_EBUSY: return "busy";
+    case VX_ENOTREADY: return "not ready";
+    case VX_EOVERFLOW: return "partition slot overflow";
+    default: return "unknown status";
+    }
+}
+
+const char *vx_last_error(const vx_plot *p) { return p ? p->err.c_str() : ""; }
+
+int vx_plot_required_bytes(int K, const vx_opts *opts, uint64_t *t1, uint64_t *t2,
+                           uint64_t *scratch)
+{
+    vx::Plan pl;
+    std::string why;
+    if (vx::make_plan(K, opts, &pl, &why) != VX_OK) return VX_EINVAL;
+    if (t1) *t1 = pl.t1_bytes;
+    if (t2) *t2 = pl.t2_bytes;
+    if (scratch) *scratch = pl.scratch_bytes;
+    return VX_OK;
+}
+
+int vx_plot_create(int K, const uint8_t key[32], const vx_opts *opts, vx_plot **out)
+{
+    if (!out || !key) return VX_EINVAL;
+    *out = nullptr;
+    vx::Plan pl;
+    std::string why;
+    if (vx::make_plan(K, opts, &pl, &why) != VX_OK) return VX_EINVAL;
+    vx_plot *p = new (std::nothrow) vx_plot();
+    if (!p) return VX_ENOMEM;
+    p->K = K;
+    memcpy(p->key, key, 32);
+    if (opts) memcpy(&p->opts, opts, std::min<size_t>(sizeof(vx_opts), opts->size ? opts->size : sizeof(vx_opts)));
+    else vx_opts_default(&p->opts);
+    p->plan = pl;
+    p->t2cap = pl.t2cap;
+    *out = p;
+    return VX_OK;
+}
+
+int vx_plot_bind(vx_plot *p, void *d_t1, void *d_t2, void *d_scratch, uint64_t t2_capacity)
+{
+    if (!p || !d_t1 || !d_t2 || !d_scratch) return VX_EINVAL;
+    if (!aligned(d_t1, 256) || !aligned(d_t2, 256) || !aligned(d_scratch, 256)) {
+        set_err(p, "bound buffers must be 256-byte aligned");
+        return VX_EINVAL;
+    }
+    if (p->ev_pending) cudaEventSynchronize(p->ev_stage);
+    // Re-binding only the Table-2 buffer (e.g. a larger one after VX_ENOMEM)
+    // keeps a finished Table 1: vx_match may run again without vx_table1.
+    const bool keep_t1 = !p->owned && p->d_t1 == (uint8_t *)d_t1 &&
+                         p->d_scratch == (uint8_t *)d_scratch && p->stage >= 1;
+    if (p->have_last) cudaStreamSynchronize(p->last);
+    free_owned(p);
+    if (keep_t1) p->stage = 1;
+    p->d_t1 = (uint8_t *)d_t1;
+    p->d_t2 = (uint8_t *)d_t2;
+    p->d_scratch = (uint8_t *)d_scratch;
+    p->owned = false;
+    p->t2cap = t2_capacity ? t2_capacity : p->plan.t2cap;
+    p->desc_dirty = true;
+    return VX_OK;
+}
+
+int vx_plot_alloc(vx_plot *p)
+{
+    if (!p) return VX_EINVAL;
+    if (p->d_t1) return VX_OK;
+    void *a = nullptr, *b = nullptr, *c = nullptr;
+    cudaError_t e = dev_alloc(&a, p->plan.t1_bytes);
+    if (e == cudaSuccess) e = dev_alloc(&b, p->plan.t2_bytes);
+    if (e == cudaSuccess) e = dev_alloc(&c, p->plan.scratch_bytes);
+    if (e != cudaSuccess) {
+        cudaFree(a);
+        cudaFree(b);
+        cudaFree(c);
+        cudaGetLastError();
+        set_err(p, std::string("device allocation failed: ") + cudaGetErrorName(e));
+        return e == cudaErrorMemoryAllocation ? VX_ENOMEM : VX_ECUDA;
+    }
+    p->d_t1 = (uint8_t *)a;
+    p->d_t2 = (uint8_t *)b;
+    p->d_scratch = (uint8_t *)c;
+    p->owned = true;
+    p->t2cap = p->plan.t2cap;
+    p->desc_dirty = true;
+    return VX_OK;
+}
+
+int vx_table1(vx_plot *p, void *stream)
+{
+    if (!p) return VX_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_memory(p);
+    if (rc) return rc;
+    if ((rc = upload_desc(p, s))) return rc;
+    cudaEvent_t *ev = nullptr;
+    p->prof_cur = -1;
+    if (p->prof_slots > 0 && p->prof_runs < p->prof_slots) {
+        p->prof_cur = p->prof_next++;
+        ev = p->prof_ev + (size_t)p->prof_cur * vx::kProfEvents;
+    }
+    cudaError_t e = launch_table1(single_set(p), s, ev);
+    if (e != cudaSuccess) return cuda_fail(p, "Table-1 launch", e);
+    p->stage = 1;
+    p->t2_known = false;
+    p->last = s;
+    p->have_last = true;
+    return VX_OK;
+}
+
+int vx_match(vx_plot *p, void *stream)
+{
+    if (!p) return VX_EINVAL;
+    if (p->stage < 1) {
+        set_err(p, "vx_match before vx_table1");
+        return VX_ENOTREADY;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = upload_desc(p, s);
+    if (rc) return rc;
+    cudaEvent_t *ev = nullptr;
+    if (p->prof_cur >= 0) {
+        ev = p->prof_ev + (size_t)p->prof_cur * vx::kProfEvents;
+        p->prof_cur = -1;
+        p->prof_runs += 1;
+    }
+    cudaError_t e = launch_match_seq(single_set(p), s, ev);
+    if (e != cudaSuccess) return cuda_fail(p, "match launch", e);
+    p->stage = 2;
+    p->t2_known = false;
+    p->last = s;
+    p->have_last = true;
+    return VX_OK;
+}
+
+int vx_sync(vx_plot *p)
+{
+    if (!p) return VX_EINVAL;
+    if (p->stage == 0) return VX_ENOTREADY;
+    if (p->have_last) VX_TRY(p, cudaStreamSynchronize(p->last));
+    uint32_t st = 0;
+    VX_TRY(p, cudaMemcpy(&st, p->d_scratch + p->plan.o_status, 4, cudaMemcpyDeviceToHost));
+    p->status = st;
+    if (p->stage >= 2) {
+        uint64_t total = 0;
+        VX_TRY(p, cudaMemcpy(&total, p->d_scratch + p->plan.o_t2off + 8 * (1ull << p->plan.p), 8,
+                             cudaMemcpyDeviceToHost));
+        p->t2_count = total;
+        p->t2_known = true;
+    }
+    const int rc = map_status(st);
+    if (rc != VX_OK) set_err(p, status_text(st));
+    return rc;
+}
+
+int vx_table_info(const vx_plot *p, int which, const void **dptr, uint64_t *nrec,
+                  uint32_t *rec_bytes)
+{
+    if (!p || (which != VX_TABLE1 && which != VX_TABLE2)) return VX_EINVAL;
+    if (which == VX_TABLE1) {
+        if (p->stage < 1) return VX_ENOTREADY;
+        if (dptr) *dptr = p->d_t1;
+        if (nrec) *nrec = p->plan.N;
+        if (rec_bytes) *rec_bytes = 12;
+        return VX_OK;
+    }
+    if (p->stage < 2 || !p->t2_known) return VX_ENOTREADY;
+    if (dptr) *dptr = p->d_t2;
+    if (nrec) *nrec = p->t2_count;
+    if (rec_bytes) *rec_bytes = 16;
+    return p->t2_count > p->t2cap ? VX_ENOMEM : VX_OK;
+}
+
+int vx_table1_offsets(vx_plot *p, void *d_out, void *stream)
+{
+    if (!p || !d_out || !aligned(d_out, 8)) return VX_EINVAL;
+    if (p->stage < 1) return VX_ENOTREADY;
+    int rc = upload_desc(p, (cudaStream_t)stream);
+    if (rc) return rc;
+    cudaError_t e = vx::launch_bucket_offsets(dev_desc(p), (uint64_t *)d_out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(p, "offsets launch", e);
+    return VX_OK;
+}
+
+int vx_table_copy(vx_plot *p, int which, uint64_t offset, void *host_dst, uint64_t bytes,
+                  void *stream)
+{
+    if (!p || !host_dst) return VX_EINVAL;
+    const void *src = nullptr;
+    uint64_t n = 0;
+    uint32_t rb = 0;
+    int rc = vx_table_info(p, which, &src, &n, &rb);
+    if (rc != VX_OK) return rc;
+    if (offset > n * rb || bytes > n * rb - offset) return VX_EINVAL;
+    if (bytes == 0) return VX_OK;
+    VX_TRY(p, cudaMemcpyAsync(host_dst, (const uint8_t *)src + offset, bytes, cudaMemcpyDeviceToHost,
+                              (cudaStream_t)stream));
+    return VX_OK;
+}
+
+void vx_plot_destroy(vx_plot *p)
+{
+    if (!p) return;
+    forget_batches(p);
+    if (p->have_last) cudaStreamSynchronize(p->last);
+    if (p->ev_pending) cudaEventSynchronize(p->ev_stage);
+    if (p->release) p->release(p->release_ctx, p);
+    free_owned(p);
+    if (p->h_stage) cudaFreeHost(p->h_stage);
+    if (p->ev_stage) cudaEventDestroy(p->ev_stage);
+    vx_plot_profile(p, 0);
+    delete p;
+}
+
+// -------------------------------------------------------------- tracing
+const char *vx_kernel_name(int k)
+{
+    static const char *names[vx::kProfKernels] = {"key_setup", "hash_scatter", "scatter2",
+                                                  "scan_counts", "sort", "scan_pairs", "match"};
+    return (k >= 0 && k < vx::kProfKernels) ? names[k] : "";
+}
+
+int vx_plot_profile(vx_plot *p, int runs)
+{
+    if (!p || runs < 0 || runs > 100000) return VX_EINVAL;
+    if (p->prof_ev) {
+        if (p->have_last) cudaStreamSynchronize(p->last);
+        for (int i = 0; i < p->prof_slots * vx::kProfEvents; ++i) cudaEventDestroy(p->prof_ev[i]);
+        delete[] p->prof_ev;
+        p->prof_ev = nullptr;
+    }
+    p->prof_slots = p->prof_next = p->prof_runs = 0;
+    p->prof_cur = -1;
+    if (runs == 0) return VX_OK;
+    p->prof_ev = new (std::nothrow) cudaEvent_t[(size_t)runs * vx::kProfEvents]();
+    if (!p->prof_ev) return VX_ENOMEM;
+    for (int i = 0; i < runs * vx::kProfEvents; ++i) {
+        cudaError_t e = cudaEventCreate(&p->prof_ev[i]);
+        if (e != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(p->prof_ev[j]);
+            delete[] p->prof_ev;
+            p->prof_ev = nullptr;
+            return cuda_fail(p, "cudaEventCreate", e);
+        }
+    }
+    p->prof_slots = runs;
+    return VX_OK;
+}
+
+int vx_plot_profile_read(vx_plot *p, double *ms, int cap, int *nkernels, int *nruns)
+{
+    if (!p || !ms || cap < vx::kProfKernels) return VX_EINVAL;
+    for (int k = 0; k < vx::kProfKernels; ++k) ms[k] = 0.0;
+    if (nkernels) *nkernels = vx::kProfKernels;
+    if (nruns) *nruns = p->prof_runs;
+    for (int r = 0; r < p->prof_runs; ++r) {
+        cudaEvent_t *ev = p->prof_ev + (size_t)r * vx::kProfEvents;
+        for (int k = 0; k < vx::kProfKernels; ++k) {
+            VX_TRY(p, cudaEventSynchronize(ev[k + 1]));
+            float t = 0.f;
+            VX_TRY(p, cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+            ms[k] += t;
+        }
+    }
+    return VX_OK;
+}
+
+// ------------------------------------------------------ stand-alone rows
+int vx_hash_nonces(const uint8_t key[32], uint64_t nonce0, uint64_t count, void *d_out,
+                   void *stream)
+{
+    if (!key || (!d_out && count) || !aligned(d_out, 4)) return VX_EINVAL;
+    if (count > (1ull << 32) || nonce0 + count > (1ull << 32)) return VX_EINVAL;
+    uint32_t w[8];
+    key_words(key, w);
+    cudaError_t e = vx::launch_hash_records(w, nonce0, count, (uint32_t *)d_out, (cudaStream_t)stream);
+    return e == cudaSuccess ? VX_OK : VX_ECUDA;
+}
+
+int vx_pair_hash(const uint8_t key[32], const void *d_pairs, uint64_t count, void *d_out,
+                 void *stream)
+{
+    if (!key || ((!d_pairs || !d_out) && count) || !aligned(d_pairs, 8) || !aligned(d_out, 16))
+        return VX_EINVAL;
+    uint32_t w[8];
+    key_words(key, w);
+    cudaError_t e = vx::launch_pair_hash(w, (const uint32_t *)d_pairs, count, (uint4 *)d_out,
+                                         (cudaStream_t)stream);
+    return e == cudaSuccess ? VX_OK : VX_ECUDA;
+}
+
+// Test hook: the next `count` device allocations made by the library fail
+// with cudaErrorMemoryAllocation (host-side fault injection).
+int vx_test_fail_next_allocs(int count)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_fail_allocs = count < 0 ? 0 : count;
+    return VX_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------- batch
+namespace {
+
+// A batch's device workspace and its recorded graph, cached by the exact
+// sequence of plot handles (and their buffers) it was built for.
+struct BatchEntry {
+    std::vector<vx_plot *> plots;
+    std::vector<uint8_t *> bufs;
+    uint8_t *d_ws = nullptr;
+    uint8_t *h_ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+};
+
+std::mutex g_batch_mu;
+std::vector<BatchEntry *> g_batches;
+
+BatchEntry *find_batch(vx_plot *const *plots, int n)
+{
+    for (BatchEntry *b : g_batches) {
+        if ((int)b->plots.size() != n) continue;
+        bool same = true;
+        for (int i = 0; i < n && same; ++i)
+            same = b->plots[i] == plots[i] && b->bufs[i] == plots[i]->d_scratch;
+        if (same) return b;
+    }
+    return nullptr;
+}
+
+void drop_batch(BatchEntry *b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    cudaFree(b->d_ws);
+    cudaFreeHost(b->h_ws);
+    delete b;
+}
+
+}  // namespace
+
+namespace vx {
+
+size_t batch_ws_bytes(int n)
+{
+    const size_t o_tiles = ((size_t)n * sizeof(Desc) + 255) & ~(size_t)255;
+    return o_tiles + 3 * (size_t)(n + 1) * 4;
+}
+
+int batch_prepare(vx_plot *const *plots, int n, uint8_t *h_ws, uint8_t *d_ws, LaunchSet *L)
+{
+    const size_t o_tiles = ((size_t)n * sizeof(Desc) + 255) & ~(size_t)255;
+    Desc *hd = reinterpret_cast<Desc *>(h_ws);
+    uint32_t *th = reinterpret_cast<uint32_t *>(h_ws + o_tiles);
+    uint32_t *ts = th + (n + 1), *tp = ts + (n + 1);
+    th[0] = ts[0] = tp[0] = 0;
+    L->max_cap2 = 0;
+    L->max_dbits = 1;
+    int min_bits = 64;
+    uint64_t sh = 0, ss = 0, sp = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!plots[i] || !plots[i]->d_t1) return VX_EINVAL;
+        const Plan &pl = plots[i]->plan;
+        fill_desc(plots[i], hd + i);
+        sh += pl.tiles_hash;
+        ss += pl.tiles_s2;
+        sp += pl.tiles_part;
+        if (sh > 0x7FFFFFFFull || ss > 0x7FFFFFFFull || sp > 0x7FFFFFFFull) return VX_EINVAL;
+        th[i + 1] = (uint32_t)sh;
+        ts[i + 1] = (uint32_t)ss;
+        tp[i + 1] = (uint32_t)sp;
+        L->max_cap2 = std::max(L->max_cap2, pl.cap2);
+        L->max_dbits = std::max(L->max_dbits, pl.dbits);
+        min_bits = std::min(min_bits, pl.p2 > 0 ? pl.p1 : pl.p);
+    }
+    L->agg = min_bits <= kAggMaxBits;
+    L->descs = reinterpret_cast<Desc *>(d_ws);
+    L->n = n;
+    L->t_hash = reinterpret_cast<uint32_t *>(d_ws + o_tiles);
+    L->t_s2 = L->t_hash + (n + 1);
+    L->t_part = L->t_s2 + (n + 1);
+    L->n_hash = th[n];
+    L->n_s2 = ts[n];
+    L->n_part = tp[n];
+    return VX_OK;
+}
+
+cudaError_t launch_plot_seq(const LaunchSet &L, cudaStream_t s)
+{
+    cudaError_t e = launch_table1(L, s);
+    if (e == cudaSuccess) e = launch_match_seq(L, s);
+    return e;
+}
+
+void mark_issued(vx_plot *const *plots, int n, cudaStream_t s)
+{
+    for (int i = 0; i < n; ++i) {
+        vx_plot *p = plots[i];
+        p->stage = 2;
+        p->t2_known = false;
+        p->last = s;
+        p->have_last = true;
+    }
+}
+
+int ensure_memory_ext(vx_plot *p) { return ensure_memory(p); }
+
+}  // namespace vx
+
+extern "C" int vx_plot_batch(vx_plot *const *plots, int n, void *stream)
+{
+    if (!plots || n <= 0) return VX_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < n; ++i) {
+        if (!plots[i]) return VX_EINVAL;
+        int rc = ensure_memory(plots[i]);
+        if (rc) return rc;
+    }
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    BatchEntry *b = find_batch(plots, n);
+    if (!b) {
+        b = new BatchEntry();
+        b->plots.assign(plots, plots + n);
+        for (int i = 0; i < n; ++i) b->bufs.push_back(plots[i]->d_scratch);
+        b->ws_bytes = vx::batch_ws_bytes(n);
+        if (cudaMallocHost((void **)&b->h_ws, b->ws_bytes) != cudaSuccess ||
+            dev_alloc((void **)&b->d_ws, b->ws_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            drop_batch(b);
+            return VX_ENOMEM;
+        }
+        LaunchSet L;
+        if (vx::batch_prepare(plots, n, b->h_ws, b->d_ws, &L) != VX_OK) {
+            drop_batch(b);
+            return VX_EINVAL;
+        }
+        // The workspace is uploaded once; replays of the graph reuse it.
+        cudaError_t e = cudaMemcpy(b->d_ws, b->h_ws, b->ws_bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+        cudaGraph_t g = nullptr;
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = vx::launch_plot_seq(L, b->cap_stream);
+            e = cudaStreamEndCapture(b->cap_stream, &g);
+            if (e == cudaSuccess) e = e1;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            drop_batch(b);
+            for (int i = 0; i < n; ++i) set_err(plots[i], std::string("batch graph: ") + cudaGetErrorName(e));
+            return VX_ECUDA;
+        }
+        g_batches.push_back(b);
+        while (g_batches.size() > 16) {  // bounded cache
+            drop_batch(g_batches.front());
+            g_batches.erase(g_batches.begin());
+        }
+    }
+    cudaError_t e = cudaGraphLaunch(b->exec, s);
+    if (e != cudaSuccess) {
+        for (int i = 0; i < n; ++i) set_err(plots[i], std::string("batch launch: ") + cudaGetErrorName(e));
+        return VX_ECUDA;
+    }
+    vx::mark_issued(plots, n, s);
+    return VX_OK;
+}
+
+namespace {
+// Forgets cached batch graphs that reference plot p (called on destroy).
+void forget_batches(vx_plot *p)
+{
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t i = 0; i < g_batches.size();) {
+        BatchEntry *b = g_batches[i];
+        if (std::find(b->plots.begin(), b->plots.end(), p) != b->plots.end()) {
+            drop_batch(b);
+            g_batches.erase(g_batches.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+}  // namespace
+
+// --------------------------------------------------------- file write
+namespace {
+std::mutex g_stage_mu;
+uint8_t *g_stage = nullptr;      // pinned staging, two halves
+cudaStream_t g_copy_stream = nullptr;
+cudaEvent_t g_copy_ev[2] = {nullptr, nullptr};
+}  // namespace
+
+extern "C" int vx_plot_write(vx_plot *p, const char *path, double *sec_d2h, double *sec_total)
+{
+    if (!p || !path) return VX_EINVAL;
+    int rc = vx_sync(p);
+    if (rc != VX_OK) return rc;
+    const void *src = nullptr;
+    uint64_t nrec = 0;
+    uint32_t rb = 0;
+    if ((rc = vx_table_info(p, VX_TABLE2, &src, &nrec, &rb)) != VX_OK) return rc;
+    std::lock_guard<std::mutex> lk(g_stage_mu);
+    if (!g_stage) {
+        VX_TRY(p, cudaMallocHost((void **)&g_stage, vx::kWriteStageBytes));
+        VX_TRY(p, cudaStreamCreateWithFlags(&g_copy_stream, cudaStreamNonBlocking));
+        VX_TRY(p, cudaEventCreateWithFlags(&g_copy_ev[0], cudaEventDisableTiming));
+        VX_TRY(p, cudaEventCreateWithFlags(&g_copy_ev[1], cudaEventDisableTiming));
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    int fd = open(path, O_WRONLY | O_CREAT | O_TRUNC, 0644);
+    if (fd < 0) {
+        set_err(p, std::string("cannot open ") + path);
+        return VX_EINVAL;
+    }
+    const uint64_t total = nrec * rb;
+    const uint64_t half = vx::kWriteStageBytes / 2;
+    double d2h = 0;
+    uint64_t done = 0;
+    int slot = 0;
+    // Double buffering: copy block k+1 while block k is written.
+    uint64_t pending_bytes[2] = {0, 0};
+    auto issue = [&](int sl, uint64_t at) -> cudaError_t {
+        const uint64_t n = std::min(half, total - at);
+        pending_bytes[sl] = n;
+        cudaError_t e = cudaMemcpyAsync(g_stage + sl * half, (const uint8_t *)src + at, n,
+                                        cudaMemcpyDeviceToHost, g_copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(g_copy_ev[sl], g_copy_stream);
+        return e;
+    };
+    bool ok = true;
+    if (total > 0) {
+        if (issue(0, 0) != cudaSuccess) ok = false;
+        uint64_t next = std::min(half, total);
+        while (ok && done < total) {
+            const auto c0 = std::chrono::steady_clock::now();
+            if (cudaEventSynchronize(g_copy_ev[slot]) != cudaSuccess) { ok = false; break; }
+            d2h += std::chrono::duration<double>(std::chrono::steady_clock::now() - c0).count();
+            if (next < total) {
+                if (issue(slot ^ 1, next) != cudaSuccess) { ok = false; break; }
+                next += pending_bytes[slot ^ 1];
+            }
+            const uint8_t *buf = g_stage + slot * half;
+            uint64_t left = pending_bytes[slot];
+            while (left > 0 && ok) {   // sequential 4 MB writes
+                const size_t chunk = (size_t)std::min<uint64_t>(left, vx::kWriteChunkBytes);
+                ssize_t w = ::write(fd, buf, chunk);
+                if (w <= 0) { ok = false; break; }
+                buf += w;
+                left -= (uint64_t)w;
+            }
+            done += pending_bytes[slot];
+            slot ^= 1;
+        }
+    }
+    if (close(fd) != 0) ok = false;
+    cudaStreamSynchronize(g_copy_stream);
+    if (!ok) {
+        set_err(p, "Table-2 write failed");
+        return VX_ECUDA;
+    }
+    if (sec_d2h) *sec_d2h = d2h;
+    if (sec_total) *sec_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return VX_OK;
+}

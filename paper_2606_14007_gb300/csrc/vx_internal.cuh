@@ -1,0 +1,265 @@
+// vx_internal.cuh -- shared definitions of the sm_103a plotting kernels.
+//
+// The plot descriptor (one per plot, in device memory), the keyed BLAKE3
+// device core, and the launch helpers the host engine and every kernel
+// translation unit agree on.  Nothing here is shared with the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vx {
+
+// ---------------------------------------------------------------- limits
+constexpr int kBucketBits = 24;          // 2^24 logical buckets (Sec. I-A, III-B)
+constexpr int kMaxK = 32;                // u32 nonces
+constexpr int kMaxCoarseBits = 10;       // first scatter level, <= 1024 bins
+constexpr int kMaxFineBits = 10;         // second scatter level, <= 1024 bins
+constexpr int kScatterTile = 4096;       // records per CTA in the second scatter level
+constexpr int kScatterThreads = 256;
+constexpr int kSortThreads = 256;
+constexpr int kMatchThreads = 256;
+constexpr int kMaxSortDigitBits = 13;    // counting-sort digit of the partition sort
+constexpr uint32_t kMaxPartition = 16384;  // records one partition may hold (smem)
+constexpr size_t kMaxSmemPerCta = 227 * 1024;  // opt-in dynamic shared memory per CTA
+
+// Status-word bits (device side; the host maps them to VX_E* codes).
+constexpr uint32_t kStSlot1Overflow = 1u << 0;
+constexpr uint32_t kStSlot2Overflow = 1u << 1;
+constexpr uint32_t kStCountMismatch = 1u << 2;
+constexpr uint32_t kStT2Capacity = 1u << 3;
+constexpr uint32_t kStPartitionTooBig = 1u << 4;
+constexpr uint32_t kStTimeout = 1u << 5;
+
+// ------------------------------------------------------ plot descriptor
+// One plot's plan and buffers.  The host fills everything but pre1/pre2,
+// which the key-setup kernel derives from the key on the device.
+struct Desc {
+    uint64_t N;          // 2^K nonces
+    uint64_t D;          // match distance
+    uint64_t t2cap;      // Table-2 capacity (records)
+    int32_t K;
+    int32_t p;           // partition bits (physical partitions = 2^p)
+    int32_t p1;          // first scatter level bits (hash kernel)
+    int32_t p2;          // second scatter level bits (p = p1 + p2)
+    int32_t dbits;       // counting-sort digit bits inside a partition
+    uint32_t cap1;       // records per level-1 slot (p2 > 0 only)
+    uint32_t cap2;       // records per level-2 slot (final partitions)
+    uint32_t chunks1;    // scatter-2 CTAs per level-1 slot = ceil(cap1 / tile)
+    uint64_t *a_keys;    // level-1 slots, SoA: key64 [2^p1 * cap1]
+    uint32_t *a_nonces;  //                      nonce [2^p1 * cap1]
+    uint64_t *b_keys;    // level-2 slots, SoA: key64 [2^p * cap2]
+    uint32_t *b_nonces;  //                      nonce [2^p * cap2]
+    uint32_t *cnt1;      // [2^p1] level-1 fill counters
+    uint32_t *cnt2;      // [2^p]  level-2 fill counters
+    uint64_t *t1off;     // [2^p + 1] Table-1 record offset of each partition
+    uint64_t *pairs;     // [2^p] Table-2 pairs of each partition
+    uint64_t *t2off;     // [2^p + 1] Table-2 record offset of each partition
+    uint32_t *status;    // status word
+    uint8_t *t1;         // Table 1, 12-byte records
+    uint8_t *t2;         // Table 2, 16-byte records
+    uint32_t key[8];     // plot key, LE words
+    uint32_t pre1[16];   // Table-1 hash state after round-1 columns 1..3
+    uint32_t pre2[16];   // pair-hash state after round-1 columns 1..3
+};
+
+// Maps a CTA's global tile index to (plot, local tile) through an exclusive
+// prefix of per-plot tile counts (batch launches group many plots).
+__device__ __forceinline__ int find_plot(const uint32_t *__restrict__ tile_start, int nplots,
+                                         uint32_t tile)
+{
+    int lo = 0, hi = nplots;  // invariant: tile_start[lo] <= tile < tile_start[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(tile_start + mid) <= tile) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------ keyed BLAKE3 core
+// BLAKE3 constants: IV (the SHA-256 initial words) and domain flags.
+constexpr uint32_t kIV0 = 0x6A09E667u, kIV1 = 0xBB67AE85u, kIV2 = 0x3C6EF372u,
+                   kIV3 = 0xA54FF53Au;
+constexpr uint32_t kFlagsKeyedRootChunk = 1u /*CHUNK_START*/ | 2u /*CHUNK_END*/ |
+                                          8u /*ROOT*/ | 16u /*KEYED_HASH*/;
+
+// Rotations by 16 and 8 are byte moves (PRMT); by 12 and 7 funnel shifts.
+__device__ __forceinline__ uint32_t ror16(uint32_t x) { return __byte_perm(x, 0, 0x1032); }
+__device__ __forceinline__ uint32_t ror8(uint32_t x) { return __byte_perm(x, 0, 0x0321); }
+__device__ __forceinline__ uint32_t ror12(uint32_t x) { return __funnelshift_r(x, x, 12); }
+__device__ __forceinline__ uint32_t ror7(uint32_t x) { return __funnelshift_r(x, x, 7); }
+__device__ __forceinline__ uint32_t bswap32(uint32_t x) { return __byte_perm(x, 0, 0x0123); }
+
+#define VX_G(a, b, c, d, mx, my)       \
+    do {                               \
+        a = a + b + (mx);              \
+        d = ::vx::ror16(d ^ a);        \
+        c = c + d;                     \
+        b = ::vx::ror12(b ^ c);        \
+        a = a + b + (my);              \
+        d = ::vx::ror8(d ^ a);         \
+        c = c + d;                     \
+        b = ::vx::ror7(b ^ c);         \
+    } while (0)
+
+// Message schedule step between rounds: new m[i] = old m[perm[i]] with
+// perm = {2,6,3,10,7,0,4,13,1,11,12,5,9,14,15,8}.  Pure register renaming.
+#define VX_PERMUTE(m)                                                              \
+    do {                                                                           \
+        uint32_t t0 = m[2], t1 = m[6], t2 = m[3], t3 = m[10], t4 = m[7], t5 = m[0], \
+                 t6 = m[4], t7 = m[13], t8 = m[1], t9 = m[11], t10 = m[12],         \
+                 t11 = m[5], t12 = m[9], t13 = m[14], t14 = m[15], t15 = m[8];      \
+        m[0] = t0; m[1] = t1; m[2] = t2; m[3] = t3; m[4] = t4; m[5] = t5;         \
+        m[6] = t6; m[7] = t7; m[8] = t8; m[9] = t9; m[10] = t10; m[11] = t11;     \
+        m[12] = t12; m[13] = t13; m[14] = t14; m[15] = t15;                       \
+    } while (0)
+
+// Per-key state of a one-block keyed hash whose message occupies words 0..1
+// only: v = {key, IV0..3, counter 0, 0, block_len, flags}, with the three
+// round-1 column G's that see only zero message words already applied.
+__device__ __forceinline__ void b3_key_setup(const uint32_t key[8], uint32_t block_len,
+                                             uint32_t pre[16])
+{
+    uint32_t v0 = key[0], v1 = key[1], v2 = key[2], v3 = key[3];
+    uint32_t v4 = key[4], v5 = key[5], v6 = key[6], v7 = key[7];
+    uint32_t v8 = kIV0, v9 = kIV1, v10 = kIV2, v11 = kIV3;
+    uint32_t v12 = 0, v13 = 0, v14 = block_len, v15 = kFlagsKeyedRootChunk;
+    VX_G(v1, v5, v9, v13, 0u, 0u);
+    VX_G(v2, v6, v10, v14, 0u, 0u);
+    VX_G(v3, v7, v11, v15, 0u, 0u);
+    pre[0] = v0; pre[1] = v1; pre[2] = v2; pre[3] = v3;
+    pre[4] = v4; pre[5] = v5; pre[6] = v6; pre[7] = v7;
+    pre[8] = v8; pre[9] = v9; pre[10] = v10; pre[11] = v11;
+    pre[12] = v12; pre[13] = v13; pre[14] = v14; pre[15] = v15;
+}
+
+// The rest of the compression for message words (m0, m1, 0, ..., 0):
+// round-1 column 0 and diagonals, rounds 2..7, and output words 0 and 1
+// (hash bytes 0..7).  TWO_WORDS = false fixes m1 = 0 (4-byte messages).
+template <bool TWO_WORDS>
+__device__ __forceinline__ void b3_finish(const uint32_t pre[16], uint32_t m0, uint32_t m1,
+                                          uint32_t &h0, uint32_t &h1)
+{
+    uint32_t v0 = pre[0], v1 = pre[1], v2 = pre[2], v3 = pre[3];
+    uint32_t v4 = pre[4], v5 = pre[5], v6 = pre[6], v7 = pre[7];
+    uint32_t v8 = pre[8], v9 = pre[9], v10 = pre[10], v11 = pre[11];
+    uint32_t v12 = pre[12], v13 = pre[13], v14 = pre[14], v15 = pre[15];
+    uint32_t m[16];
+    m[0] = m0;
+    m[1] = TWO_WORDS ? m1 : 0u;
+#pragma unroll
+    for (int i = 2; i < 16; ++i) m[i] = 0u;
+    // Round 1 (columns 1..3 are in pre).
+    VX_G(v0, v4, v8, v12, m[0], m[1]);
+    VX_G(v0, v5, v10, v15, m[8], m[9]);
+    VX_G(v1, v6, v11, v12, m[10], m[11]);
+    VX_G(v2, v7, v8, v13, m[12], m[13]);
+    VX_G(v3, v4, v9, v14, m[14], m[15]);
+#pragma unroll
+    for (int r = 1; r < 7; ++r) {
+        VX_PERMUTE(m);
+        VX_G(v0, v4, v8, v12, m[0], m[1]);
+        VX_G(v1, v5, v9, v13, m[2], m[3]);
+        VX_G(v2, v6, v10, v14, m[4], m[5]);
+        VX_G(v3, v7, v11, v15, m[6], m[7]);
+        VX_G(v0, v5, v10, v15, m[8], m[9]);
+        VX_G(v1, v6, v11, v12, m[10], m[11]);
+        VX_G(v2, v7, v8, v13, m[12], m[13]);
+        VX_G(v3, v4, v9, v14, m[14], m[15]);
+    }
+    h0 = v0 ^ v8;
+    h1 = v1 ^ v9;
+}
+
+// key64 = big-endian u64 of hash bytes 0..7 (h0 holds bytes 0..3 LE).
+__device__ __forceinline__ uint64_t key64_of(uint32_t h0, uint32_t h1)
+{
+    return ((uint64_t)bswap32(h0) << 32) | (uint64_t)bswap32(h1);
+}
+
+// --------------------------------------------------------- block helpers
+// Exclusive scan of one u32 per thread over a CTA of NT threads; returns the
+// thread's exclusive prefix, writes the CTA total to *total.  `ws` holds
+// NT/32 + 1 words of shared memory.
+template <int NT>
+__device__ __forceinline__ uint32_t block_exclusive_scan_u32(uint32_t x, uint32_t *ws,
+                                                             uint32_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) ws[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < NT / 32 ? ws[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < NT / 32) ws[lane] = wi - w;
+        if (lane == NT / 32 - 1) ws[NT / 32] = wi;
+    }
+    __syncthreads();
+    uint32_t r = ws[warp] + incl - x;
+    *total = ws[NT / 32];
+    __syncthreads();
+    return r;
+}
+
+template <int NT>
+__device__ __forceinline__ uint64_t block_sum_u64(uint64_t x, uint64_t *ws)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) ws[warp] = x;
+    __syncthreads();
+    uint64_t s = 0;
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < NT / 32; ++w) s += ws[w];
+        ws[NT / 32] = s;
+    }
+    __syncthreads();
+    s = ws[NT / 32];
+    __syncthreads();
+    return s;
+}
+
+}  // namespace vx
+
+// ----------------------------------------------- launch entry points (host)
+// Each returns the launch's cudaGetLastError().  `descs` and the tile_start
+// arrays (exclusive prefixes of per-plot CTA counts, nplots + 1 entries)
+// live in device memory; nplots >= 1.
+namespace vx {
+struct HashCfg {
+    bool agg;     // warp-aggregated histogram (few first-level bins)
+};
+cudaError_t launch_key_setup(Desc *descs, int nplots, cudaStream_t s);
+cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *tile_start,
+                                uint32_t total_tiles, HashCfg cfg, cudaStream_t s);
+cudaError_t launch_scatter2(const Desc *descs, int nplots, const uint32_t *tile_start,
+                            uint32_t total_tiles, cudaStream_t s);
+cudaError_t launch_scan_counts(const Desc *descs, int nplots, cudaStream_t s);
+cudaError_t launch_sort(const Desc *descs, int nplots, const uint32_t *tile_start,
+                        uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits);
+cudaError_t launch_scan_pairs(const Desc *descs, int nplots, cudaStream_t s);
+cudaError_t launch_match(const Desc *descs, int nplots, const uint32_t *tile_start,
+                         uint32_t total_tiles, cudaStream_t s, uint32_t max_cap);
+cudaError_t launch_bucket_offsets(const Desc *desc, uint64_t *out, cudaStream_t s);
+cudaError_t launch_hash_records(const uint32_t key[8], uint64_t nonce0, uint64_t count,
+                                uint32_t *out, cudaStream_t s);
+cudaError_t launch_pair_hash(const uint32_t key[8], const uint32_t *pairs, uint64_t count,
+                             uint4 *out, cudaStream_t s);
+size_t sort_smem_bytes(uint32_t cap, int dbits);
+size_t match_smem_bytes(uint32_t cap);
+constexpr int kHashThreads = 256;
+constexpr int kHashNoncesPerThread = 8;
+constexpr int kHashTile = kHashThreads * kHashNoncesPerThread;
+}  // namespace vx

@@ -1,0 +1,169 @@
+// vx_plan.h -- the plot planner: from (K, options) to partition counts, slot
+// capacities, buffer sizes and kernel grid sizes.  Host only, no CUDA calls,
+// so it can be checked on a machine without a GPU.
+//
+// Paper basis: Table 1 has 2^K records in 2^24 buckets (Sec. I-A, III-B);
+// the paper's per-bucket capacity RPB (Sec. III-B) is replaced by physical
+// partitions (runs of 2^(24-p) whole logical buckets) with Poisson-sized
+// slots; Table 2 gets a capacity from the expected pair count.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+
+#include "../../include/vaultx.h"
+
+namespace vx {
+
+constexpr int kDefaultPartLog2 = 12;       // mean records per physical partition: 4096
+constexpr uint32_t kDefaultSlackSigma = 12;
+constexpr int kMaxPartBits = 20;           // two scatter levels of <= 10 bits each
+constexpr int kAggMaxBits = 6;             // warp-aggregate ranks up to 64 bins
+constexpr size_t kStageBytes = 4096;       // pinned staging: Desc + tile prefixes
+constexpr size_t kStageTilesOffset = 3584;
+constexpr uint64_t kWriteStageBytes = 256ull << 20;  // Sec. III-B: 256 MB pinned staging
+constexpr uint64_t kWriteChunkBytes = 4ull << 20;    // Sec. III-A: 4 MB sequential chunks
+constexpr uint64_t kPlanHashTile = 2048;   // nonces per hash CTA (threads x nonces/thread)
+
+struct Plan {
+    int K, s, p, p1, p2, dbits;
+    uint64_t N, D, t2cap;
+    uint32_t cap1, cap2, chunks1;
+    bool agg;
+    uint32_t tiles_hash, tiles_s2, tiles_part;
+    uint64_t regionA_keys, regionB_keys;   // byte offset of the nonce array in each slot region
+    uint64_t regionA_bytes, regionB_bytes;
+    uint64_t t1_bytes, t2_bytes, scratch_bytes;
+    uint64_t o_status, o_cnt1, o_cnt2, o_t1off, o_pairs, o_t2off, o_desc, o_tiles;
+};
+
+inline uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+// Capacity of a slot expecting `avg` records (Poisson): avg + slack * sd,
+// rounded up to a multiple of 4 records.
+inline uint64_t slot_capacity(double avg, uint32_t slack)
+{
+    return round_up((uint64_t)std::ceil(avg + slack * std::sqrt(avg) + 16.0), 4);
+}
+
+// Expected Table-2 pairs: 2^24 buckets of Poisson(lambda) records, key64
+// uniform over a bucket of width 2^40; a pair matches with probability
+// 2u - u^2 (u = D / 2^40, all pairs when u >= 1).
+inline double expected_pairs(uint64_t N, uint64_t D)
+{
+    const double lam = (double)N / 16777216.0;
+    const double u = (double)D / 1099511627776.0;
+    const double q = u >= 1.0 ? 1.0 : 2.0 * u - u * u;
+    return 16777216.0 * lam * lam / 2.0 * q;
+}
+
+inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, std::string *why, size_t desc_bytes)
+{
+    if (K < 1 || K > 32) {
+        *why = "K must be in 1..32";
+        return VX_EINVAL;
+    }
+    vx_opts opts;
+    memset(&opts, 0, sizeof(opts));
+    opts.coarse_bits = -1;
+    if (o) {
+        if (o->size != 0 && o->size < sizeof(vx_opts)) {
+            *why = "vx_opts.size too small";
+            return VX_EINVAL;
+        }
+        memcpy(&opts, o, sizeof(opts));
+    }
+    Plan P;
+    memset(&P, 0, sizeof(P));
+    P.K = K;
+    P.N = 1ull << K;
+    P.D = opts.match_distance ? opts.match_distance : (1ull << (64 - K));
+    P.s = opts.partition_log2 ? opts.partition_log2 : kDefaultPartLog2;
+    if (P.s < 6 || P.s > 13) {
+        *why = "partition_log2 must be in 6..13";
+        return VX_EINVAL;
+    }
+    const uint32_t slack = opts.slack_sigma ? opts.slack_sigma : kDefaultSlackSigma;
+    P.p = K - P.s;
+    if (P.p < 0) P.p = 0;
+    if (P.p > kMaxPartBits) P.p = kMaxPartBits;
+    if (opts.coarse_bits >= 0) {
+        P.p1 = opts.coarse_bits < P.p ? opts.coarse_bits : P.p;
+    } else {
+        P.p1 = P.p <= 10 ? P.p : P.p / 2;
+    }
+    P.p2 = P.p - P.p1;
+    if (P.p1 > 10 || P.p2 > 10) {
+        *why = "coarse_bits leaves a scatter level wider than 10 bits";
+        return VX_EINVAL;
+    }
+    const double avg2 = (double)P.N / (double)(1ull << P.p);
+    uint64_t cap2 = P.p == 0 ? round_up(P.N, 4) : slot_capacity(avg2, slack);
+    if (cap2 > round_up(P.N, 4)) cap2 = round_up(P.N, 4);
+    if (cap2 > 16384) {
+        *why = "partition slot larger than the sort's shared-memory capacity";
+        return VX_EINVAL;
+    }
+    P.cap2 = (uint32_t)cap2;
+    if (P.p2 > 0) {
+        const double avg1 = (double)P.N / (double)(1ull << P.p1);
+        uint64_t cap1 = P.p1 == 0 ? round_up(P.N, 4) : slot_capacity(avg1, slack);
+        if (cap1 > round_up(P.N, 4)) cap1 = round_up(P.N, 4);
+        if (cap1 > 0xFFFFFF00ull) {
+            *why = "first-level slot too large";
+            return VX_EINVAL;
+        }
+        P.cap1 = (uint32_t)cap1;
+        P.chunks1 = (uint32_t)((cap1 + 4095) / 4096);
+    }
+    int db = K - P.p;
+    if (db < 1) db = 1;
+    if (db > 13) db = 13;
+    P.dbits = db;
+    P.agg = (P.p2 > 0 ? P.p1 : P.p) <= kAggMaxBits;
+
+    if (opts.t2_capacity) {
+        P.t2cap = opts.t2_capacity;
+    } else {
+        const double E = expected_pairs(P.N, P.D);
+        P.t2cap = round_up((uint64_t)std::ceil(E + 24.0 * std::sqrt(E) + 4096.0), 256);
+    }
+    // Grids (tile sizes are the kernels' compile-time tiles).
+    P.tiles_hash = (uint32_t)((P.N + kPlanHashTile - 1) / kPlanHashTile);
+    P.tiles_s2 = P.p2 > 0 ? (uint32_t)(((uint64_t)1 << P.p1) * P.chunks1) : 0u;
+    P.tiles_part = (uint32_t)(1ull << P.p);
+
+    // Slot regions (SoA: key64 array, then nonce array).
+    if (P.p2 > 0) {
+        const uint64_t recs = ((uint64_t)1 << P.p1) * P.cap1;
+        P.regionA_keys = recs * 8;
+        P.regionA_bytes = recs * 12;
+    }
+    {
+        const uint64_t recs = ((uint64_t)1 << P.p) * P.cap2;
+        P.regionB_keys = recs * 8;
+        P.regionB_bytes = recs * 12;
+    }
+    const uint64_t t1_tab = 12 * P.N;
+    const uint64_t t2_tab = 16 * P.t2cap;
+    P.t1_bytes = round_up((t1_tab > P.regionA_bytes ? t1_tab : P.regionA_bytes) + 256, 256);
+    P.t2_bytes = round_up((t2_tab > P.regionB_bytes ? t2_tab : P.regionB_bytes) + 256, 256);
+    // Scratch layout.
+    const uint64_t np = 1ull << P.p;
+    uint64_t at = 0;
+    P.o_status = at; at += 256;
+    P.o_cnt1 = at; at = round_up(at + 4 * ((uint64_t)1 << P.p1), 256);
+    P.o_cnt2 = at; at = round_up(at + 4 * np, 256);
+    P.o_t1off = at; at = round_up(at + 8 * (np + 1), 256);
+    P.o_pairs = at; at = round_up(at + 8 * np, 256);
+    P.o_t2off = at; at = round_up(at + 8 * (np + 1), 256);
+    P.o_desc = at; at = round_up(at + desc_bytes, 256);
+    P.o_tiles = at; at = round_up(at + 64, 256);
+    P.scratch_bytes = at;
+    *pl = P;
+    return VX_OK;
+}
+
+}  // namespace vx

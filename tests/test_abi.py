@@ -1,0 +1,127 @@
+"""C ABI checks that need no GPU: the library builds and loads, exports every
+symbol include/vaultx.h declares, and its host logic (planner, argument
+validation, call-order errors) behaves.  No compute call is made here."""
+import ctypes
+import math
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "vaultx.h")
+
+
+@pytest.fixture(scope="module")
+def vx():
+    from paper_2606_14007_gb300 import _build
+    _build.build()
+    from paper_2606_14007_gb300 import vaultx
+    vaultx.lib()
+    return vaultx
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vx_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_boundary_calls():
+    names = declared_symbols()
+    for must in ["vx_plot_create", "vx_table1", "vx_match", "vx_plot_batch", "vx_serve_submit",
+                 "vx_serve_poll", "vx_plot_required_bytes", "vx_plot_bind", "vx_table_info",
+                 "vx_table1_offsets", "vx_table_copy", "vx_plot_write", "vx_plot_destroy",
+                 "vx_sync", "vx_strerror", "vx_hash_nonces", "vx_pair_hash"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(vx):
+    out = subprocess.run(["nm", "-D", "--defined-only", vx.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (vx_[a-z0-9_]+)$", out, flags=re.M))
+    missing = [n for n in declared_symbols() if n not in exported]
+    assert not missing, missing
+    L = vx.lib()
+    for n in declared_symbols():
+        assert getattr(L, n) is not None
+
+
+def test_library_is_sm103a_only():
+    from paper_2606_14007_gb300 import _build
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_strerror_and_version(vx):
+    assert vx.strerror(0) == "ok"
+    assert "overflow" in vx.strerror(vx.VX_EOVERFLOW)
+    assert vx.lib().vx_version() >> 16 == 1
+
+
+def test_required_bytes_footprints(vx):
+    for K in range(1, 33):
+        t1, t2, sc = vx.vx_plot_required_bytes(K)
+        N = 1 << K
+        assert t1 >= 12 * N and t1 % 256 == 0
+        lam = N / 2 ** 24
+        E = 2 ** 24 * lam * lam / 2 * (1.0 if K <= 24 else (2 / lam - 1 / lam ** 2))
+        assert t2 >= 16 * E
+        assert sc > 0 and sc % 256 == 0
+    # K = 31: the tables dominate, scratch is megabytes (offsets, counters).
+    t1, t2, sc = vx.vx_plot_required_bytes(31)
+    assert t1 < 1.05 * 12 * 2 ** 31
+    assert t2 < 1.05 * 16 * 2 ** 31
+    assert sc < 64 << 20
+
+
+def test_required_bytes_rejects_bad_arguments(vx):
+    for K in [0, -1, 33, 64]:
+        with pytest.raises(vx.VxError) as ei:
+            vx.vx_plot_required_bytes(K)
+        assert ei.value.code == vx.VX_EINVAL
+    for kw in [dict(partition_log2=5), dict(partition_log2=14), dict(coarse_bits=11),
+               dict(slack_sigma=400, partition_log2=13)]:
+        with pytest.raises(vx.VxError):
+            vx.vx_plot_required_bytes(31, vx.make_opts(**kw))
+    bad = vx.make_opts()
+    bad.size = 8
+    with pytest.raises(vx.VxError):
+        vx.vx_plot_required_bytes(20, bad)
+
+
+def test_create_and_destroy_without_device(vx):
+    key = bytes(range(32))
+    h = vx.vx_plot_create(20, key)
+    assert h
+    # Call-order errors are reported, not crashed on.
+    _, _, _, rc = vx.vx_table_info(h, vx.VX_TABLE1, check=False)
+    assert rc == vx.VX_ENOTREADY
+    assert vx.lib().vx_match(h, None) == vx.VX_ENOTREADY
+    assert vx.lib().vx_sync(h) == vx.VX_ENOTREADY
+    vx.vx_plot_destroy(h)
+    with pytest.raises(ValueError):
+        vx.vx_plot_create(20, b"short")
+    assert vx.lib().vx_plot_create(40, key, None, ctypes.byref(ctypes.c_void_p())) == vx.VX_EINVAL
+
+
+def test_bind_rejects_misaligned(vx):
+    h = vx.vx_plot_create(12, bytes(32))
+    assert vx.lib().vx_plot_bind(h, 0x1000 + 8, 0x2000, 0x3000, 0) == vx.VX_EINVAL
+    assert vx.lib().vx_plot_bind(h, None, 0x2000, 0x3000, 0) == vx.VX_EINVAL
+    vx.vx_plot_destroy(h)
+
+
+def test_partition_plan_shape(vx):
+    # More partitions as K grows; single level while partitions fit one
+    # scatter level; a slot must hold the mean plus the slack.
+    prev = None
+    for K in [12, 16, 22, 24, 27, 31, 32]:
+        t1, t2, sc = vx.vx_plot_required_bytes(K)
+        if prev:
+            assert sc >= prev
+        prev = sc
+    o = vx.make_opts(partition_log2=13)
+    t1a, _, _ = vx.vx_plot_required_bytes(31, o)
+    t1b, _, _ = vx.vx_plot_required_bytes(31)
+    assert t1a >= 12 * 2 ** 31 and t1b >= 12 * 2 ** 31

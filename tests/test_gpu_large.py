@@ -1,0 +1,137 @@
+"""Full-size plots (K=27 and K=31, the configuration bench.py times), checked
+through properties that hold at any size, computed on the device with torch
+independently of the kernels, plus sampled recomputation by the oracle:
+
+Table 1: strictly increasing in (key64, nonce); every nonce exactly once;
+sampled records' hash bytes equal the oracle's keyed hash.
+Table 2: every entry (a, b) has pos(a) < pos(b) in Table 1, the same logical
+bucket and key64_b - key64_a < D; entries strictly increasing in
+(pos(a), pos(b)); their number equals an independent count of qualifying
+pairs; sampled hash2 equal the oracle's; the count is within the closed-form
+expectation 2^24 (lambda - 1/2).
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as orc  # noqa: E402
+from paper_2606_14007_gb300.inputs import plot_key  # noqa: E402
+
+CHUNK = 1 << 27
+
+
+@pytest.fixture(scope="module")
+def vx():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_14007_gb300 import vaultx
+    return vaultx
+
+
+def fields(t1_rows):
+    b = t1_rows.long()
+    nonce = b[:, 0] | (b[:, 1] << 8) | (b[:, 2] << 16) | (b[:, 3] << 24)
+    hi = (b[:, 4] << 24) | (b[:, 5] << 16) | (b[:, 6] << 8) | b[:, 7]
+    lo = (b[:, 8] << 24) | (b[:, 9] << 16) | (b[:, 10] << 8) | b[:, 11]
+    return nonce, hi, lo
+
+
+def check_plot(vx, K, seed):
+    key = plot_key(seed)
+    N = 1 << K
+    D = 1 << (64 - K)
+    p = vx.Plot(K, key)
+    p.run()
+    n2 = p.sync()
+    t1 = p.t1
+    dev = t1.device
+    counts = torch.zeros(N, dtype=torch.int32, device=dev)
+    pos = torch.empty(N, dtype=torch.int32, device=dev)
+    independent = 0
+    prev = None
+    for s in range(0, N, CHUNK):
+        e = min(N, s + CHUNK)
+        nonce, hi, lo = fields(t1[s:e])
+        counts.index_add_(0, nonce, torch.ones_like(nonce, dtype=torch.int32))
+        pos[nonce] = torch.arange(s, e, dtype=torch.int32, device=dev)
+        # strictly increasing (key64, nonce), including across the chunk seam
+        if prev is not None:
+            nonce = torch.cat([prev[0], nonce]); hi = torch.cat([prev[1], hi]); lo = torch.cat([prev[2], lo])
+        inc = (hi[1:] > hi[:-1]) | ((hi[1:] == hi[:-1]) & ((lo[1:] > lo[:-1]) |
+                                                           ((lo[1:] == lo[:-1]) & (nonce[1:] > nonce[:-1]))))
+        assert bool(inc.all()), "Table 1 not sorted near record %d" % s
+        prev = (nonce[-1:], hi[-1:], lo[-1:])
+        # independent pair count for records of this chunk (needs a look-ahead)
+        ahead = min(N, e + 4096)
+        _, hi2, lo2 = fields(t1[s:ahead])
+        bucket = hi2 >> 8
+        k40 = ((hi2 & 0xFF) << 32) | lo2
+        n_own = e - s
+        idx = torch.arange(n_own, device=dev)
+        alive = torch.ones(n_own, dtype=torch.bool, device=dev)
+        k = 1
+        while bool(alive.any()):
+            j = idx + k
+            ok = j < bucket.shape[0]
+            jj = torch.where(ok, j, torch.zeros_like(j))
+            m = alive & ok & (bucket[jj] == bucket[:n_own]) & ((k40[jj] - k40[:n_own]) < D)
+            independent += int(m.sum())
+            alive = m
+            k += 1
+            assert k < 4096, "look-ahead too short"
+    assert bool((counts == 1).all()), "a nonce is missing or repeated in Table 1"
+    assert n2 == independent, (n2, independent)
+    lam = N / 2 ** 24
+    E = 2 ** 24 * (lam - 0.5)
+    assert abs(n2 - E) < 8 * math.sqrt(8 * N), (n2, E)
+    # Table 2 entries
+    t2 = p.t2
+    last = None
+    for s in range(0, n2, CHUNK):
+        e = min(n2, s + CHUNK)
+        b = t2[s:e].long()
+        a_n = b[:, 0] | (b[:, 1] << 8) | (b[:, 2] << 16) | (b[:, 3] << 24)
+        b_n = b[:, 4] | (b[:, 5] << 8) | (b[:, 6] << 16) | (b[:, 7] << 24)
+        i = pos[a_n].long()
+        j = pos[b_n].long()
+        assert bool((j > i).all())
+        _, hi_i, lo_i = fields(t1[i])
+        _, hi_j, lo_j = fields(t1[j])
+        assert bool(((hi_i >> 8) == (hi_j >> 8)).all()), "pair crosses a bucket"
+        k40i = ((hi_i & 0xFF) << 32) | lo_i
+        k40j = ((hi_j & 0xFF) << 32) | lo_j
+        assert bool(((k40j - k40i) < D).all()), "pair beyond the match distance"
+        if last is not None:
+            i = torch.cat([last[0], i]); j = torch.cat([last[1], j])
+        order = (i[1:] > i[:-1]) | ((i[1:] == i[:-1]) & (j[1:] > j[:-1]))
+        assert bool(order.all()), "Table 2 out of (i, j) order"
+        last = (i[-1:], j[-1:])
+    # sampled oracle recomputation
+    rng = np.random.default_rng(seed)
+    rows = torch.from_numpy(rng.integers(0, N, 3000)).to(dev)
+    t1s = t1[rows].cpu().numpy()
+    for r in t1s:
+        assert r[4:].tobytes() == orc.keyed_hash(key, r[:4].tobytes(), 8)
+    rows = torch.from_numpy(rng.integers(0, n2, 3000)).to(dev)
+    for r in t2[rows].cpu().numpy():
+        assert r[8:].tobytes() == orc.keyed_hash(key, r[:8].tobytes(), 8)
+    # first and last records of Table 1 and Table 2, and the bucket offsets
+    off = p.offsets()
+    assert int(off[0]) == 0 and int(off[-1]) == N
+    b_first = int(fields(t1[:1])[1][0] >> 8)
+    assert int(off[b_first]) == 0 and int(off[b_first + 1]) > 0
+    p.close()
+    del counts, pos
+    torch.cuda.empty_cache()
+
+
+def test_plot_k27_properties(vx):
+    check_plot(vx, 27, 27)
+
+
+def test_plot_k31_properties(vx):
+    check_plot(vx, 31, 31)

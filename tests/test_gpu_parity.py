@@ -1,0 +1,212 @@
+"""GPU path vs the CPU oracle, element by element (bit-exact: all integer).
+
+Every call goes through the C ABI (ctypes binding).  Sizes run from K=1 to
+K=22 (the small configuration) and cover both scatter levels, ragged tiles,
+custom match distances, slot overflow, Table-2 capacity and determinism.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import oracle as orc  # noqa: E402
+from paper_2606_14007_gb300.inputs import plot_key  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def vx():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_14007_gb300 import vaultx
+    assert torch.cuda.is_available()
+    return vaultx
+
+
+def run_plot(vx, K, key, opts=None):
+    p = vx.Plot(K, key, opts)
+    p.run()
+    n2 = p.sync()
+    t1 = p.t1.cpu().numpy()
+    t2 = p.t2.cpu().numpy()
+    off = p.offsets().cpu().numpy()
+    torch.cuda.synchronize()
+    p.close()
+    return t1, t2, n2, off
+
+
+def oracle_plot(K, key, D=None):
+    t1 = orc.table1(K, key)
+    t2 = orc.match(key, t1, orc.default_distance(K) if D is None else D)
+    return t1, t2
+
+
+def test_hash_row_matches_oracle(vx):
+    key = plot_key(3)
+    for nonce0, count in [(0, 5000), (2 ** 32 - 3000, 3000), (123456789, 777), (2 ** 31 - 5, 10)]:
+        out = torch.empty(12 * count, dtype=torch.uint8, device="cuda")
+        vx.vx_hash_nonces(key, nonce0, count, out.data_ptr())
+        got = out.view(count, 12).cpu().numpy()
+        ref = orc.hash_range(key, nonce0, nonce0 + count, threads=4)
+        assert np.array_equal(got, ref), (nonce0, count)
+
+
+def test_pair_hash_row_matches_oracle(vx):
+    key = plot_key(4)
+    rng = np.random.default_rng(5)
+    pairs = rng.integers(0, 2 ** 32, size=(3000, 2), dtype=np.uint64).astype(np.uint32)
+    pairs[0] = [0, 0]
+    pairs[1] = [0xFFFFFFFF, 0xFFFFFFFF]
+    dp = torch.from_numpy(pairs.view(np.int32)).cuda()
+    out = torch.empty(3000 * 16, dtype=torch.uint8, device="cuda")
+    vx.vx_pair_hash(key, dp.data_ptr(), 3000, out.data_ptr())
+    got = out.view(3000, 16).cpu().numpy()
+    assert np.array_equal(got[:, :8].view("<u4"), pairs)
+    for i in range(3000):
+        assert got[i, 8:].tobytes() == orc.keyed_hash(key, got[i, :8].tobytes(), 8), i
+
+
+# (K, seed, opts) -- opts exercise both scatter levels and the sort digit widths.
+CASES = [
+    (1, 0, {}), (2, 1, {}), (3, 2, {}), (5, 3, {}), (8, 4, {}), (11, 5, {}), (12, 6, {}),
+    (13, 7, {}), (14, 8, {}), (16, 9, {}), (18, 10, {}), (20, 11, {}), (22, 0, {}),
+    (16, 12, dict(partition_log2=6, coarse_bits=4)),       # two levels, 1024 partitions
+    (20, 13, dict(partition_log2=8)),                      # two levels (auto), 4096 partitions
+    (18, 14, dict(partition_log2=13)),                     # large partitions, 13-bit digits
+    (12, 15, dict(partition_log2=6, coarse_bits=0)),       # single first-level slot
+    (17, 16, dict(partition_log2=7, coarse_bits=10)),      # 10 + 0 bits
+    (19, 17, dict(partition_log2=9, slack_sigma=40)),      # roomy slots
+]
+
+
+@pytest.mark.parametrize("K,seed,kw", CASES)
+def test_plot_matches_oracle(vx, K, seed, kw):
+    key = plot_key(seed)
+    opts = vx.make_opts(**kw) if kw else None
+    t1, t2, n2, off = run_plot(vx, K, key, opts)
+    r1, r2 = oracle_plot(K, key)
+    assert np.array_equal(t1, r1)
+    assert n2 == r2.shape[0]
+    assert np.array_equal(t2, r2)
+    assert np.array_equal(off.astype(np.uint64), orc.bucket_offsets(r1))
+
+
+@pytest.mark.parametrize("K,seed,D", [(16, 20, 1 << 34), (18, 21, 1 << 37), (14, 22, 1),
+                                      (15, 23, (1 << 64) - 1), (17, 24, 12345678901)])
+def test_custom_match_distance(vx, K, seed, D):
+    key = plot_key(seed)
+    t1, t2, n2, _ = run_plot(vx, K, key, vx.make_opts(match_distance=D))
+    r1, r2 = oracle_plot(K, key, D)
+    assert np.array_equal(t1, r1)
+    assert np.array_equal(t2, r2)
+
+
+def test_dense_buckets_match(vx):
+    # K=22 with D spanning all buckets is the K <= 24 all-pairs regime;
+    # a D of 1/8 bucket mimics the K=27 density on a small plot.
+    key = plot_key(30)
+    D = 1 << 37
+    t1, t2, _, _ = run_plot(vx, 22, key, vx.make_opts(match_distance=D))
+    r1, r2 = oracle_plot(22, key, D)
+    assert np.array_equal(t2, r2)
+
+
+def test_deterministic_repeat(vx):
+    key = plot_key(40)
+    p = vx.Plot(20, key)
+    outs = []
+    for _ in range(3):
+        p.run()
+        p.sync()
+        outs.append((p.t1.cpu().numpy().copy(), p.t2.cpu().numpy().copy()))
+    p.close()
+    for a in outs[1:]:
+        assert np.array_equal(a[0], outs[0][0]) and np.array_equal(a[1], outs[0][1])
+
+
+def test_slot_overflow_is_reported(vx):
+    # Slots of mean + 1 sd (+16) overflow in many partitions: the plot must
+    # report VX_EOVERFLOW, never produce silently short tables or fault.
+    key = plot_key(50)
+    p = vx.Plot(18, key, vx.make_opts(partition_log2=6, slack_sigma=1))
+    p.run()
+    rc = vx.vx_sync(p.handle, check=False)
+    assert rc == vx.VX_EOVERFLOW
+    p.close()
+
+
+def test_table2_capacity_then_rebind(vx):
+    key = plot_key(60)
+    K = 16
+    p = vx.Plot(K, key, vx.make_opts(t2_capacity=16))
+    p.run()
+    assert vx.vx_sync(p.handle, check=False) == vx.VX_ENOMEM
+    _, need, _, rc = vx.vx_table_info(p.handle, vx.VX_TABLE2, check=False)
+    assert rc == vx.VX_ENOMEM
+    r1, r2 = oracle_plot(K, key)
+    assert need == r2.shape[0] > 16
+    # A bigger Table-2 buffer, same Table 1 and scratch: only vx_match reruns.
+    big = torch.empty(16 * need + 256, dtype=torch.uint8, device="cuda")
+    vx.vx_plot_bind(p.handle, p._t1.data_ptr(), big.data_ptr(), p._scratch.data_ptr(), need)
+    vx.vx_match(p.handle)
+    vx.vx_sync(p.handle)
+    got = big[: 16 * need].view(need, 16).cpu().numpy()
+    assert np.array_equal(got, r2)
+    p.close()
+
+
+def test_alloc_failure_injection(vx):
+    h = vx.vx_plot_create(16, plot_key(1))
+    vx.vx_test_fail_next_allocs(1)
+    with pytest.raises(vx.VxError) as ei:
+        vx.vx_plot_alloc(h)
+    assert ei.value.code == vx.VX_ENOMEM
+    vx.vx_plot_alloc(h)      # the next one succeeds
+    vx.vx_table1(h)
+    vx.vx_match(h)
+    vx.vx_sync(h)
+    vx.vx_plot_destroy(h)
+
+
+def test_library_owned_memory_and_copy(vx):
+    K, key = 15, plot_key(70)
+    h = vx.vx_plot_create(K, key)
+    vx.vx_table1(h)
+    vx.vx_match(h)
+    vx.vx_sync(h)
+    _, n2, rb, _ = vx.vx_table_info(h, vx.VX_TABLE2)
+    host = torch.empty(n2 * 16, dtype=torch.uint8).pin_memory()
+    vx.vx_table_copy(h, vx.VX_TABLE2, host.data_ptr(), n2 * 16)
+    torch.cuda.synchronize()
+    r1, r2 = oracle_plot(K, key)
+    assert np.array_equal(host.numpy().reshape(-1, 16), r2)
+    vx.vx_plot_destroy(h)
+
+
+def test_plot_write_file(vx, tmp_path):
+    K, key = 17, plot_key(80)
+    p = vx.Plot(K, key)
+    p.run()
+    p.sync()
+    path = str(tmp_path / "plot.bin")
+    d2h, total = vx.vx_plot_write(p.handle, path)
+    data = np.fromfile(path, dtype=np.uint8).reshape(-1, 16)
+    assert np.array_equal(data, p.t2.cpu().numpy())
+    assert total >= d2h >= 0
+    p.close()
+
+
+def test_profile_trace(vx):
+    p = vx.Plot(20, plot_key(90))
+    vx.vx_plot_profile(p.handle, 2)
+    for _ in range(2):
+        p.run()
+    p.sync()
+    ms, runs = vx.vx_plot_profile_read(p.handle)
+    assert runs == 2
+    assert set(ms) == {"key_setup", "hash_scatter", "scatter2", "scan_counts", "sort",
+                       "scan_pairs", "match"}
+    assert ms["hash_scatter"] > 0 and ms["match"] > 0
+    p.close()
