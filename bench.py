@@ -39,7 +39,8 @@ LANES = 32
 # 4 xors, 4 rotates), minus 14 ops of the last round that do not reach
 # output words 0..1, plus the 2 output xors.
 INT_OPS_PER_COMPRESSION = 53 * 12 - 14 + 2
-KERNELS = ["key_setup", "hash_scatter", "scatter2", "scan_counts", "sort", "scan_pairs", "match"]
+KERNELS = ["key_setup", "hash_staged", "hash_direct", "scatter2", "scan_counts", "sort",
+           "scan_pairs", "match", "sortmatch", "pairhash"]
 
 
 def peaks():
@@ -122,11 +123,15 @@ def source_digest(files) -> str:
     return h.hexdigest()[:16]
 
 
+_H = "paper_2606_14007_gb300/csrc/vx_internal.cuh"
 KERNEL_SOURCES = {
-    "hash_scatter": ["paper_2606_14007_gb300/csrc/k_hash.cu", "paper_2606_14007_gb300/csrc/vx_internal.cuh"],
-    "scatter2": ["paper_2606_14007_gb300/csrc/k_sort.cu", "paper_2606_14007_gb300/csrc/vx_internal.cuh"],
-    "sort": ["paper_2606_14007_gb300/csrc/k_sort.cu", "paper_2606_14007_gb300/csrc/vx_internal.cuh"],
-    "match": ["paper_2606_14007_gb300/csrc/k_match.cu", "paper_2606_14007_gb300/csrc/vx_internal.cuh"],
+    "hash_staged": ["paper_2606_14007_gb300/csrc/k_hash.cu", _H],
+    "hash_direct": ["paper_2606_14007_gb300/csrc/k_hash.cu", _H],
+    "scatter2": ["paper_2606_14007_gb300/csrc/k_sort.cu", _H],
+    "sort": ["paper_2606_14007_gb300/csrc/k_sortmatch.cu", _H],
+    "sortmatch": ["paper_2606_14007_gb300/csrc/k_sortmatch.cu", _H],
+    "pairhash": ["paper_2606_14007_gb300/csrc/k_hash.cu", _H],
+    "match": ["paper_2606_14007_gb300/csrc/k_match.cu", _H],
 }
 
 
@@ -261,8 +266,7 @@ def main():
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        vx.vx_table1(plot.handle, stream)
-        vx.vx_match(plot.handle, stream)
+        vx.vx_plot_run(plot.handle, stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -283,9 +287,23 @@ def main():
     pk_peak = peaks()
     hbm_peak = pk_peak["hbm_gbs"]
     int_peak = int_peak_ops(pk_peak["sm_max_mhz"])
-    algo_bytes = {"scatter2": 24 * N, "sort": 24 * N, "match": 12 * N + 16 * n2}
-    algo_ops = {"hash_scatter": INT_OPS_PER_COMPRESSION * N, "match": INT_OPS_PER_COMPRESSION * n2}
+    # Algorithmic work per launch: a hash kernel does one compression per
+    # nonce and writes 12 B per record; the second scatter level reads and
+    # writes 12 B per record; sort+match reads 12 B and writes 12 B per
+    # record and writes 16 B per pair, and hashes the pairs unless the
+    # separate pair-hash pass (read + write 16 B per pair) does.
+    separate = "pairhash" in vx.vx_plot_kernel_mask(plot.handle)
+    algo_bytes = {"scatter2": 24 * N, "sort": 24 * N, "match": 12 * N + 16 * n2,
+                  "sortmatch": 24 * N + 16 * n2, "hash_direct": 12 * N, "hash_staged": 12 * N,
+                  "pairhash": 32 * n2}
+    algo_ops = {"hash_staged": INT_OPS_PER_COMPRESSION * N, "hash_direct": INT_OPS_PER_COMPRESSION * N,
+                "match": INT_OPS_PER_COMPRESSION * n2, "pairhash": INT_OPS_PER_COMPRESSION * n2}
+    if not separate:
+        algo_ops["sortmatch"] = INT_OPS_PER_COMPRESSION * n2
+    launched = vx.vx_plot_kernel_mask(plot.handle)
     for k in KERNELS:
+        if k not in launched:
+            continue
         ms = per_kernel[k] / max(1, runs)
         e = {"ms_per_launch": ms}
         if k in algo_ops and ms > 0:
@@ -295,7 +313,7 @@ def main():
             e["gbs"] = algo_bytes[k] / (ms / 1e3) / 1e9
             e["hbm_frac"] = e["gbs"] / hbm_peak
         pk[k] = e
-    dom = max(KERNELS, key=lambda k: pk[k]["ms_per_launch"])
+    dom = max(pk, key=lambda k: pk[k]["ms_per_launch"])
     if dom in algo_ops:
         ach = pk[dom]["int_tops"] * 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach / 1e12, "peak": int_peak / 1e12,
@@ -325,8 +343,7 @@ def main():
         for i in range(args.e2e_steps):
             h = vx.vx_plot_create(K, plot_key(K + 1000 * rank + 1 + i))
             vx.vx_plot_bind(h, plot._t1.data_ptr(), plot._t2.data_ptr(), plot._scratch.data_ptr(), 0)
-            vx.vx_table1(h, stream)
-            vx.vx_match(h, stream)
+            vx.vx_plot_run(h, stream)
             vx.vx_sync(h)
             _, m, _, _ = vx.vx_table_info(h, vx.VX_TABLE2)
             off, k = 0, 0
@@ -345,14 +362,14 @@ def main():
         e2e = {"value": N * args.e2e_steps * world / dt, "unit": UNIT,
                "h2d_bytes_per_step": desc_bytes, "d2h_bytes_per_step": t2_bytes + 12,
                "steps": args.e2e_steps,
-               "note": "vx_plot_create from a host key, vx_table1, vx_match, vx_sync, then Table 2 "
+               "note": "vx_plot_create from a host key, vx_plot_run, vx_sync, then Table 2 "
                        "copied to pinned host memory through a 2 x 1 GiB ring"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
 
-    launches_per_step = 7 if plot_two_level(vx, K) else 6
+    launches_per_step = len(launched)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -376,13 +393,6 @@ def main():
     if world > 1:
         dist.destroy_process_group()
     return 0
-
-
-def plot_two_level(vx, K):
-    """True when the plan of K uses the second scatter level (7 kernels)."""
-    # The planner keeps one level up to 10 partition bits (K <= 22 at the
-    # default 4096-record partitions).
-    return K - 12 > 10
 
 
 if __name__ == "__main__":

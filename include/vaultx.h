@@ -57,6 +57,9 @@ enum {
 /* Table selectors. */
 enum { VX_TABLE1 = 1, VX_TABLE2 = 2 };
 
+/* vx_opts.test_flags bits. */
+enum { VX_TEST_WITHHOLD_PREFIX = 1 };
+
 /* Plot states reported by the server. */
 enum { VX_QUEUED = 0, VX_RUNNING = 1, VX_DONE = 2, VX_FAILED = 3 };
 
@@ -64,10 +67,15 @@ enum { VX_QUEUED = 0, VX_RUNNING = 1, VX_DONE = 2, VX_FAILED = 3 };
  * always set .size = sizeof(vx_opts) (vx_opts_default does). */
 typedef struct vx_opts {
     uint32_t size;              /* sizeof(vx_opts)                                   */
-    uint32_t reserved0;
+    uint32_t test_flags;        /* fault injection for tests, 0 in normal use:
+                                   VX_TEST_WITHHOLD_PREFIX makes partition 0 of the
+                                   fused sort + match never publish its Table-2
+                                   prefix, so every later partition's bounded wait
+                                   runs out (short limit) and vx_sync returns
+                                   VX_ETIMEDOUT; the paper has no counterpart       */
     uint64_t match_distance;    /* D of the match predicate; 0 = 2^(64-K)            */
     int32_t partition_log2;     /* log2 of the mean records per physical partition
-                                   (6..13); 0 = default (12).  Partitions are runs
+                                   (6..13); 0 = default (11).  Partitions are runs
                                    of whole logical buckets; at most 2^24 of them.  */
     int32_t coarse_bits;        /* bits of the first scatter level (0..10);
                                    -1 = automatic                                     */
@@ -77,8 +85,16 @@ typedef struct vx_opts {
                                    multiple of 32); 0 = default                      */
     uint32_t nonces_per_thread; /* nonces each hash thread handles (2..64, even);
                                    0 = default                                        */
-    uint32_t reserved1;
+    uint32_t scatter_mode;      /* bucketing of hashed records: 0 = automatic
+                                   (staged), 1 = staged (shared-memory histogram per CTA, one
+                                   claim per (CTA, bin), two levels), 2 = direct
+                                   (one slot claim per record into the final
+                                   partition)                                          */
     uint64_t t2_capacity;       /* Table-2 capacity in records; 0 = default bound    */
+    uint32_t fuse_pair_hash;    /* vx_plot_run: 1 = hash the pairs inside the sort +
+                                   match kernel; 0 = (default) the sort writes {a, b}
+                                   records and a streaming pass hashes them         */
+    uint32_t reserved[7];       /* must be zero                                      */
 } vx_opts;
 
 typedef struct vx_plot vx_plot;
@@ -97,11 +113,12 @@ const char *vx_last_error(const vx_plot *plot);
 int vx_version(void);
 
 /* Device memory one plot needs (Sec. I-A: Table 1 stays resident in VRAM).
- *   t1_bytes:      Table-1 buffer (>= 12 * 2^K; the first scatter level also
- *                  uses it as its staging area, so it may be a little larger)
- *   t2_bytes:      Table-2 buffer (>= 16 * Table-2 capacity; the second
- *                  scatter level stages in it before vx_match runs)
- *   scratch_bytes: counters, offsets and the plot descriptor
+ *   t1_bytes:      Table-1 buffer (>= 12 * 2^K; a staged two-level scatter
+ *                  also uses it for its first level, so it may be larger)
+ *   t2_bytes:      Table-2 buffer (16 * Table-2 capacity, + 256)
+ *   scratch_bytes: counters, offsets, the plot descriptor, and the partition
+ *                  slots the hashed records are bucketed into (about
+ *                  12 * 2^K * 1.3 bytes)
  * Any output pointer may be NULL.  1 <= K <= 32.  No allocation. */
 int vx_plot_required_bytes(int K, const vx_opts *opts, uint64_t *t1_bytes,
                            uint64_t *t2_bytes, uint64_t *scratch_bytes);
@@ -131,6 +148,14 @@ int vx_table1(vx_plot *plot, void *stream);
  * capacity nothing is written and vx_sync returns VX_ENOMEM; the needed
  * count is then in vx_table_info(VX_TABLE2).nrec.  Asynchronous. */
 int vx_match(vx_plot *plot, void *stream);
+
+/* Table 1 and Table 2 in one pass (Sec. III-A pipeline): key setup, hash +
+ * bucketing scatter, then the fused partition sort + match kernel, which
+ * sorts each partition in shared memory, writes it to Table 1, and hashes
+ * its pairs straight into Table 2 at the offset a decoupled look-back over
+ * the earlier partitions gives.  Same tables as vx_table1 + vx_match.
+ * Allocates if nothing is bound.  Asynchronous. */
+int vx_plot_run(vx_plot *plot, void *stream);
 
 /* Waits for the plot's last stream, reads its device status word and the
  * Table-2 count, and maps the status to VX_OK / VX_EOVERFLOW / VX_ENOMEM /
@@ -170,18 +195,24 @@ void vx_plot_destroy(vx_plot *plot);
 
 /* ------------------------------------------------------------ tracing */
 
-/* Records CUDA events around every kernel of this plot's next `runs`
- * vx_table1 + vx_match pairs (single-plot path; the paper's per-stage
- * timing of Sec. IV-C at kernel granularity).  runs = 0 turns tracing off
+/* Records CUDA events around every kernel of this plot's next `runs` runs
+ * (a run is vx_plot_run, or vx_table1 followed by vx_match; single-plot
+ * path; the paper's per-stage timing of Sec. IV-C at kernel granularity).  runs = 0 turns tracing off
  * and frees the events.  Adds one event record per kernel, no sync. */
 int vx_plot_profile(vx_plot *plot, int runs);
 
 /* Sums the traced runs: ms[k] = total milliseconds of kernel k, k <
- * *nkernels (cap must be >= 7); *nruns = runs recorded.  Waits for them. */
+ * *nkernels (cap must be >= 9); *nruns = runs recorded.  Waits for them. */
 int vx_plot_profile_read(vx_plot *plot, double *ms, int cap, int *nkernels, int *nruns);
 
-/* Name of traced kernel k ("key_setup", "hash_scatter", "scatter2",
- * "scan_counts", "sort", "scan_pairs", "match"), or "" if out of range. */
+/* Which kernel slots (bit k = kernel k of vx_kernel_name) one run of this
+ * plot launches: split != 0 for vx_table1 + vx_match, else vx_plot_run.
+ * Host only. */
+int vx_plot_kernel_mask(const vx_plot *plot, int split, uint32_t *mask);
+
+/* Name of traced kernel k ("key_setup", "hash_staged", "hash_direct",
+ * "scatter2", "scan_counts", "sort", "scan_pairs", "match", "sortmatch"),
+ * or "" if out of range.  Kernels a run does not use time as zero. */
 const char *vx_kernel_name(int k);
 
 /* ------------------------------------------------ stand-alone stages */

@@ -28,13 +28,18 @@ __global__ void k_key_setup(Desc *descs)
         b3_key_setup(d.key, 8u, pre);
         for (int i = 0; i < 16; ++i) d.pre2[i] = pre[i];
         *d.status = 0u;
+        *d.ticket = 0u;
+        *d.ticket_s = 0u;
     }
     const uint64_t n1 = d.p2 > 0 ? (1ull << d.p1) : 0ull;
     const uint64_t n2 = 1ull << d.p;
+    const uint64_t nchunks = (n2 + kScanChunk - 1) / kScanChunk;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
         d.cnt2[i] = 0u;
+        d.lb[i] = 0ull;
         if (i < n1) d.cnt1[i] = 0u;
+        if (i < nchunks) d.lbs[i] = 0ull;
     }
 }
 
@@ -189,11 +194,124 @@ static cudaError_t launch_hs(const Desc *descs, int nplots, const uint32_t *tile
 cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *tile_start,
                                 uint32_t total_tiles, HashCfg cfg, cudaStream_t s)
 {
+    if (total_tiles == 0) return cudaSuccess;
     if (cfg.agg)
         return launch_hs<kHashThreads, kHashNoncesPerThread, true>(descs, nplots, tile_start,
                                                                    total_tiles, s);
     return launch_hs<kHashThreads, kHashNoncesPerThread, false>(descs, nplots, tile_start,
                                                                 total_tiles, s);
+}
+
+// ------------------------------------------------- hash + direct scatter
+// The other bucketing strategy (the paper's, Sec. III-B: an atomicAdd slot
+// claim per nonce), here straight into the final partitions: every thread
+// hashes NPT nonces, then claims one slot per record in its partition with
+// a global atomic and stores key64 and nonce there.  No shared memory and
+// no second scatter pass; the claims and scattered stores run on the LSU
+// and L2 while the ALU pipe -- the kernel's bound -- keeps hashing.
+template <int NT, int NPT>
+__global__ void __launch_bounds__(NT) k_hash_direct(const Desc *__restrict__ descs, int nplots,
+                                                    const uint32_t *__restrict__ tile_start)
+{
+    const int plot = find_plot(tile_start, nplots, blockIdx.x);
+    const Desc &d = descs[plot];
+    const uint64_t N = d.N;
+    const uint64_t base = (uint64_t)(blockIdx.x - tile_start[plot]) * (NT * NPT);
+    const int bits = d.p;
+    const uint32_t cap = d.cap2;
+    uint32_t pre[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) pre[i] = d.pre1[i];
+    uint64_t key[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        uint32_t h0, h1;
+        b3_finish<false>(pre, (uint32_t)(base + (uint64_t)j * NT + threadIdx.x), 0u, h0, h1);
+        key[j] = key64_of(h0, h1);
+    }
+    uint32_t slot[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
+        const uint32_t bin = bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u;
+        slot[j] = nonce < N ? atomicAdd(&d.cnt2[bin], 1u) : 0xffffffffu;
+    }
+    bool overflow = false;
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+        const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
+        if (nonce >= N) continue;
+        const uint32_t bin = bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u;
+        if (slot[j] < cap) {
+            const uint64_t at = (uint64_t)bin * cap + slot[j];
+            d.b_keys[at] = key[j];
+            d.b_nonces[at] = (uint32_t)nonce;
+        } else {
+            overflow = true;
+        }
+    }
+    if (overflow) atomicOr(d.status, kStSlot2Overflow);
+}
+
+cudaError_t launch_hash_direct(const Desc *descs, int nplots, const uint32_t *tile_start,
+                               uint32_t total_tiles, cudaStream_t s)
+{
+    if (total_tiles == 0) return cudaSuccess;
+    k_hash_direct<kHashThreads, kHashNoncesPerThread><<<total_tiles, kHashThreads, 0, s>>>(
+        descs, nplots, tile_start);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------ Table-2 pair hashing
+// Fills hash2 of the Table-2 records {a, b, 0, 0} the sort wrote at their
+// final offsets: a streaming, barrier-free pass (one compression per
+// record, all lanes busy) over [0, total) of each plot, where total is the
+// count the sort's look-back published.  Skips plots whose Table 2 is
+// invalid (capacity exceeded or a wait timed out).
+constexpr int kT2HashThreads = 256;
+constexpr int kT2HashPer = 8;
+
+__global__ void __launch_bounds__(kT2HashThreads) k_t2_hash(const Desc *__restrict__ descs,
+                                                            int nplots,
+                                                            const uint32_t *__restrict__ tile_start)
+{
+    constexpr int NT = kT2HashThreads, PER = kT2HashPer;
+    const int plot = find_plot(tile_start, nplots, blockIdx.x);
+    const Desc &d = descs[plot];
+    if (*d.status & (kStT2Capacity | kStTimeout | kStBadTicket)) return;
+    const uint64_t total = d.t2off[1ull << d.p];
+    const uint64_t base = (uint64_t)(blockIdx.x - tile_start[plot]) * (NT * PER);
+    if (base >= total) return;
+    uint32_t g[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) g[i] = d.pre2[i];
+    uint4 *__restrict__ t2 = reinterpret_cast<uint4 *>(d.t2);
+    uint2 ab[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const uint64_t q = base + (uint64_t)j * NT + threadIdx.x;
+        if (q < total) {
+            const uint4 v = t2[q];
+            ab[j] = make_uint2(v.x, v.y);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const uint64_t q = base + (uint64_t)j * NT + threadIdx.x;
+        if (q < total) {
+            uint32_t h0, h1;
+            b3_finish<true>(g, ab[j].x, ab[j].y, h0, h1);
+            t2[q] = make_uint4(ab[j].x, ab[j].y, h0, h1);
+        }
+    }
+}
+
+cudaError_t launch_t2_hash(const Desc *descs, int nplots, const uint32_t *tile_start,
+                           uint32_t total_tiles, cudaStream_t s)
+{
+    if (total_tiles == 0) return cudaSuccess;
+    k_t2_hash<<<total_tiles, kT2HashThreads, 0, s>>>(descs, nplots, tile_start);
+    return cudaGetLastError();
 }
 
 // --------------------------------------------------- stand-alone hashing

@@ -33,12 +33,14 @@ using vx::LaunchSet;
 
 namespace vx {
 static_assert(kPlanHashTile == (uint64_t)kHashTile, "planner and hash kernel tiles differ");
+static_assert(kPlanScanChunk == (uint64_t)kScanChunk, "planner and scan kernel chunks differ");
+static_assert(kPlanT2HashTile == kT2HashTile, "planner and pair-hash kernel tiles differ");
 static_assert(sizeof(Desc) + 64 <= kStageTilesOffset, "descriptor overlaps staged tiles");
 inline int make_plan(int K, const vx_opts *o, Plan *pl, std::string *why)
 {
     int rc = make_plan_sized(K, o, pl, why, sizeof(Desc));
     if (rc != VX_OK) return rc;
-    if (sort_smem_bytes(pl->cap2, pl->dbits) > kMaxSmemPerCta ||
+    if (sortmatch_smem_bytes(pl->cap2, pl->dbits) > kMaxSmemPerCta ||
         match_smem_bytes(pl->cap2) > kMaxSmemPerCta) {
         *why = "partition slot too large for shared memory";
         return VX_EINVAL;
@@ -122,22 +124,36 @@ void fill_desc(const vx_plot *p, Desc *d)
     d->cap1 = pl.cap1;
     d->cap2 = pl.cap2;
     d->chunks1 = pl.chunks1;
+    d->spin_limit = pl.spin_limit;
+    d->test_flags = pl.test_flags;
     if (pl.p2 > 0) {
         d->a_keys = reinterpret_cast<uint64_t *>(p->d_t1);
         d->a_nonces = reinterpret_cast<uint32_t *>(p->d_t1 + pl.regionA_keys);
     }
-    d->b_keys = reinterpret_cast<uint64_t *>(p->d_t2);
-    d->b_nonces = reinterpret_cast<uint32_t *>(p->d_t2 + pl.regionB_keys);
     uint8_t *s = p->d_scratch;
+    d->b_keys = reinterpret_cast<uint64_t *>(s + pl.o_regionB);
+    d->b_nonces = reinterpret_cast<uint32_t *>(s + pl.o_regionB + pl.regionB_keys);
     d->status = reinterpret_cast<uint32_t *>(s + pl.o_status);
     d->cnt1 = reinterpret_cast<uint32_t *>(s + pl.o_cnt1);
     d->cnt2 = reinterpret_cast<uint32_t *>(s + pl.o_cnt2);
     d->t1off = reinterpret_cast<uint64_t *>(s + pl.o_t1off);
     d->pairs = reinterpret_cast<uint64_t *>(s + pl.o_pairs);
     d->t2off = reinterpret_cast<uint64_t *>(s + pl.o_t2off);
+    d->lb = reinterpret_cast<uint64_t *>(s + pl.o_lb);
+    d->ticket = reinterpret_cast<uint32_t *>(s + pl.o_ticket);
+    d->lbs = reinterpret_cast<uint64_t *>(s + pl.o_lbs);
+    d->ticket_s = reinterpret_cast<uint32_t *>(s + pl.o_ticket_s);
     d->t1 = p->d_t1;
     d->t2 = p->d_t2;
     key_words(p->key, d->key);
+}
+
+// Pair-hash CTAs of a plot: enough for its bound Table-2 capacity (a caller
+// may bind a larger buffer than planned); 0 when the sort hashes the pairs.
+uint32_t pairhash_tiles(const vx_plot *p)
+{
+    if (p->plan.fuse_pair_hash) return 0u;
+    return (uint32_t)((p->t2cap + vx::kPlanT2HashTile - 1) / vx::kPlanT2HashTile);
 }
 
 Desc *dev_desc(vx_plot *p) { return reinterpret_cast<Desc *>(p->d_scratch + p->plan.o_desc); }
@@ -157,13 +173,16 @@ int upload_desc(vx_plot *p, cudaStream_t s)
     fill_desc(p, p->h_stage);
     uint32_t *t = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(p->h_stage) +
                                                vx::kStageTilesOffset);
-    t[0] = 0; t[1] = p->plan.tiles_hash;   // hash + first scatter
-    t[2] = 0; t[3] = p->plan.tiles_s2;     // second scatter
-    t[4] = 0; t[5] = p->plan.tiles_part;   // sort and match
+    t[0] = 0; t[1] = p->plan.tiles_staged;   // hash + staged first scatter
+    t[2] = 0; t[3] = p->plan.tiles_direct;   // hash + direct scatter
+    t[4] = 0; t[5] = p->plan.tiles_s2;       // second scatter
+    t[6] = 0; t[7] = p->plan.tiles_part;     // sort / match / sort+match
+    t[8] = 0; t[9] = p->plan.tiles_scan;     // Table-1 offset scan
+    t[10] = 0; t[11] = pairhash_tiles(p);    // pair hash over the bound Table-2 capacity
     // Only the host-filled part: pre1/pre2 are derived on the device by the
     // key-setup kernel and must survive a re-upload after vx_plot_bind.
     VX_TRY(p, cudaMemcpyAsync(dev_desc(p), p->h_stage, offsetof(Desc, pre1), cudaMemcpyHostToDevice, s));
-    VX_TRY(p, cudaMemcpyAsync(dev_tiles(p), t, 6 * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    VX_TRY(p, cudaMemcpyAsync(dev_tiles(p), t, 12 * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
     VX_TRY(p, cudaEventRecord(p->ev_stage, s));
     p->ev_pending = true;
     p->desc_dirty = false;
@@ -179,6 +198,7 @@ int ensure_memory(vx_plot *p)
 int map_status(uint32_t st)
 {
     if (st & vx::kStTimeout) return VX_ETIMEDOUT;
+    if (st & vx::kStBadTicket) return VX_ECUDA;
     if (st & (vx::kStSlot1Overflow | vx::kStSlot2Overflow | vx::kStCountMismatch |
               vx::kStPartitionTooBig))
         return VX_EOVERFLOW;
@@ -195,37 +215,79 @@ std::string status_text(uint32_t st)
     if (st & vx::kStPartitionTooBig) s += "partition larger than shared memory; ";
     if (st & vx::kStT2Capacity) s += "Table 2 exceeds its capacity; ";
     if (st & vx::kStTimeout) s += "device wait timed out; ";
+    if (st & vx::kStBadTicket) s += "work ticket out of range (state not reset); ";
     return s;
 }
 
-// Kernel sequences.  ev (nullable) receives an event before the first
-// kernel and after each one (tracing); skipped kernels still record.
-cudaError_t launch_table1(const LaunchSet &L, cudaStream_t s, cudaEvent_t *ev = nullptr)
+// Kernel sequences.  ev (nullable, vx::kProfEvents entries) receives an
+// event before the first kernel and after each traced kernel slot; slots a
+// path skips record back to back (zero time).
+inline void rec(cudaEvent_t *ev, int i, cudaStream_t s)
+{
+    if (ev) cudaEventRecord(ev[i], s);
+}
+
+// Traced kernel slots: 0 key_setup, 1 hash_staged, 2 hash_direct,
+// 3 scatter2, 4 scan_counts, 5 sort, 6 scan_pairs, 7 match, 8 sortmatch,
+// 9 pairhash; event k+1 follows kernel k.
+//
+// Key setup, hashing + bucketing, Table-1 offsets (slots 0..4).
+cudaError_t launch_front(const LaunchSet &L, cudaStream_t s, cudaEvent_t *ev)
 {
     cudaError_t e;
-    if (ev) cudaEventRecord(ev[0], s);
+    rec(ev, 0, s);
     if ((e = vx::launch_key_setup(L.descs, L.n, s)) != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[1], s);
+    rec(ev, 1, s);
     if ((e = vx::launch_hash_scatter(L.descs, L.n, L.t_hash, L.n_hash, vx::HashCfg{L.agg}, s)) !=
         cudaSuccess)
         return e;
-    if (ev) cudaEventRecord(ev[2], s);
+    rec(ev, 2, s);
+    if ((e = vx::launch_hash_direct(L.descs, L.n, L.t_direct, L.n_direct, s)) != cudaSuccess) return e;
+    rec(ev, 3, s);
     if (L.n_s2 && (e = vx::launch_scatter2(L.descs, L.n, L.t_s2, L.n_s2, s)) != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[3], s);
-    if ((e = vx::launch_scan_counts(L.descs, L.n, s)) != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[4], s);
+    rec(ev, 4, s);
+    if ((e = vx::launch_scan_counts(L.descs, L.n, L.t_scan, L.n_scan, s)) != cudaSuccess) return e;
+    rec(ev, 5, s);
+    return cudaSuccess;
+}
+
+// Split path, Table 1: front + partition sort (slot 5).
+cudaError_t launch_table1(const LaunchSet &L, cudaStream_t s, cudaEvent_t *ev = nullptr)
+{
+    cudaError_t e = launch_front(L, s, ev);
+    if (e != cudaSuccess) return e;
     e = vx::launch_sort(L.descs, L.n, L.t_part, L.n_part, s, L.max_cap2, L.max_dbits);
-    if (ev) cudaEventRecord(ev[5], s);
+    rec(ev, 6, s);
     return e;
 }
 
+// Split path, Table 2: pair-offset scan + match (slots 6, 7).
 cudaError_t launch_match_seq(const LaunchSet &L, cudaStream_t s, cudaEvent_t *ev = nullptr)
 {
     cudaError_t e;
     if ((e = vx::launch_scan_pairs(L.descs, L.n, s)) != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[6], s);
+    rec(ev, 7, s);
     e = vx::launch_match(L.descs, L.n, L.t_part, L.n_part, s, L.max_cap2);
-    if (ev) cudaEventRecord(ev[7], s);
+    rec(ev, 8, s);
+    rec(ev, 9, s);
+    rec(ev, 10, s);
+    return e;
+}
+
+// One-pass path: front + sort+match (slot 8) + streaming pair hash (slot 9).
+cudaError_t launch_fused(const LaunchSet &L, cudaStream_t s, cudaEvent_t *ev = nullptr)
+{
+    cudaError_t e = launch_front(L, s, ev);
+    if (e != cudaSuccess) return e;
+    rec(ev, 6, s);
+    rec(ev, 7, s);
+    rec(ev, 8, s);
+    e = vx::launch_sortmatch(L.descs, L.n, L.t_part, L.n_part, s, L.max_cap2, L.max_dbits,
+                             L.fuse_pair_hash);
+    if (e != cudaSuccess) return e;
+    rec(ev, 9, s);
+    if (!L.fuse_pair_hash) e = vx::launch_t2_hash(L.descs, L.n, L.t_t2h, L.n_t2h, s);
+    rec(ev, 10, s);
     return e;
 }
 
@@ -236,9 +298,16 @@ LaunchSet single_set(vx_plot *p)
     L.n = 1;
     uint32_t *t = dev_tiles(p);
     L.t_hash = t;
-    L.t_s2 = t + 2;
-    L.t_part = t + 4;
-    L.n_hash = p->plan.tiles_hash;
+    L.t_direct = t + 2;
+    L.t_s2 = t + 4;
+    L.t_part = t + 6;
+    L.t_scan = t + 8;
+    L.t_t2h = t + 10;
+    L.n_hash = p->plan.tiles_staged;
+    L.n_direct = p->plan.tiles_direct;
+    L.n_scan = p->plan.tiles_scan;
+    L.fuse_pair_hash = p->plan.fuse_pair_hash;
+    L.n_t2h = pairhash_tiles(p);
     L.n_s2 = p->plan.tiles_s2;
     L.n_part = p->plan.tiles_part;
     L.agg = p->plan.agg;
@@ -407,6 +476,28 @@ int vx_match(vx_plot *p, void *stream)
     return VX_OK;
 }
 
+int vx_plot_run(vx_plot *p, void *stream)
+{
+    if (!p) return VX_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_memory(p);
+    if (rc) return rc;
+    if ((rc = upload_desc(p, s))) return rc;
+    cudaEvent_t *ev = nullptr;
+    p->prof_cur = -1;
+    if (p->prof_slots > 0 && p->prof_runs < p->prof_slots) {
+        ev = p->prof_ev + (size_t)p->prof_next++ * vx::kProfEvents;
+        p->prof_runs += 1;
+    }
+    cudaError_t e = launch_fused(single_set(p), s, ev);
+    if (e != cudaSuccess) return cuda_fail(p, "plot launch", e);
+    p->stage = 2;
+    p->t2_known = false;
+    p->last = s;
+    p->have_last = true;
+    return VX_OK;
+}
+
 int vx_sync(vx_plot *p)
 {
     if (!p) return VX_EINVAL;
@@ -489,9 +580,24 @@ void vx_plot_destroy(vx_plot *p)
 // -------------------------------------------------------------- tracing
 const char *vx_kernel_name(int k)
 {
-    static const char *names[vx::kProfKernels] = {"key_setup", "hash_scatter", "scatter2",
-                                                  "scan_counts", "sort", "scan_pairs", "match"};
+    static const char *names[vx::kProfKernels] = {"key_setup",  "hash_staged", "hash_direct",
+                                                  "scatter2",   "scan_counts", "sort",
+                                                  "scan_pairs", "match",       "sortmatch",
+                                                  "pairhash"};
     return (k >= 0 && k < vx::kProfKernels) ? names[k] : "";
+}
+
+int vx_plot_kernel_mask(const vx_plot *p, int split, uint32_t *mask)
+{
+    if (!p || !mask) return VX_EINVAL;
+    const vx::Plan &pl = p->plan;
+    uint32_t m = 1u << 0 | 1u << 4;                         // key_setup, scan_counts
+    m |= pl.mode == vx::kScatterStaged ? 1u << 1 : 1u << 2;  // hash_staged / hash_direct
+    if (pl.mode == vx::kScatterStaged && pl.p2 > 0) m |= 1u << 3;  // scatter2
+    if (split) m |= 1u << 5 | 1u << 6 | 1u << 7;           // sort, scan_pairs, match
+    else m |= 1u << 8 | (pl.fuse_pair_hash ? 0u : 1u << 9);  // sortmatch, pairhash
+    *mask = m;
+    return VX_OK;
 }
 
 int vx_plot_profile(vx_plot *p, int runs)
@@ -620,7 +726,7 @@ namespace vx {
 size_t batch_ws_bytes(int n)
 {
     const size_t o_tiles = ((size_t)n * sizeof(Desc) + 255) & ~(size_t)255;
-    return o_tiles + 3 * (size_t)(n + 1) * 4;
+    return o_tiles + 6 * (size_t)(n + 1) * 4;
 }
 
 int batch_prepare(vx_plot *const *plots, int n, uint8_t *h_ws, uint8_t *d_ws, LaunchSet *L)
@@ -628,45 +734,59 @@ int batch_prepare(vx_plot *const *plots, int n, uint8_t *h_ws, uint8_t *d_ws, La
     const size_t o_tiles = ((size_t)n * sizeof(Desc) + 255) & ~(size_t)255;
     Desc *hd = reinterpret_cast<Desc *>(h_ws);
     uint32_t *th = reinterpret_cast<uint32_t *>(h_ws + o_tiles);
-    uint32_t *ts = th + (n + 1), *tp = ts + (n + 1);
-    th[0] = ts[0] = tp[0] = 0;
+    uint32_t *tdir = th + (n + 1), *ts = tdir + (n + 1), *tp = ts + (n + 1);
+    uint32_t *tsc = tp + (n + 1), *tt2 = tsc + (n + 1);
+    th[0] = tdir[0] = ts[0] = tp[0] = tsc[0] = tt2[0] = 0;
+    bool fuse = true;
+    for (int i = 0; i < n; ++i)
+        if (!plots[i] || !plots[i]->plan.fuse_pair_hash) fuse = false;
     L->max_cap2 = 0;
     L->max_dbits = 1;
     int min_bits = 64;
-    uint64_t sh = 0, ss = 0, sp = 0;
+    uint64_t sh = 0, sd = 0, ss = 0, sp = 0, ssc = 0, st2 = 0;
     for (int i = 0; i < n; ++i) {
         if (!plots[i] || !plots[i]->d_t1) return VX_EINVAL;
         const Plan &pl = plots[i]->plan;
         fill_desc(plots[i], hd + i);
-        sh += pl.tiles_hash;
+        sh += pl.tiles_staged;
+        sd += pl.tiles_direct;
         ss += pl.tiles_s2;
         sp += pl.tiles_part;
-        if (sh > 0x7FFFFFFFull || ss > 0x7FFFFFFFull || sp > 0x7FFFFFFFull) return VX_EINVAL;
+        ssc += pl.tiles_scan;
+        st2 += fuse ? 0u : pairhash_tiles(plots[i]);
+        if (sh > 0x7FFFFFFFull || sd > 0x7FFFFFFFull || ss > 0x7FFFFFFFull || sp > 0x7FFFFFFFull ||
+            ssc > 0x7FFFFFFFull || st2 > 0x7FFFFFFFull)
+            return VX_EINVAL;
+        tsc[i + 1] = (uint32_t)ssc;
+        tt2[i + 1] = (uint32_t)st2;
         th[i + 1] = (uint32_t)sh;
+        tdir[i + 1] = (uint32_t)sd;
         ts[i + 1] = (uint32_t)ss;
         tp[i + 1] = (uint32_t)sp;
         L->max_cap2 = std::max(L->max_cap2, pl.cap2);
         L->max_dbits = std::max(L->max_dbits, pl.dbits);
-        min_bits = std::min(min_bits, pl.p2 > 0 ? pl.p1 : pl.p);
+        if (pl.mode == kScatterStaged) min_bits = std::min(min_bits, pl.p2 > 0 ? pl.p1 : pl.p);
     }
     L->agg = min_bits <= kAggMaxBits;
     L->descs = reinterpret_cast<Desc *>(d_ws);
     L->n = n;
     L->t_hash = reinterpret_cast<uint32_t *>(d_ws + o_tiles);
-    L->t_s2 = L->t_hash + (n + 1);
+    L->t_direct = L->t_hash + (n + 1);
+    L->t_s2 = L->t_direct + (n + 1);
     L->t_part = L->t_s2 + (n + 1);
+    L->t_scan = L->t_part + (n + 1);
+    L->t_t2h = L->t_scan + (n + 1);
     L->n_hash = th[n];
+    L->n_direct = tdir[n];
+    L->n_scan = tsc[n];
+    L->n_t2h = tt2[n];
+    L->fuse_pair_hash = fuse;
     L->n_s2 = ts[n];
     L->n_part = tp[n];
     return VX_OK;
 }
 
-cudaError_t launch_plot_seq(const LaunchSet &L, cudaStream_t s)
-{
-    cudaError_t e = launch_table1(L, s);
-    if (e == cudaSuccess) e = launch_match_seq(L, s);
-    return e;
-}
+cudaError_t launch_plot_seq(const LaunchSet &L, cudaStream_t s) { return launch_fused(L, s); }
 
 void mark_issued(vx_plot *const *plots, int n, cudaStream_t s)
 {

@@ -40,8 +40,8 @@ struct vx_plot {
 };
 
 namespace vx {
-// Kernels of one single-plot run, in launch order (tracing names).
-constexpr int kProfKernels = 7;
+// Kernels a single-plot run may launch, in launch order (tracing names).
+constexpr int kProfKernels = 10;
 constexpr int kProfEvents = kProfKernels + 1;
 }  // namespace vx
 
@@ -52,20 +52,22 @@ namespace vx {
 struct LaunchSet {
     Desc *descs;
     int n;
-    const uint32_t *t_hash, *t_s2, *t_part;
-    uint32_t n_hash, n_s2, n_part;
+    const uint32_t *t_hash, *t_direct, *t_s2, *t_part, *t_scan, *t_t2h;  // tile prefixes (device)
+    uint32_t n_hash, n_direct, n_s2, n_part, n_scan, n_t2h;            // n_hash: staged hash CTAs
+    bool fuse_pair_hash;
     bool agg;
     uint32_t max_cap2;
     int max_dbits;
 };
 
 
-// Batch workspace: descs[n] | tile prefixes hash[n+1] | s2[n+1] | part[n+1].
+// Batch workspace: descs[n] | tile prefixes staged[n+1] | direct[n+1] |
+// s2[n+1] | part[n+1] | scan[n+1] | t2h[n+1].
 size_t batch_ws_bytes(int n);
 // Fills the host workspace for plots[0..n) (each bound) and the launch set
 // that reads it from d_ws.  Returns VX_OK or VX_EINVAL.
 int batch_prepare(vx_plot *const *plots, int n, uint8_t *h_ws, uint8_t *d_ws, LaunchSet *L);
-// Whole-plot kernel sequence (Table 1 then Table 2) of a launch set.
+// Whole-plot kernel sequence (fused sort + match) of a launch set.
 cudaError_t launch_plot_seq(const LaunchSet &L, cudaStream_t s);
 // Marks plots as issued on stream s (vx_sync waits on it).
 void mark_issued(vx_plot *const *plots, int n, cudaStream_t s);

@@ -16,7 +16,7 @@ constexpr int kMaxK = 32;                // u32 nonces
 constexpr int kMaxCoarseBits = 10;       // first scatter level, <= 1024 bins
 constexpr int kMaxFineBits = 10;         // second scatter level, <= 1024 bins
 constexpr int kScatterTile = 4096;       // records per CTA in the second scatter level
-constexpr int kScatterThreads = 256;
+constexpr int kScatterThreads = 512;
 constexpr int kSortThreads = 256;
 constexpr int kMatchThreads = 256;
 constexpr int kMaxSortDigitBits = 13;    // counting-sort digit of the partition sort
@@ -30,6 +30,7 @@ constexpr uint32_t kStCountMismatch = 1u << 2;
 constexpr uint32_t kStT2Capacity = 1u << 3;
 constexpr uint32_t kStPartitionTooBig = 1u << 4;
 constexpr uint32_t kStTimeout = 1u << 5;
+constexpr uint32_t kStBadTicket = 1u << 6;
 
 // ------------------------------------------------------ plot descriptor
 // One plot's plan and buffers.  The host fills everything but pre1/pre2,
@@ -46,6 +47,8 @@ struct Desc {
     uint32_t cap1;       // records per level-1 slot (p2 > 0 only)
     uint32_t cap2;       // records per level-2 slot (final partitions)
     uint32_t chunks1;    // scatter-2 CTAs per level-1 slot = ceil(cap1 / tile)
+    uint32_t spin_limit; // polls before a device-side wait gives up
+    uint32_t test_flags; // vx_opts.test_flags (fault injection)
     uint64_t *a_keys;    // level-1 slots, SoA: key64 [2^p1 * cap1]
     uint32_t *a_nonces;  //                      nonce [2^p1 * cap1]
     uint64_t *b_keys;    // level-2 slots, SoA: key64 [2^p * cap2]
@@ -55,6 +58,10 @@ struct Desc {
     uint64_t *t1off;     // [2^p + 1] Table-1 record offset of each partition
     uint64_t *pairs;     // [2^p] Table-2 pairs of each partition
     uint64_t *t2off;     // [2^p + 1] Table-2 record offset of each partition
+    uint64_t *lb;        // [2^p] look-back words of the fused sort+match
+    uint32_t *ticket;    // partition ticket of the fused sort+match
+    uint64_t *lbs;       // [chunks] look-back words of the Table-1 offset scan
+    uint32_t *ticket_s;  // chunk ticket of the Table-1 offset scan
     uint32_t *status;    // status word
     uint8_t *t1;         // Table 1, 12-byte records
     uint8_t *t2;         // Table 2, 16-byte records
@@ -231,6 +238,134 @@ __device__ __forceinline__ uint64_t block_sum_u64(uint64_t x, uint64_t *ws)
     return s;
 }
 
+// ------------------------------------------------ decoupled look-back
+// Per-item words: 2 flag bits (aggregate / inclusive prefix / poisoned) and
+// a 62-bit value.  Items are taken in ticket order, so every item an item
+// waits on is already running; waits are bounded (spin limit) and a
+// timeout poisons the item so that later items stop at once.
+constexpr uint64_t kLbAgg = 1ull << 62;       // look-back: aggregate published
+constexpr uint64_t kLbIncl = 2ull << 62;      // look-back: inclusive prefix published
+constexpr uint64_t kLbPoison = 3ull << 62;    // look-back: chain broken (timeout)
+constexpr uint64_t kLbMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ void st_release_u64(uint64_t *p, uint64_t v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p)
+{
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Exclusive prefix of item f (value agg) by decoupled look-back, run by
+// all 32 lanes of one warp: each step reads 32 predecessors at once, adds
+// the aggregates back to the nearest published inclusive prefix, and
+// retries (bounded) while one of them has published nothing yet.  Lane 0
+// publishes f's aggregate first and its inclusive prefix at the end.
+// Returns false (every lane) if the chain is poisoned or a wait ran out
+// (status gets kStTimeout); `withhold` (test hook) keeps item 0 silent.
+__device__ __forceinline__ bool lookback_warp(uint64_t *lb, uint32_t f, uint64_t agg,
+                                              uint32_t *status, uint32_t limit, bool withhold,
+                                              uint64_t *excl_out)
+{
+    const int lane = threadIdx.x & 31;
+    if (f == 0) {
+        if (withhold) return false;
+        if (lane == 0) st_release_u64(lb, kLbIncl | agg);
+        *excl_out = 0;
+        return true;
+    }
+    if (lane == 0) st_release_u64(lb + f, kLbAgg | agg);
+    uint64_t excl = 0;
+    int64_t hi = (int64_t)f - 1;   // newest predecessor not yet added
+    uint32_t spins = 0;
+    for (;;) {
+        const int64_t j = hi - lane;
+        // Items before 0 read as an inclusive prefix of 0.
+        const uint64_t v = j >= 0 ? ld_acquire_u64(lb + j) : kLbIncl;
+        const uint64_t fl = v & ~kLbMask;
+        const uint32_t incl = __ballot_sync(0xffffffffu, fl == kLbIncl);
+        const uint32_t stop = incl ? (uint32_t)(__ffs(incl) - 1) : 31u;
+        const uint32_t upto = stop == 31u ? 0xffffffffu : ((2u << stop) - 1u);
+        const uint32_t poison = __ballot_sync(0xffffffffu, fl == kLbPoison) & upto;
+        const uint32_t waiting = __ballot_sync(0xffffffffu, fl == 0) & upto;
+        if (poison) {
+            if (lane == 0) st_release_u64(lb + f, kLbPoison);
+            return false;
+        }
+        if (waiting) {
+            if (++spins > limit) {
+                if (lane == 0) {
+                    atomicOr(status, kStTimeout);
+                    st_release_u64(lb + f, kLbPoison);
+                }
+                return false;
+            }
+            __nanosleep(64);
+            continue;
+        }
+        uint64_t x = ((uint32_t)lane <= stop) ? (v & kLbMask) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        excl += x;
+        if (incl) break;
+        hi -= 32;
+    }
+    if (lane == 0) st_release_u64(lb + f, kLbIncl | (excl + agg));
+    *excl_out = excl;
+    return true;
+}
+
+// -------------------------------------------------- TMA bulk copy helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bulk global -> shared copy (addresses 16-byte aligned, bytes % 16 == 0)
+// completing on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Waits for phase `parity` of the mbarrier; gives up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit)
+{
+    for (uint32_t i = 0; i < limit; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 }  // namespace vx
 
 // ----------------------------------------------- launch entry points (host)
@@ -244,9 +379,20 @@ struct HashCfg {
 cudaError_t launch_key_setup(Desc *descs, int nplots, cudaStream_t s);
 cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *tile_start,
                                 uint32_t total_tiles, HashCfg cfg, cudaStream_t s);
+cudaError_t launch_hash_direct(const Desc *descs, int nplots, const uint32_t *tile_start,
+                               uint32_t total_tiles, cudaStream_t s);
+cudaError_t launch_sortmatch(const Desc *descs, int nplots, const uint32_t *tile_start,
+                             uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits,
+                             bool fused_hash);
+cudaError_t launch_t2_hash(const Desc *descs, int nplots, const uint32_t *tile_start,
+                           uint32_t total_tiles, cudaStream_t s);
+constexpr uint64_t kT2HashTile = 256 * 8;  // Table-2 records per pair-hash CTA
+size_t sortmatch_smem_bytes(uint32_t cap, int dbits);
 cudaError_t launch_scatter2(const Desc *descs, int nplots, const uint32_t *tile_start,
                             uint32_t total_tiles, cudaStream_t s);
-cudaError_t launch_scan_counts(const Desc *descs, int nplots, cudaStream_t s);
+cudaError_t launch_scan_counts(const Desc *descs, int nplots, const uint32_t *tile_start,
+                               uint32_t total_tiles, cudaStream_t s);
+constexpr uint32_t kScanChunk = 4096;      // counters per CTA of the Table-1 offset scan
 cudaError_t launch_sort(const Desc *descs, int nplots, const uint32_t *tile_start,
                         uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits);
 cudaError_t launch_scan_pairs(const Desc *descs, int nplots, cudaStream_t s);

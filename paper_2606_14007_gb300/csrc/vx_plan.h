@@ -17,7 +17,7 @@
 
 namespace vx {
 
-constexpr int kDefaultPartLog2 = 12;       // mean records per physical partition: 4096
+constexpr int kDefaultPartLog2 = 11;       // mean records per physical partition: 2048
 constexpr uint32_t kDefaultSlackSigma = 12;
 constexpr int kMaxPartBits = 20;           // two scatter levels of <= 10 bits each
 constexpr int kAggMaxBits = 6;             // warp-aggregate ranks up to 64 bins
@@ -26,17 +26,28 @@ constexpr size_t kStageTilesOffset = 3584;
 constexpr uint64_t kWriteStageBytes = 256ull << 20;  // Sec. III-B: 256 MB pinned staging
 constexpr uint64_t kWriteChunkBytes = 4ull << 20;    // Sec. III-A: 4 MB sequential chunks
 constexpr uint64_t kPlanHashTile = 2048;   // nonces per hash CTA (threads x nonces/thread)
+constexpr uint64_t kPlanScanChunk = 4096;  // counters per Table-1 offset-scan CTA
+constexpr uint64_t kPlanT2HashTile = 2048; // Table-2 records per pair-hash CTA
+
+enum { kScatterAuto = 0, kScatterStaged = 1, kScatterDirect = 2 };
 
 struct Plan {
     int K, s, p, p1, p2, dbits;
+    int mode;                              // kScatterStaged or kScatterDirect
+    uint32_t test_flags, spin_limit;
+    bool fuse_pair_hash;
     uint64_t N, D, t2cap;
     uint32_t cap1, cap2, chunks1;
     bool agg;
     uint32_t tiles_hash, tiles_s2, tiles_part;
+    uint32_t tiles_staged, tiles_direct;   // tiles_hash of the kernel the mode uses, 0 for the other
+    uint32_t tiles_scan, tiles_t2h;        // Table-1 offset scan chunks, pair-hash CTAs
     uint64_t regionA_keys, regionB_keys;   // byte offset of the nonce array in each slot region
     uint64_t regionA_bytes, regionB_bytes;
     uint64_t t1_bytes, t2_bytes, scratch_bytes;
-    uint64_t o_status, o_cnt1, o_cnt2, o_t1off, o_pairs, o_t2off, o_desc, o_tiles;
+    uint64_t o_status, o_ticket, o_ticket_s, o_cnt1, o_cnt2, o_t1off, o_pairs, o_t2off, o_lb, o_lbs,
+        o_desc, o_tiles;
+    uint64_t o_regionB;                    // final-partition slots (scratch buffer)
 };
 
 inline uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
@@ -86,16 +97,39 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, std::string *why, 
         return VX_EINVAL;
     }
     const uint32_t slack = opts.slack_sigma ? opts.slack_sigma : kDefaultSlackSigma;
+    if (opts.test_flags & ~1u) {
+        *why = "unknown test_flags bit";
+        return VX_EINVAL;
+    }
+    P.test_flags = opts.test_flags;
+    for (int i = 0; i < 7; ++i)
+        if (opts.reserved[i]) {
+            *why = "reserved vx_opts fields must be zero";
+            return VX_EINVAL;
+        }
+    P.fuse_pair_hash = opts.fuse_pair_hash != 0;
+    // ~1 us per poll: ~4 s in normal use (never reached unless a partition
+    // fails to publish), ~4 ms when a test withholds a prefix on purpose.
+    P.spin_limit = opts.test_flags ? (1u << 12) : (1u << 22);
     P.p = K - P.s;
     if (P.p < 0) P.p = 0;
     if (P.p > kMaxPartBits) P.p = kMaxPartBits;
-    if (opts.coarse_bits >= 0) {
+    if (opts.scatter_mode > kScatterDirect) {
+        *why = "scatter_mode must be 0 (auto), 1 (staged) or 2 (direct)";
+        return VX_EINVAL;
+    }
+    // Automatic = staged: on GB300 the per-record slot claims of the direct
+    // strategy cost more L2 atomic throughput than the second scatter pass.
+    P.mode = opts.scatter_mode == kScatterDirect ? kScatterDirect : kScatterStaged;
+    if (P.mode == kScatterDirect) {
+        P.p1 = P.p;  // one level: the hash kernel claims final-partition slots
+    } else if (opts.coarse_bits >= 0) {
         P.p1 = opts.coarse_bits < P.p ? opts.coarse_bits : P.p;
     } else {
         P.p1 = P.p <= 10 ? P.p : P.p / 2;
     }
     P.p2 = P.p - P.p1;
-    if (P.p1 > 10 || P.p2 > 10) {
+    if (P.mode == kScatterStaged && (P.p1 > 10 || P.p2 > 10)) {
         *why = "coarse_bits leaves a scatter level wider than 10 bits";
         return VX_EINVAL;
     }
@@ -132,8 +166,12 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, std::string *why, 
     }
     // Grids (tile sizes are the kernels' compile-time tiles).
     P.tiles_hash = (uint32_t)((P.N + kPlanHashTile - 1) / kPlanHashTile);
+    P.tiles_staged = P.mode == kScatterStaged ? P.tiles_hash : 0u;
+    P.tiles_direct = P.mode == kScatterDirect ? P.tiles_hash : 0u;
     P.tiles_s2 = P.p2 > 0 ? (uint32_t)(((uint64_t)1 << P.p1) * P.chunks1) : 0u;
     P.tiles_part = (uint32_t)(1ull << P.p);
+    P.tiles_scan = (uint32_t)(((1ull << P.p) + kPlanScanChunk - 1) / kPlanScanChunk);
+    P.tiles_t2h = (uint32_t)((P.t2cap + kPlanT2HashTile - 1) / kPlanT2HashTile);
 
     // Slot regions (SoA: key64 array, then nonce array).
     if (P.p2 > 0) {
@@ -146,21 +184,31 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, std::string *why, 
         P.regionB_keys = recs * 8;
         P.regionB_bytes = recs * 12;
     }
+    // Buffers.  The first-level slots alias the Table-1 buffer (they are
+    // consumed by the second scatter level before any Table-1 write).  The
+    // final-partition slots get their own region in the scratch buffer: the
+    // fused sort + match reads them while it writes both tables.
     const uint64_t t1_tab = 12 * P.N;
     const uint64_t t2_tab = 16 * P.t2cap;
     P.t1_bytes = round_up((t1_tab > P.regionA_bytes ? t1_tab : P.regionA_bytes) + 256, 256);
-    P.t2_bytes = round_up((t2_tab > P.regionB_bytes ? t2_tab : P.regionB_bytes) + 256, 256);
+    P.t2_bytes = round_up(t2_tab + 256, 256);
     // Scratch layout.
     const uint64_t np = 1ull << P.p;
     uint64_t at = 0;
-    P.o_status = at; at += 256;
+    P.o_status = at;
+    P.o_ticket = at + 64;
+    P.o_ticket_s = at + 128;
+    at += 256;
     P.o_cnt1 = at; at = round_up(at + 4 * ((uint64_t)1 << P.p1), 256);
     P.o_cnt2 = at; at = round_up(at + 4 * np, 256);
     P.o_t1off = at; at = round_up(at + 8 * (np + 1), 256);
     P.o_pairs = at; at = round_up(at + 8 * np, 256);
     P.o_t2off = at; at = round_up(at + 8 * (np + 1), 256);
+    P.o_lb = at; at = round_up(at + 8 * np, 256);
+    P.o_lbs = at; at = round_up(at + 8 * (uint64_t)P.tiles_scan, 256);
     P.o_desc = at; at = round_up(at + desc_bytes, 256);
     P.o_tiles = at; at = round_up(at + 64, 256);
+    P.o_regionB = at; at = round_up(at + P.regionB_bytes, 256);
     P.scratch_bytes = at;
     *pl = P;
     return VX_OK;

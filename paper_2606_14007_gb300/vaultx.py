@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(PKG, "libvaultx.so")
 VX_OK, VX_EINVAL, VX_ENOMEM, VX_ECUDA, VX_ETIMEDOUT, VX_EBUSY, VX_ENOTREADY, VX_EOVERFLOW = (
     0, -1, -2, -3, -4, -5, -6, -7)
 VX_TABLE1, VX_TABLE2 = 1, 2
+VX_TEST_WITHHOLD_PREFIX = 1
 VX_QUEUED, VX_RUNNING, VX_DONE, VX_FAILED = 0, 1, 2, 3
 T1_REC, T2_REC = 12, 16
 
@@ -37,15 +38,17 @@ class VxError(RuntimeError):
 class vx_opts(ctypes.Structure):
     _fields_ = [
         ("size", ctypes.c_uint32),
-        ("reserved0", ctypes.c_uint32),
+        ("test_flags", ctypes.c_uint32),
         ("match_distance", ctypes.c_uint64),
         ("partition_log2", ctypes.c_int32),
         ("coarse_bits", ctypes.c_int32),
         ("slack_sigma", ctypes.c_uint32),
         ("hash_block", ctypes.c_uint32),
         ("nonces_per_thread", ctypes.c_uint32),
-        ("reserved1", ctypes.c_uint32),
+        ("scatter_mode", ctypes.c_uint32),
         ("t2_capacity", ctypes.c_uint64),
+        ("fuse_pair_hash", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 7),
     ]
 
 
@@ -88,6 +91,7 @@ def lib():
             "vx_plot_alloc": (c_int, [vp]),
             "vx_table1": (c_int, [vp, vp]),
             "vx_match": (c_int, [vp, vp]),
+            "vx_plot_run": (c_int, [vp, vp]),
             "vx_sync": (c_int, [vp]),
             "vx_table_info": (c_int, [vp, c_int, P(vp), P(u64), P(u32)]),
             "vx_table1_offsets": (c_int, [vp, vp, vp]),
@@ -101,6 +105,7 @@ def lib():
             "vx_plot_profile": (c_int, [vp, c_int]),
             "vx_plot_profile_read": (c_int, [vp, P(ctypes.c_double), c_int, P(c_int), P(c_int)]),
             "vx_kernel_name": (ctypes.c_char_p, [c_int]),
+            "vx_plot_kernel_mask": (c_int, [vp, c_int, P(u32)]),
             "vx_serve_create": (c_int, [P(vx_serve_opts), P(vp)]),
             "vx_serve_submit": (c_int, [vp, c_int, u8p, P(u64)]),
             "vx_serve_poll": (c_int, [vp, u64, P(c_int), P(vp)]),
@@ -188,6 +193,10 @@ def vx_match(plot, stream=None):
     return _check(lib().vx_match(plot, _stream(stream)), "vx_match", plot)
 
 
+def vx_plot_run(plot, stream=None):
+    return _check(lib().vx_plot_run(plot, _stream(stream)), "vx_plot_run", plot)
+
+
 def vx_sync(plot, check: bool = True) -> int:
     rc = lib().vx_sync(plot)
     return _check(rc, "vx_sync", plot) if check else rc
@@ -249,6 +258,14 @@ def vx_plot_profile_read(plot) -> tuple[dict, int]:
     _check(lib().vx_plot_profile_read(plot, ms, 16, ctypes.byref(nk), ctypes.byref(nr)),
            "vx_plot_profile_read", plot)
     return {lib().vx_kernel_name(k).decode(): ms[k] for k in range(nk.value)}, nr.value
+
+
+def vx_plot_kernel_mask(plot, split: bool = False) -> list[str]:
+    """Names of the kernels one run of the plot launches."""
+    m = ctypes.c_uint32()
+    _check(lib().vx_plot_kernel_mask(plot, 1 if split else 0, ctypes.byref(m)),
+           "vx_plot_kernel_mask", plot)
+    return [lib().vx_kernel_name(k).decode() for k in range(32) if m.value >> k & 1]
 
 
 def vx_test_fail_next_allocs(count: int):
@@ -328,6 +345,12 @@ class Plot:
         return self
 
     def run(self, stream=None):
+        """Both tables in one pass (fused sort + match)."""
+        vx_plot_run(self.handle, stream)
+        return self
+
+    def run_split(self, stream=None):
+        """Both tables through vx_table1 then vx_match."""
         return self.table1(stream).match(stream)
 
     def sync(self) -> int:

@@ -68,11 +68,12 @@ def test_required_bytes_footprints(vx):
         E = 2 ** 24 * lam * lam / 2 * (1.0 if K <= 24 else (2 / lam - 1 / lam ** 2))
         assert t2 >= 16 * E
         assert sc > 0 and sc % 256 == 0
-    # K = 31: the tables dominate, scratch is megabytes (offsets, counters).
+    # K = 31: tables at their record sizes; scratch holds the partition slots
+    # (12 B per record plus the slot slack) and megabytes of counters.
     t1, t2, sc = vx.vx_plot_required_bytes(31)
     assert t1 < 1.05 * 12 * 2 ** 31
     assert t2 < 1.05 * 16 * 2 ** 31
-    assert sc < 64 << 20
+    assert 12 * 2 ** 31 < sc < 1.4 * 12 * 2 ** 31
 
 
 def test_required_bytes_rejects_bad_arguments(vx):
@@ -80,7 +81,8 @@ def test_required_bytes_rejects_bad_arguments(vx):
         with pytest.raises(vx.VxError) as ei:
             vx.vx_plot_required_bytes(K)
         assert ei.value.code == vx.VX_EINVAL
-    for kw in [dict(partition_log2=5), dict(partition_log2=14), dict(coarse_bits=11),
+    for kw in [dict(partition_log2=5), dict(partition_log2=14),
+               dict(coarse_bits=11, scatter_mode=1), dict(scatter_mode=3),
                dict(slack_sigma=400, partition_log2=13)]:
         with pytest.raises(vx.VxError):
             vx.vx_plot_required_bytes(31, vx.make_opts(**kw))
@@ -103,6 +105,16 @@ def test_create_and_destroy_without_device(vx):
     with pytest.raises(ValueError):
         vx.vx_plot_create(20, b"short")
     assert vx.lib().vx_plot_create(40, key, None, ctypes.byref(ctypes.c_void_p())) == vx.VX_EINVAL
+
+
+def test_kernel_mask_follows_plan(vx):
+    h = vx.vx_plot_create(31, bytes(32))
+    assert vx.vx_plot_kernel_mask(h) == ["key_setup", "hash_staged", "scatter2", "scan_counts",
+                                         "sortmatch", "pairhash"]
+    vx.vx_plot_destroy(h)
+    h = vx.vx_plot_create(20, bytes(32), vx.make_opts(scatter_mode=2, fuse_pair_hash=1))
+    assert vx.vx_plot_kernel_mask(h) == ["key_setup", "hash_direct", "scan_counts", "sortmatch"]
+    vx.vx_plot_destroy(h)
 
 
 def test_bind_rejects_misaligned(vx):

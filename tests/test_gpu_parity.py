@@ -25,9 +25,12 @@ def vx():
     return vaultx
 
 
-def run_plot(vx, K, key, opts=None):
+def run_plot(vx, K, key, opts=None, split=False):
     p = vx.Plot(K, key, opts)
-    p.run()
+    if split:
+        p.run_split()
+    else:
+        p.run()
     n2 = p.sync()
     t1 = p.t1.cpu().numpy()
     t2 = p.t2.cpu().numpy()
@@ -68,24 +71,36 @@ def test_pair_hash_row_matches_oracle(vx):
         assert got[i, 8:].tobytes() == orc.keyed_hash(key, got[i, :8].tobytes(), 8), i
 
 
-# (K, seed, opts) -- opts exercise both scatter levels and the sort digit widths.
+STAGED = dict(scatter_mode=1)
+DIRECT = dict(scatter_mode=2)
+FUSED = dict(fuse_pair_hash=1)
+# (K, seed, opts) -- sizes from one record to the small configuration;
+# opts exercise both bucketing strategies, both scatter levels and the sort
+# digit widths.
 CASES = [
     (1, 0, {}), (2, 1, {}), (3, 2, {}), (5, 3, {}), (8, 4, {}), (11, 5, {}), (12, 6, {}),
     (13, 7, {}), (14, 8, {}), (16, 9, {}), (18, 10, {}), (20, 11, {}), (22, 0, {}),
-    (16, 12, dict(partition_log2=6, coarse_bits=4)),       # two levels, 1024 partitions
-    (20, 13, dict(partition_log2=8)),                      # two levels (auto), 4096 partitions
-    (18, 14, dict(partition_log2=13)),                     # large partitions, 13-bit digits
-    (12, 15, dict(partition_log2=6, coarse_bits=0)),       # single first-level slot
-    (17, 16, dict(partition_log2=7, coarse_bits=10)),      # 10 + 0 bits
-    (19, 17, dict(partition_log2=9, slack_sigma=40)),      # roomy slots
+    (1, 0, STAGED), (5, 3, STAGED), (12, 6, STAGED), (17, 18, STAGED), (22, 0, STAGED),
+    (1, 0, DIRECT), (5, 3, DIRECT), (12, 6, DIRECT), (17, 18, DIRECT), (22, 0, DIRECT),
+    (20, 20, dict(DIRECT, partition_log2=6)),
+    (1, 0, FUSED), (9, 21, FUSED), (16, 22, FUSED), (22, 0, FUSED),
+    (19, 23, dict(FUSED, scatter_mode=2, partition_log2=7)),
+    (16, 12, dict(STAGED, partition_log2=6, coarse_bits=4)),   # two levels, 1024 partitions
+    (20, 13, dict(STAGED, partition_log2=8)),                  # two levels (auto)
+    (12, 15, dict(STAGED, partition_log2=6, coarse_bits=0)),   # single first-level slot
+    (17, 16, dict(STAGED, partition_log2=7, coarse_bits=10)),  # 10 + 0 bits
+    (18, 14, dict(partition_log2=13)),                         # large partitions, 13-bit digits
+    (19, 17, dict(partition_log2=9, slack_sigma=40)),          # roomy slots
+    (20, 19, dict(partition_log2=6)),                          # 2^14 tiny partitions
 ]
 
 
+@pytest.mark.parametrize("split", [False, True], ids=["fused", "split"])
 @pytest.mark.parametrize("K,seed,kw", CASES)
-def test_plot_matches_oracle(vx, K, seed, kw):
+def test_plot_matches_oracle(vx, K, seed, kw, split):
     key = plot_key(seed)
     opts = vx.make_opts(**kw) if kw else None
-    t1, t2, n2, off = run_plot(vx, K, key, opts)
+    t1, t2, n2, off = run_plot(vx, K, key, opts, split)
     r1, r2 = oracle_plot(K, key)
     assert np.array_equal(t1, r1)
     assert n2 == r2.shape[0]
@@ -93,11 +108,12 @@ def test_plot_matches_oracle(vx, K, seed, kw):
     assert np.array_equal(off.astype(np.uint64), orc.bucket_offsets(r1))
 
 
+@pytest.mark.parametrize("split", [False, True], ids=["fused", "split"])
 @pytest.mark.parametrize("K,seed,D", [(16, 20, 1 << 34), (18, 21, 1 << 37), (14, 22, 1),
                                       (15, 23, (1 << 64) - 1), (17, 24, 12345678901)])
-def test_custom_match_distance(vx, K, seed, D):
+def test_custom_match_distance(vx, K, seed, D, split):
     key = plot_key(seed)
-    t1, t2, n2, _ = run_plot(vx, K, key, vx.make_opts(match_distance=D))
+    t1, t2, n2, _ = run_plot(vx, K, key, vx.make_opts(match_distance=D), split)
     r1, r2 = oracle_plot(K, key, D)
     assert np.array_equal(t1, r1)
     assert np.array_equal(t2, r2)
@@ -126,22 +142,24 @@ def test_deterministic_repeat(vx):
         assert np.array_equal(a[0], outs[0][0]) and np.array_equal(a[1], outs[0][1])
 
 
-def test_slot_overflow_is_reported(vx):
+@pytest.mark.parametrize("mode", [1, 2], ids=["staged", "direct"])
+def test_slot_overflow_is_reported(vx, mode):
     # Slots of mean + 1 sd (+16) overflow in many partitions: the plot must
     # report VX_EOVERFLOW, never produce silently short tables or fault.
     key = plot_key(50)
-    p = vx.Plot(18, key, vx.make_opts(partition_log2=6, slack_sigma=1))
+    p = vx.Plot(18, key, vx.make_opts(partition_log2=6, slack_sigma=1, scatter_mode=mode))
     p.run()
     rc = vx.vx_sync(p.handle, check=False)
     assert rc == vx.VX_EOVERFLOW
     p.close()
 
 
-def test_table2_capacity_then_rebind(vx):
+@pytest.mark.parametrize("split", [False, True], ids=["fused", "split"])
+def test_table2_capacity_then_rebind(vx, split):
     key = plot_key(60)
     K = 16
     p = vx.Plot(K, key, vx.make_opts(t2_capacity=16))
-    p.run()
+    p.run_split() if split else p.run()
     assert vx.vx_sync(p.handle, check=False) == vx.VX_ENOMEM
     _, need, _, rc = vx.vx_table_info(p.handle, vx.VX_TABLE2, check=False)
     assert rc == vx.VX_ENOMEM
@@ -155,6 +173,20 @@ def test_table2_capacity_then_rebind(vx):
     got = big[: 16 * need].view(need, 16).cpu().numpy()
     assert np.array_equal(got, r2)
     p.close()
+
+
+def test_lookback_wait_times_out(vx):
+    # Partition 0 withholds its Table-2 prefix: every later partition's wait
+    # must run out (bounded), the plot must report VX_ETIMEDOUT, and the
+    # context must stay usable for the next plot.
+    p = vx.Plot(16, plot_key(61), vx.make_opts(partition_log2=8,
+                                                test_flags=vx.VX_TEST_WITHHOLD_PREFIX))
+    p.run()
+    assert vx.vx_sync(p.handle, check=False) == vx.VX_ETIMEDOUT
+    p.close()
+    t1, t2, n2, _ = run_plot(vx, 14, plot_key(62))
+    r1, r2 = oracle_plot(14, plot_key(62))
+    assert np.array_equal(t2, r2)
 
 
 def test_alloc_failure_injection(vx):
@@ -200,13 +232,35 @@ def test_plot_write_file(vx, tmp_path):
 
 def test_profile_trace(vx):
     p = vx.Plot(20, plot_key(90))
-    vx.vx_plot_profile(p.handle, 2)
-    for _ in range(2):
-        p.run()
+    vx.vx_plot_profile(p.handle, 3)
+    p.run()
+    p.run_split()
+    p.run()
     p.sync()
     ms, runs = vx.vx_plot_profile_read(p.handle)
-    assert runs == 2
-    assert set(ms) == {"key_setup", "hash_scatter", "scatter2", "scan_counts", "sort",
-                       "scan_pairs", "match"}
-    assert ms["hash_scatter"] > 0 and ms["match"] > 0
+    assert runs == 3
+    assert set(ms) == {"key_setup", "hash_staged", "hash_direct", "scatter2", "scan_counts",
+                       "sort", "scan_pairs", "match", "sortmatch", "pairhash"}
+    assert ms["hash_staged"] > 0 and ms["sortmatch"] > 0 and ms["sort"] > 0 and ms["match"] > 0
+    assert ms["pairhash"] > 0
+    assert vx.vx_plot_kernel_mask(p.handle) == ["key_setup", "hash_staged", "scan_counts",
+                                                "sortmatch", "pairhash"]
+    assert vx.vx_plot_kernel_mask(p.handle, split=True) == [
+        "key_setup", "hash_staged", "scan_counts", "sort", "scan_pairs", "match"]
     p.close()
+
+
+def test_split_and_fused_agree_mid_size(vx):
+    # K=24 (no oracle at this size in the fast suite): both paths and both
+    # bucketing strategies give identical bytes.
+    key = plot_key(91)
+    outs = []
+    for kw, split in [({}, False), ({}, True), (DIRECT, False), (dict(partition_log2=13), False),
+                      (FUSED, False)]:
+        p = vx.Plot(24, key, vx.make_opts(**kw) if kw else None)
+        p.run_split() if split else p.run()
+        p.sync()
+        outs.append((p.t1.clone(), p.t2.clone()))
+        p.close()
+    for t1, t2 in outs[1:]:
+        assert torch.equal(t1, outs[0][0]) and torch.equal(t2, outs[0][1])
