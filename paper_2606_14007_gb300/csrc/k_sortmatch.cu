@@ -25,21 +25,24 @@
 
 namespace vx {
 
-constexpr int kSMThreads = 256;
 enum { kSortCount = 0, kSortHash = 1, kSortEmit = 2 };
-constexpr uint32_t kSMList = 2048;            // pair-list window (entries)
+constexpr uint32_t kSMList = 2048;  // pair-list window (entries), kSortHash only
+constexpr int kSMThreads = 256;
 
+// Shared layout: sorted key64 [cap] | sorted nonce [cap] | rank within the
+// digit, u16 [cap] | digit counters [2^dbits] | per-record pair count ->
+// Table-2 offset [cap] | pair list (kSortHash) | scan workspace.
 struct SMLayout {
     size_t sn, rank, dcnt, start, list, ws, bytes;
     __host__ __device__ SMLayout(uint32_t cap, int dbits, bool with_list)
     {
-        sn = (size_t)cap * 8;                    // sorted key64 [cap] at 0
-        rank = sn + (size_t)cap * 4;             // sorted nonce [cap]
-        dcnt = rank + (size_t)((cap + 1) & ~1u) * 2;  // rank within digit, u16 [cap]
-        start = dcnt + ((size_t)1 << dbits) * 4; // digit counters -> starts [2^dbits]
-        list = start + (size_t)cap * 4;          // per-record pair count -> start [cap]
-        ws = list + (with_list ? (size_t)kSMList * 4 : 0);  // pair list window
-        bytes = ws + (kSMThreads / 32 + 2) * 4 + 16;
+        sn = (size_t)cap * 8;
+        rank = sn + (size_t)cap * 4;
+        dcnt = rank + (size_t)((cap + 1) & ~1u) * 2;
+        start = dcnt + ((size_t)1 << dbits) * 4;
+        list = start + (size_t)cap * 4;
+        ws = list + (with_list ? (size_t)kSMList * 4 : 0);
+        bytes = ws + 40 * 4;
     }
 };
 
@@ -91,23 +94,10 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
         RK[i] = (uint16_t)atomicAdd(&DC[dg], 1u);
     }
     __syncthreads();
-    {   // 2. exclusive scan of the digit counters (contiguous run per thread)
-        const uint32_t per = (ndig + NT - 1) / NT;
-        const uint32_t b0 = threadIdx.x * per;
-        uint32_t loc = 0;
-        for (uint32_t k = 0; k < per; ++k)
-            if (b0 + k < ndig) loc += DC[b0 + k];
-        uint32_t total;
-        uint32_t run = block_exclusive_scan_u32<NT>(loc, WS, &total);
-        for (uint32_t k = 0; k < per; ++k)
-            if (b0 + k < ndig) {
-                const uint32_t h = DC[b0 + k];
-                DC[b0 + k] = run;
-                run += h;
-            }
-    }
-    __syncthreads();
-    // 3. place records at their digit position (second read hits L1/L2)
+    // 2. digit counters -> digit start positions
+    block_scan_inplace_u32<NT>(DC, ndig, WS);
+    // 3. place records at their digit position (the second read of the
+    //    slot hits L1/L2)
     for (uint32_t i = threadIdx.x; i < n; i += NT) {
         const uint64_t k = __ldg(ikeys + i);
         const uint32_t pos = DC[(uint32_t)(k >> shift) & dmask] + RK[i];
@@ -115,7 +105,8 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
         SN[pos] = __ldg(inonces + i);
     }
     __syncthreads();
-    // 4. finish every digit run by insertion sort on (key64, nonce)
+    // 4. finish every digit run (about one record each) by insertion sort on
+    //    (key64, nonce)
     for (uint32_t dg = threadIdx.x; dg < ndig; dg += NT) {
         const uint32_t s0 = DC[dg];
         const uint32_t s1 = dg + 1 < ndig ? DC[dg + 1] : n;
@@ -136,67 +127,91 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
         }
     }
     __syncthreads();
-    // 5. Table-1 words {nonce, h0, h1}, consecutive threads on consecutive words
-    uint32_t *__restrict__ t1w = reinterpret_cast<uint32_t *>(d.t1) + 3 * off;
-    for (uint32_t w = threadIdx.x; w < 3 * n; w += NT) {
-        const uint32_t r = w / 3, q = w - 3 * r;
-        const uint64_t k = SK[r];
-        t1w[w] = q == 0 ? SN[r] : bswap32(q == 1 ? (uint32_t)(k >> 32) : (uint32_t)k);
-    }
-    // 6. pairs starting at each record: later records of its logical bucket
-    //    closer than D
+    // 5. pairs starting at each record r: the later records up to
+    //    lim = min(last key of r's logical bucket, key_r + D - 1); four
+    //    probes per step (key64 sorted ascending)
     const uint64_t D = d.D;
     for (uint32_t r = threadIdx.x; r < n; r += NT) {
         const uint64_t k = SK[r];
-        const uint64_t bucket = k >> 40;
+        const uint64_t last_in_bucket = k | ((1ull << 40) - 1);
+        uint64_t reach = k + (D - 1);
+        if (reach < k) reach = ~0ull;  // saturate
+        const uint64_t lim = reach < last_in_bucket ? reach : last_in_bucket;
         uint32_t c = 0;
-        for (uint32_t r2 = r + 1; r2 < n; ++r2) {
-            const uint64_t k2 = SK[r2];
-            if ((k2 >> 40) != bucket || k2 - k >= D) break;
-            ++c;
+        for (uint32_t q = r + 1; q < n; q += 4) {
+            const bool m0 = SK[q] <= lim;
+            const bool m1 = m0 && q + 1 < n && SK[q + 1] <= lim;
+            const bool m2 = m1 && q + 2 < n && SK[q + 2] <= lim;
+            const bool m3 = m2 && q + 3 < n && SK[q + 3] <= lim;
+            c += (uint32_t)m0 + (uint32_t)m1 + (uint32_t)m2 + (uint32_t)m3;
+            if (!m3) break;
         }
         ST[r] = c;
     }
     __syncthreads();
-    uint32_t P;
-    {   // exclusive scan of the counts -> per-record Table-2 offsets
-        const uint32_t per = (n + NT - 1) / NT;
-        const uint32_t b0 = min(n, threadIdx.x * per), b1 = min(n, b0 + per);
-        uint32_t loc = 0;
-        for (uint32_t r = b0; r < b1; ++r) loc += ST[r];
-        uint32_t run = block_exclusive_scan_u32<NT>(loc, WS, &P);
-        for (uint32_t r = b0; r < b1; ++r) {
-            const uint32_t c = ST[r];
-            ST[r] = run;
-            run += c;
+    // 6. counts -> per-record Table-2 offsets; the partition's pair count
+    //    is published at once so later partitions are not held up
+    const uint32_t P = block_scan_inplace_u32<NT>(ST, n, WS);
+    const bool withhold = (d.test_flags & 1u) != 0;
+    if (threadIdx.x == 0) {
+        d.pairs[f] = P;  // lets vx_match re-run the match alone
+        if (EMIT) lb_publish(d.lb, f, P, withhold);
+    }
+    // 7. Table 1.  Records 12 B each: the head up to a 16-byte boundary and
+    //    the tail go word by word; the body goes as groups of 4 records =
+    //    three 16-byte stores per thread.
+    {
+        uint32_t *__restrict__ t1w = reinterpret_cast<uint32_t *>(d.t1) + 3 * off;
+        const uint32_t head = min(n, (uint32_t)((4u - (uint32_t)(off & 3u)) & 3u));
+        const uint32_t groups = (n - head) / 4u;
+        const uint32_t tail0 = head + 4u * groups;
+        for (uint32_t r = threadIdx.x; r < head + (n - tail0); r += NT) {
+            const uint32_t rr = r < head ? r : tail0 + (r - head);
+            const uint64_t k = SK[rr];
+            t1w[3 * rr] = SN[rr];
+            t1w[3 * rr + 1] = bswap32((uint32_t)(k >> 32));
+            t1w[3 * rr + 2] = bswap32((uint32_t)k);
+        }
+        uint4 *__restrict__ body = reinterpret_cast<uint4 *>(t1w + 3 * head);
+        for (uint32_t g = threadIdx.x; g < groups; g += NT) {
+            const uint32_t r = head + 4u * g;
+            uint32_t w[12];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t k = SK[r + j];
+                w[3 * j] = SN[r + j];
+                w[3 * j + 1] = bswap32((uint32_t)(k >> 32));
+                w[3 * j + 2] = bswap32((uint32_t)k);
+            }
+            body[3 * g] = make_uint4(w[0], w[1], w[2], w[3]);
+            body[3 * g + 1] = make_uint4(w[4], w[5], w[6], w[7]);
+            body[3 * g + 2] = make_uint4(w[8], w[9], w[10], w[11]);
+        }
+    }
+    if (!EMIT) return;
+    // 8. Table-2 base: resolve the look-back (warp 0)
+    const uint64_t np = 1ull << d.p;
+    if (threadIdx.x < 32) {
+        uint64_t excl = 0;
+        int ok = lb_resolve(d.lb, f, P, d.status, d.spin_limit, withhold, &excl) ? 1 : 0;
+        if (threadIdx.x == 0) {
+            if (ok) {
+                d.t2off[f] = excl;
+                if (f + 1 == np) d.t2off[np] = excl + P;
+                if (excl + P > d.t2cap) {
+                    atomicOr(d.status, kStT2Capacity);
+                    ok = 0;
+                }
+            }
+            s_base = excl;
+            s_ok = ok;
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) d.pairs[f] = P;  // lets vx_match re-run the match alone
-    if (!EMIT) return;
-    const uint64_t np = 1ull << d.p;
+    if (!s_ok) return;
+    uint4 *__restrict__ out = reinterpret_cast<uint4 *>(d.t2) + s_base;
     if (MODE == kSortEmit) {
-        // Table-2 base by look-back, then {a, b, 0, 0} records in (i, j) order.
-        if (threadIdx.x < 32) {
-            uint64_t excl = 0;
-            int ok = lookback_warp(d.lb, f, P, d.status, d.spin_limit, (d.test_flags & 1u) != 0,
-                                   &excl) ? 1 : 0;
-            if (threadIdx.x == 0) {
-                if (ok) {
-                    d.t2off[f] = excl;
-                    if (f + 1 == np) d.t2off[np] = excl + P;
-                    if (excl + P > d.t2cap) {
-                        atomicOr(d.status, kStT2Capacity);
-                        ok = 0;
-                    }
-                }
-                s_base = excl;
-                s_ok = ok;
-            }
-        }
-        __syncthreads();
-        if (!s_ok) return;
-        uint4 *__restrict__ out = reinterpret_cast<uint4 *>(d.t2) + s_base;
+        // 9a. {a, b, 0, 0} records in (i, j) order; hashes come later
         for (uint32_t r = threadIdx.x; r < n; r += NT) {
             const uint32_t s0 = ST[r];
             const uint32_t s1 = r + 1 < n ? ST[r + 1] : P;
@@ -205,14 +220,11 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
         }
         return;
     }
-    // 7. Table-2 base by look-back (after the first window is listed, to
-    //    give the partitions before this one time to publish)
+    // 9b. hash here: list the pairs window by window, every lane hashes
     uint32_t g[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) g[i] = d.pre2[i];
-    bool first = true;
-    uint32_t w0 = 0;
-    do {
+    for (uint32_t w0 = 0; w0 < P; w0 += kSMList) {
         const uint32_t w1 = min(P, w0 + kSMList);
         for (uint32_t r = threadIdx.x; r < n; r += NT) {
             const uint32_t s = ST[r];
@@ -220,29 +232,7 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
             const uint32_t lo = max(s, w0), hi = min(e, w1);
             for (uint32_t k = lo; k < hi; ++k) LS[k - w0] = r | ((r + 1 + (k - s)) << 16);
         }
-        if (first) {
-            if (threadIdx.x < 32) {
-                uint64_t excl = 0;
-                int ok = lookback_warp(d.lb, f, P, d.status, d.spin_limit,
-                                       (d.test_flags & 1u) != 0, &excl) ? 1 : 0;
-                if (threadIdx.x == 0) {
-                    if (ok) {
-                        d.t2off[f] = excl;
-                        if (f + 1 == np) d.t2off[np] = excl + P;
-                        if (excl + P > d.t2cap) {
-                            atomicOr(d.status, kStT2Capacity);
-                            ok = 0;
-                        }
-                    }
-                    s_base = excl;
-                    s_ok = ok;
-                }
-            }
-            first = false;
-        }
         __syncthreads();
-        if (!s_ok) return;
-        uint4 *__restrict__ out = reinterpret_cast<uint4 *>(d.t2) + s_base;
         for (uint32_t q = threadIdx.x; q < w1 - w0; q += NT) {
             const uint32_t e = LS[q];
             const uint32_t a = SN[e & 0xffffu], b = SN[e >> 16];
@@ -251,11 +241,12 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
             out[w0 + q] = make_uint4(a, b, h0, h1);
         }
         __syncthreads();
-        w0 = w1;
-    } while (w0 < P);
+    }
 }
 
 size_t sortmatch_smem_bytes(uint32_t cap, int dbits) { return SMLayout(cap, dbits, true).bytes; }
+
+uint32_t sortmatch_max_cap() { return 16384u; }
 
 template <int MODE>
 static cudaError_t launch_sm(const Desc *descs, int nplots, const uint32_t *tile_start,

@@ -40,7 +40,7 @@ inline int make_plan(int K, const vx_opts *o, Plan *pl, std::string *why)
 {
     int rc = make_plan_sized(K, o, pl, why, sizeof(Desc));
     if (rc != VX_OK) return rc;
-    if (sortmatch_smem_bytes(pl->cap2, pl->dbits) > kMaxSmemPerCta ||
+    if (pl->cap2 > sortmatch_max_cap() || sortmatch_smem_bytes(pl->cap2, pl->dbits) > kMaxSmemPerCta ||
         match_smem_bytes(pl->cap2) > kMaxSmemPerCta) {
         *why = "partition slot too large for shared memory";
         return VX_EINVAL;

@@ -219,6 +219,46 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_u32(uint32_t x, uint32_
     return r;
 }
 
+// In-place exclusive scan of A[0..M) by a CTA of NT threads; returns the
+// total.  Warp w takes a contiguous run of A and walks it 32 entries at a
+// time (lane i on entry i: no bank conflicts); `ws` holds NT/32 words.
+// Ends with a __syncthreads.
+template <int NT>
+__device__ __forceinline__ uint32_t block_scan_inplace_u32(uint32_t *A, uint32_t M, uint32_t *ws)
+{
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t chunk = (M + NW - 1) / NW;
+    const uint32_t lo = min(M, (uint32_t)warp * chunk), hi = min(M, lo + chunk);
+    uint32_t sum = 0;
+    for (uint32_t i = lo + lane; i < hi; i += 32) sum += A[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) ws[warp] = sum;
+    __syncthreads();
+    uint32_t carry = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const uint32_t t = ws[w];
+        carry += w < warp ? t : 0u;
+        total += t;
+    }
+    for (uint32_t base = lo; base < hi; base += 32) {
+        const uint32_t i = base + lane;
+        const uint32_t v = i < hi ? A[i] : 0u;
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (i < hi) A[i] = carry + incl - v;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncthreads();
+    return total;
+}
+
 template <int NT>
 __device__ __forceinline__ uint64_t block_sum_u64(uint64_t x, uint64_t *ws)
 {
@@ -260,25 +300,32 @@ __device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p)
     return v;
 }
 
-// Exclusive prefix of item f (value agg) by decoupled look-back, run by
-// all 32 lanes of one warp: each step reads 32 predecessors at once, adds
-// the aggregates back to the nearest published inclusive prefix, and
-// retries (bounded) while one of them has published nothing yet.  Lane 0
-// publishes f's aggregate first and its inclusive prefix at the end.
-// Returns false (every lane) if the chain is poisoned or a wait ran out
-// (status gets kStTimeout); `withhold` (test hook) keeps item 0 silent.
-__device__ __forceinline__ bool lookback_warp(uint64_t *lb, uint32_t f, uint64_t agg,
-                                              uint32_t *status, uint32_t limit, bool withhold,
-                                              uint64_t *excl_out)
+// Publishes item f's own value (lane 0): its inclusive prefix when f == 0,
+// else its aggregate.  `withhold` (test hook) keeps item 0 silent.
+__device__ __forceinline__ void lb_publish(uint64_t *lb, uint32_t f, uint64_t agg, bool withhold)
+{
+    if (f == 0) {
+        if (!withhold) st_release_u64(lb, kLbIncl | agg);
+    } else {
+        st_release_u64(lb + f, kLbAgg | agg);
+    }
+}
+
+// Exclusive prefix of item f (value agg, already published by lb_publish)
+// by decoupled look-back, run by all 32 lanes of one warp: each step reads
+// 32 predecessors at once, adds the aggregates back to the nearest
+// published inclusive prefix, and retries (bounded) while one of them has
+// published nothing yet.  Lane 0 publishes f's inclusive prefix.  Returns
+// false (every lane) if the chain is poisoned or a wait ran out (status
+// gets kStTimeout), or for item 0 when it was withheld.
+__device__ __forceinline__ bool lb_resolve(uint64_t *lb, uint32_t f, uint64_t agg, uint32_t *status,
+                                           uint32_t limit, bool withhold, uint64_t *excl_out)
 {
     const int lane = threadIdx.x & 31;
     if (f == 0) {
-        if (withhold) return false;
-        if (lane == 0) st_release_u64(lb, kLbIncl | agg);
         *excl_out = 0;
-        return true;
+        return !withhold;
     }
-    if (lane == 0) st_release_u64(lb + f, kLbAgg | agg);
     uint64_t excl = 0;
     int64_t hi = (int64_t)f - 1;   // newest predecessor not yet added
     uint32_t spins = 0;
@@ -317,6 +364,16 @@ __device__ __forceinline__ bool lookback_warp(uint64_t *lb, uint32_t f, uint64_t
     if (lane == 0) st_release_u64(lb + f, kLbIncl | (excl + agg));
     *excl_out = excl;
     return true;
+}
+
+// Both steps at once (publish, then resolve).
+__device__ __forceinline__ bool lookback_warp(uint64_t *lb, uint32_t f, uint64_t agg,
+                                              uint32_t *status, uint32_t limit, bool withhold,
+                                              uint64_t *excl_out)
+{
+    if ((threadIdx.x & 31) == 0) lb_publish(lb, f, agg, withhold);
+    __syncwarp();
+    return lb_resolve(lb, f, agg, status, limit, withhold, excl_out);
 }
 
 // -------------------------------------------------- TMA bulk copy helpers
@@ -388,6 +445,7 @@ cudaError_t launch_t2_hash(const Desc *descs, int nplots, const uint32_t *tile_s
                            uint32_t total_tiles, cudaStream_t s);
 constexpr uint64_t kT2HashTile = 256 * 8;  // Table-2 records per pair-hash CTA
 size_t sortmatch_smem_bytes(uint32_t cap, int dbits);
+uint32_t sortmatch_max_cap();  // largest slot the sort keeps in registers
 cudaError_t launch_scatter2(const Desc *descs, int nplots, const uint32_t *tile_start,
                             uint32_t total_tiles, cudaStream_t s);
 cudaError_t launch_scan_counts(const Desc *descs, int nplots, const uint32_t *tile_start,

@@ -83,7 +83,7 @@ def test_required_bytes_rejects_bad_arguments(vx):
         assert ei.value.code == vx.VX_EINVAL
     for kw in [dict(partition_log2=5), dict(partition_log2=14),
                dict(coarse_bits=11, scatter_mode=1), dict(scatter_mode=3),
-               dict(slack_sigma=400, partition_log2=13)]:
+               dict(slack_sigma=400, partition_log2=12)]:
         with pytest.raises(vx.VxError):
             vx.vx_plot_required_bytes(31, vx.make_opts(**kw))
     bad = vx.make_opts()
@@ -133,7 +133,7 @@ def test_partition_plan_shape(vx):
         if prev:
             assert sc >= prev
         prev = sc
-    o = vx.make_opts(partition_log2=13)
+    o = vx.make_opts(partition_log2=12)
     t1a, _, _ = vx.vx_plot_required_bytes(31, o)
     t1b, _, _ = vx.vx_plot_required_bytes(31)
     assert t1a >= 12 * 2 ** 31 and t1b >= 12 * 2 ** 31

@@ -255,7 +255,7 @@ def test_split_and_fused_agree_mid_size(vx):
     # bucketing strategies give identical bytes.
     key = plot_key(91)
     outs = []
-    for kw, split in [({}, False), ({}, True), (DIRECT, False), (dict(partition_log2=13), False),
+    for kw, split in [({}, False), ({}, True), (DIRECT, False), (dict(partition_log2=12), False),
                       (FUSED, False)]:
         p = vx.Plot(24, key, vx.make_opts(**kw) if kw else None)
         p.run_split() if split else p.run()
