@@ -94,7 +94,15 @@ typedef struct vx_opts {
     uint32_t fuse_pair_hash;    /* vx_plot_run: 1 = hash the pairs inside the sort +
                                    match kernel; 0 = (default) the sort writes {a, b}
                                    records and a streaming pass hashes them         */
-    uint32_t reserved[7];       /* must be zero                                      */
+    uint32_t pipeline_chunks;   /* vx_plot_run / batches: the hash and the second
+                                   scatter level, and the sort and the pair hash,
+                                   run in this many chunks on two streams, each
+                                   memory-bound chunk overlapping the next ALU-bound
+                                   one; 0 = automatic (currently no overlap: on
+                                   GB300 the kernel pairs take turns on the SMs
+                                   rather than share them), 1 = no overlap; else
+                                   2, 4 or 8                                          */
+    uint32_t reserved[6];       /* must be zero                                      */
 } vx_opts;
 
 typedef struct vx_plot vx_plot;

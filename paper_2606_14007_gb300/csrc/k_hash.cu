@@ -31,13 +31,16 @@ __global__ void k_key_setup(Desc *descs)
         *d.ticket = 0u;
         *d.ticket_s = 0u;
     }
-    const uint64_t n1 = d.p2 > 0 ? (1ull << d.p1) : 0ull;
+    const uint64_t n1 = d.p2 > 0 ? ((uint64_t)d.hchunks << d.p1) : 0ull;
     const uint64_t n2 = 1ull << d.p;
     const uint64_t nchunks = (n2 + kScanChunk - 1) / kScanChunk;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
-        d.cnt2[i] = 0u;
-        d.lb[i] = 0ull;
+    const uint64_t nz = n2 > n1 ? n2 : n1;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nz; i += stride) {
+        if (i < n2) {
+            d.cnt2[i] = 0u;
+            d.lb[i] = 0ull;
+        }
         if (i < n1) d.cnt1[i] = 0u;
         if (i < nchunks) d.lbs[i] = 0ull;
     }
@@ -108,7 +111,8 @@ __device__ __forceinline__ void scan_and_claim(uint32_t *hist, uint32_t *loff, u
 
 template <int NT, int NPT, bool AGG>
 __global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ descs, int nplots,
-                                                     const uint32_t *__restrict__ tile_start)
+                                                     const uint32_t *__restrict__ tile_start,
+                                                     int chunk)
 {
     using S = HashSmem<NT, NPT>;
     constexpr int T = S::T;
@@ -117,15 +121,18 @@ __global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ de
 
     const int plot = find_plot(tile_start, nplots, blockIdx.x);
     const Desc &d = descs[plot];
-    const uint64_t N = d.N;
-    const uint64_t base = (uint64_t)(blockIdx.x - tile_start[plot]) * T;
+    uint64_t lo, N;  // this chunk's nonces: [lo, N)
+    nonce_chunk(d, chunk, lo, N);
+    const uint64_t base = lo + (uint64_t)(blockIdx.x - tile_start[plot]) * T;
     const bool two_level = d.p2 > 0;
     const int bits = two_level ? d.p1 : d.p;
     const int nbins = 1 << bits;
     const uint32_t cap = two_level ? d.cap1 : d.cap2;
-    uint64_t *__restrict__ okeys = two_level ? d.a_keys : d.b_keys;
-    uint32_t *__restrict__ ononces = two_level ? d.a_nonces : d.b_nonces;
-    uint32_t *cnt = two_level ? d.cnt1 : d.cnt2;
+    // Two levels: this chunk's own level-1 slots; one level: the final slots.
+    const uint64_t slot0 = two_level ? ((uint64_t)chunk << d.p1) : 0ull;
+    uint64_t *__restrict__ okeys = two_level ? d.a_keys + slot0 * cap : d.b_keys;
+    uint32_t *__restrict__ ononces = two_level ? d.a_nonces + slot0 * cap : d.b_nonces;
+    uint32_t *cnt = two_level ? d.cnt1 + slot0 : d.cnt2;
 
     uint32_t pre[16];
 #pragma unroll
@@ -179,27 +186,27 @@ __global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ de
 
 template <int NT, int NPT, bool AGG>
 static cudaError_t launch_hs(const Desc *descs, int nplots, const uint32_t *tile_start,
-                             uint32_t total_tiles, cudaStream_t s)
+                             uint32_t total_tiles, int chunk, cudaStream_t s)
 {
     const size_t smem = sizeof(HashSmem<NT, NPT>);
     auto fn = k_hash_scatter<NT, NPT, AGG>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<total_tiles, NT, smem, s>>>(descs, nplots, tile_start);
+    fn<<<total_tiles, NT, smem, s>>>(descs, nplots, tile_start, chunk);
     return cudaGetLastError();
 }
 
 // AGG (warp-aggregated ranks) pays off when a warp's 32 records fall into
 // few bins; the host picks it from the smallest bin count in the launch.
 cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *tile_start,
-                                uint32_t total_tiles, HashCfg cfg, cudaStream_t s)
+                                uint32_t total_tiles, HashCfg cfg, int chunk, cudaStream_t s)
 {
     if (total_tiles == 0) return cudaSuccess;
     if (cfg.agg)
         return launch_hs<kHashThreads, kHashNoncesPerThread, true>(descs, nplots, tile_start,
-                                                                   total_tiles, s);
+                                                                   total_tiles, chunk, s);
     return launch_hs<kHashThreads, kHashNoncesPerThread, false>(descs, nplots, tile_start,
-                                                                total_tiles, s);
+                                                                total_tiles, chunk, s);
 }
 
 // ------------------------------------------------- hash + direct scatter
@@ -211,12 +218,14 @@ cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *t
 // and L2 while the ALU pipe -- the kernel's bound -- keeps hashing.
 template <int NT, int NPT>
 __global__ void __launch_bounds__(NT) k_hash_direct(const Desc *__restrict__ descs, int nplots,
-                                                    const uint32_t *__restrict__ tile_start)
+                                                    const uint32_t *__restrict__ tile_start,
+                                                    int chunk)
 {
     const int plot = find_plot(tile_start, nplots, blockIdx.x);
     const Desc &d = descs[plot];
-    const uint64_t N = d.N;
-    const uint64_t base = (uint64_t)(blockIdx.x - tile_start[plot]) * (NT * NPT);
+    uint64_t lo, N;  // this chunk's nonces: [lo, N)
+    nonce_chunk(d, chunk, lo, N);
+    const uint64_t base = lo + (uint64_t)(blockIdx.x - tile_start[plot]) * (NT * NPT);
     const int bits = d.p;
     const uint32_t cap = d.cap2;
     uint32_t pre[16];
@@ -254,63 +263,79 @@ __global__ void __launch_bounds__(NT) k_hash_direct(const Desc *__restrict__ des
 }
 
 cudaError_t launch_hash_direct(const Desc *descs, int nplots, const uint32_t *tile_start,
-                               uint32_t total_tiles, cudaStream_t s)
+                               uint32_t total_tiles, int chunk, cudaStream_t s)
 {
     if (total_tiles == 0) return cudaSuccess;
     k_hash_direct<kHashThreads, kHashNoncesPerThread><<<total_tiles, kHashThreads, 0, s>>>(
-        descs, nplots, tile_start);
+        descs, nplots, tile_start, chunk);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------ Table-2 pair hashing
 // Fills hash2 of the Table-2 records {a, b, 0, 0} the sort wrote at their
 // final offsets: a streaming, barrier-free pass (one compression per
-// record, all lanes busy) over [0, total) of each plot, where total is the
-// count the sort's look-back published.  Skips plots whose Table 2 is
-// invalid (capacity exceeded or a wait timed out).
+// record, all lanes busy).  One launch covers one chunk of partitions --
+// the records between the look-back prefixes at the chunk's ends -- so it
+// can run on a second stream while the sort works on the next chunk.  A
+// plot's CTAs stride over its range.  Skips plots whose Table 2 is invalid
+// (capacity exceeded, a wait timed out).
 constexpr int kT2HashThreads = 256;
 constexpr int kT2HashPer = 8;
 
 __global__ void __launch_bounds__(kT2HashThreads) k_t2_hash(const Desc *__restrict__ descs,
                                                             int nplots,
-                                                            const uint32_t *__restrict__ tile_start)
+                                                            const uint32_t *__restrict__ tile_start,
+                                                            int chunk)
 {
     constexpr int NT = kT2HashThreads, PER = kT2HashPer;
     const int plot = find_plot(tile_start, nplots, blockIdx.x);
     const Desc &d = descs[plot];
     if (*d.status & (kStT2Capacity | kStTimeout | kStBadTicket)) return;
-    const uint64_t total = d.t2off[1ull << d.p];
-    const uint64_t base = (uint64_t)(blockIdx.x - tile_start[plot]) * (NT * PER);
-    if (base >= total) return;
+    // Records of this partition chunk: [prefix before its first partition,
+    // inclusive prefix of its last), from the sort's look-back words.
+    const uint64_t np = 1ull << d.p;
+    const uint64_t fa = np * (uint64_t)chunk / (uint64_t)d.pchunks;
+    const uint64_t fb = np * (uint64_t)(chunk + 1) / (uint64_t)d.pchunks;
+    if (fa >= fb) return;
+    const uint64_t w = ld_acquire_u64(d.lb + (fb - 1));
+    if ((w & ~kLbMask) != kLbIncl) return;  // chain broken: status says why
+    const uint64_t lo = fa == 0 ? 0ull : d.t2off[fa];
+    uint64_t hi = w & kLbMask;
+    if (hi > d.t2cap) hi = d.t2cap;
+    const uint32_t me = blockIdx.x - tile_start[plot];
+    const uint32_t ctas = tile_start[plot + 1] - tile_start[plot];
     uint32_t g[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) g[i] = d.pre2[i];
     uint4 *__restrict__ t2 = reinterpret_cast<uint4 *>(d.t2);
-    uint2 ab[PER];
+    for (uint64_t base = lo + (uint64_t)me * (NT * PER); base < hi;
+         base += (uint64_t)ctas * (NT * PER)) {
+        uint2 ab[PER];
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const uint64_t q = base + (uint64_t)j * NT + threadIdx.x;
-        if (q < total) {
-            const uint4 v = t2[q];
-            ab[j] = make_uint2(v.x, v.y);
+        for (int j = 0; j < PER; ++j) {
+            const uint64_t q = base + (uint64_t)j * NT + threadIdx.x;
+            if (q < hi) {
+                const uint4 v = t2[q];
+                ab[j] = make_uint2(v.x, v.y);
+            }
         }
-    }
 #pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const uint64_t q = base + (uint64_t)j * NT + threadIdx.x;
-        if (q < total) {
-            uint32_t h0, h1;
-            b3_finish<true>(g, ab[j].x, ab[j].y, h0, h1);
-            t2[q] = make_uint4(ab[j].x, ab[j].y, h0, h1);
+        for (int j = 0; j < PER; ++j) {
+            const uint64_t q = base + (uint64_t)j * NT + threadIdx.x;
+            if (q < hi) {
+                uint32_t h0, h1;
+                b3_finish<true>(g, ab[j].x, ab[j].y, h0, h1);
+                t2[q] = make_uint4(ab[j].x, ab[j].y, h0, h1);
+            }
         }
     }
 }
 
 cudaError_t launch_t2_hash(const Desc *descs, int nplots, const uint32_t *tile_start,
-                           uint32_t total_tiles, cudaStream_t s)
+                           uint32_t total_tiles, int chunk, cudaStream_t s)
 {
     if (total_tiles == 0) return cudaSuccess;
-    k_t2_hash<<<total_tiles, kT2HashThreads, 0, s>>>(descs, nplots, tile_start);
+    k_t2_hash<<<total_tiles, kT2HashThreads, 0, s>>>(descs, nplots, tile_start, chunk);
     return cudaGetLastError();
 }
 

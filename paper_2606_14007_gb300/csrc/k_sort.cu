@@ -27,7 +27,8 @@ struct Scatter2Smem {
 
 __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__restrict__ descs,
                                                              int nplots,
-                                                             const uint32_t *__restrict__ tile_start)
+                                                             const uint32_t *__restrict__ tile_start,
+                                                             int chunk)
 {
     constexpr int NT = kScatterThreads;
     constexpr int PER = kScatterTile / NT;
@@ -37,10 +38,11 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__rest
     const int plot = find_plot(tile_start, nplots, blockIdx.x);
     const Desc &d = descs[plot];
     const uint32_t local = blockIdx.x - tile_start[plot];
-    const uint32_t c = local / d.chunks1;              // level-1 slot
-    const uint32_t chunk = local - c * d.chunks1;
-    const uint32_t filled = min(d.cnt1[c], d.cap1);
-    const uint32_t start = chunk * (uint32_t)kScatterTile;
+    const uint32_t c = local / d.chunks1;              // level-1 bin of this nonce chunk
+    const uint32_t part = local - c * d.chunks1;       // tile of the slot
+    const uint64_t cs = ((uint64_t)chunk << d.p1) + c; // the slot
+    const uint32_t filled = min(d.cnt1[cs], d.cap1);
+    const uint32_t start = part * (uint32_t)kScatterTile;
     if (start >= filled) return;
     const uint32_t count = min((uint32_t)kScatterTile, filled - start);
     const int p2 = d.p2;
@@ -52,8 +54,8 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__rest
     if (threadIdx.x == 0) {
         mbar_init(&sm.bar, 1);
         mbar_expect_tx(&sm.bar, ncopy * 12u);
-        bulk_g2s(sm.keys, d.a_keys + (uint64_t)c * d.cap1 + start, ncopy * 8u, &sm.bar);
-        bulk_g2s(sm.nonces, d.a_nonces + (uint64_t)c * d.cap1 + start, ncopy * 4u, &sm.bar);
+        bulk_g2s(sm.keys, d.a_keys + cs * d.cap1 + start, ncopy * 8u, &sm.bar);
+        bulk_g2s(sm.nonces, d.a_nonces + cs * d.cap1 + start, ncopy * 4u, &sm.bar);
     }
     for (int b = threadIdx.x; b < nbins; b += NT) sm.hist[b] = 0u;
     __syncthreads();
@@ -125,14 +127,14 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__rest
 }
 
 cudaError_t launch_scatter2(const Desc *descs, int nplots, const uint32_t *tile_start,
-                            uint32_t total_tiles, cudaStream_t s)
+                            uint32_t total_tiles, int chunk, cudaStream_t s)
 {
     if (total_tiles == 0) return cudaSuccess;
     const size_t smem = sizeof(Scatter2Smem);
     cudaError_t e = cudaFuncSetAttribute(k_scatter2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_scatter2<<<total_tiles, kScatterThreads, smem, s>>>(descs, nplots, tile_start);
+    k_scatter2<<<total_tiles, kScatterThreads, smem, s>>>(descs, nplots, tile_start, chunk);
     return cudaGetLastError();
 }
 

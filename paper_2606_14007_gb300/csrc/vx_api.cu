@@ -126,6 +126,8 @@ void fill_desc(const vx_plot *p, Desc *d)
     d->chunks1 = pl.chunks1;
     d->spin_limit = pl.spin_limit;
     d->test_flags = pl.test_flags;
+    d->hchunks = pl.hchunks;
+    d->pchunks = pl.pchunks;
     if (pl.p2 > 0) {
         d->a_keys = reinterpret_cast<uint64_t *>(p->d_t1);
         d->a_nonces = reinterpret_cast<uint32_t *>(p->d_t1 + pl.regionA_keys);
@@ -148,18 +150,87 @@ void fill_desc(const vx_plot *p, Desc *d)
     key_words(p->key, d->key);
 }
 
-// Pair-hash CTAs of a plot: enough for its bound Table-2 capacity (a caller
-// may bind a larger buffer than planned); 0 when the sort hashes the pairs.
-uint32_t pairhash_tiles(const vx_plot *p)
-{
-    if (p->plan.fuse_pair_hash) return 0u;
-    return (uint32_t)((p->t2cap + vx::kPlanT2HashTile - 1) / vx::kPlanT2HashTile);
-}
-
 Desc *dev_desc(vx_plot *p) { return reinterpret_cast<Desc *>(p->d_scratch + p->plan.o_desc); }
 uint32_t *dev_tiles(vx_plot *p) { return reinterpret_cast<uint32_t *>(p->d_scratch + p->plan.o_tiles); }
 
-// Uploads the descriptor and the single-plot tile prefixes if they changed.
+// Tile prefixes (exclusive prefix of per-plot CTA counts) of every launch of
+// a run over plots[0..n), written to h (host) for upload to d (device), and
+// the launch set pointing at d.  Arrays of n + 1 entries in the order
+// staged[8] direct[8] s2[8] pchunk[8] t2h[8] scan part.  Nonce chunk g and
+// partition chunk c exist for a plot while g < its hchunks, c < its pchunks.
+// Pair-hash grids follow the bound Table-2 capacity (a caller may bind a
+// larger buffer than planned) and stride over their records.
+int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, LaunchSet *L)
+{
+    using namespace vx;
+    const int W = n + 1;
+    enum { A_STG = 0, A_DIR = 8, A_S2 = 16, A_PC = 24, A_T2H = 32, A_SCAN = 40, A_PART = 41 };
+    static_assert(A_PART + 1 == vx::kTileArrays, "tile arrays");
+    bool fuse = true;
+    L->G = L->C = 1;
+    L->max_cap2 = 0;
+    L->max_dbits = 1;
+    int min_bits = 64;
+    for (int i = 0; i < n; ++i) {
+        if (!plots[i] || !plots[i]->d_t1) return VX_EINVAL;
+        const Plan &pl = plots[i]->plan;
+        fuse = fuse && pl.fuse_pair_hash;
+        L->G = std::max(L->G, pl.hchunks);
+        L->C = std::max(L->C, pl.pchunks);
+        L->max_cap2 = std::max(L->max_cap2, pl.cap2);
+        L->max_dbits = std::max(L->max_dbits, pl.dbits);
+        if (pl.mode == kScatterStaged) min_bits = std::min(min_bits, pl.p2 > 0 ? pl.p1 : pl.p);
+    }
+    uint64_t acc[vx::kTileArrays] = {};
+    for (int a = 0; a < vx::kTileArrays; ++a) h[a * W] = 0;
+    for (int i = 0; i < n; ++i) {
+        const Plan &pl = plots[i]->plan;
+        uint64_t cnt[vx::kTileArrays] = {};
+        const bool staged = pl.mode == kScatterStaged;
+        for (int g = 0; g < vx::kMaxChunks && g < pl.hchunks; ++g) {
+            cnt[(staged ? A_STG : A_DIR) + g] = pl.tiles_hash;
+            if (staged && pl.p2 > 0) cnt[A_S2 + g] = pl.tiles_s2;
+        }
+        const uint64_t np = 1ull << pl.p;
+        for (int c = 0; c < vx::kMaxChunks && c < pl.pchunks; ++c) {
+            cnt[A_PC + c] = np * (c + 1) / pl.pchunks - np * c / pl.pchunks;
+            if (!fuse) {
+                const uint64_t per = (plots[i]->t2cap / pl.pchunks + kPlanT2HashTile - 1) / kPlanT2HashTile;
+                cnt[A_T2H + c] = per ? per : 1;
+            }
+        }
+        cnt[A_SCAN] = pl.tiles_scan;
+        cnt[A_PART] = pl.tiles_part;
+        for (int a = 0; a < vx::kTileArrays; ++a) {
+            acc[a] += cnt[a];
+            if (acc[a] > 0x7FFFFFFFull) return VX_EINVAL;
+            h[a * W + i + 1] = (uint32_t)acc[a];
+        }
+    }
+    L->n = n;
+    L->agg = min_bits <= kAggMaxBits;
+    L->fuse_pair_hash = fuse;
+    for (int g = 0; g < vx::kMaxChunks; ++g) {
+        L->t_staged[g] = d + (A_STG + g) * W;
+        L->t_direct[g] = d + (A_DIR + g) * W;
+        L->t_s2[g] = d + (A_S2 + g) * W;
+        L->t_pchunk[g] = d + (A_PC + g) * W;
+        L->t_t2h[g] = d + (A_T2H + g) * W;
+        L->n_staged[g] = (uint32_t)acc[A_STG + g];
+        L->n_direct[g] = (uint32_t)acc[A_DIR + g];
+        L->n_s2[g] = (uint32_t)acc[A_S2 + g];
+        L->n_pchunk[g] = (uint32_t)acc[A_PC + g];
+        L->n_t2h[g] = (uint32_t)acc[A_T2H + g];
+    }
+    L->t_scan = d + A_SCAN * W;
+    L->t_part = d + A_PART * W;
+    L->n_scan = (uint32_t)acc[A_SCAN];
+    L->n_part = (uint32_t)acc[A_PART];
+    return VX_OK;
+}
+
+// Uploads the descriptor and the single-plot tile prefixes if they changed
+// and caches the single-plot launch set.
 int upload_desc(vx_plot *p, cudaStream_t s)
 {
     if (!p->desc_dirty) return VX_OK;
@@ -173,16 +244,17 @@ int upload_desc(vx_plot *p, cudaStream_t s)
     fill_desc(p, p->h_stage);
     uint32_t *t = reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(p->h_stage) +
                                                vx::kStageTilesOffset);
-    t[0] = 0; t[1] = p->plan.tiles_staged;   // hash + staged first scatter
-    t[2] = 0; t[3] = p->plan.tiles_direct;   // hash + direct scatter
-    t[4] = 0; t[5] = p->plan.tiles_s2;       // second scatter
-    t[6] = 0; t[7] = p->plan.tiles_part;     // sort / match / sort+match
-    t[8] = 0; t[9] = p->plan.tiles_scan;     // Table-1 offset scan
-    t[10] = 0; t[11] = pairhash_tiles(p);    // pair hash over the bound Table-2 capacity
+    vx_plot *one[1] = {p};
+    if (build_tiles(one, 1, t, dev_tiles(p), &p->single) != VX_OK) {
+        set_err(p, "grid too large");
+        return VX_EINVAL;
+    }
+    p->single.descs = dev_desc(p);
     // Only the host-filled part: pre1/pre2 are derived on the device by the
     // key-setup kernel and must survive a re-upload after vx_plot_bind.
     VX_TRY(p, cudaMemcpyAsync(dev_desc(p), p->h_stage, offsetof(Desc, pre1), cudaMemcpyHostToDevice, s));
-    VX_TRY(p, cudaMemcpyAsync(dev_tiles(p), t, 12 * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    VX_TRY(p, cudaMemcpyAsync(dev_tiles(p), t, vx::kTileArrays * 2 * sizeof(uint32_t),
+                              cudaMemcpyHostToDevice, s));
     VX_TRY(p, cudaEventRecord(p->ev_stage, s));
     p->ev_pending = true;
     p->desc_dirty = false;
@@ -219,101 +291,138 @@ std::string status_text(uint32_t st)
     return s;
 }
 
-// Kernel sequences.  ev (nullable, vx::kProfEvents entries) receives an
-// event before the first kernel and after each traced kernel slot; slots a
-// path skips record back to back (zero time).
-inline void rec(cudaEvent_t *ev, int i, cudaStream_t s)
+// ----------------------------------------------------- kernel sequences
+// Tracing ids (vx_kernel_name order).
+enum { KID_SETUP = 0, KID_STAGED, KID_DIRECT, KID_S2, KID_SCAN, KID_SORT, KID_SCANP, KID_MATCH,
+       KID_SORTMATCH, KID_PAIRHASH };
+
+int tr_begin(const vx::Trace *T, int kid, cudaStream_t s)
 {
-    if (ev) cudaEventRecord(ev[i], s);
+    if (!T || *T->used >= vx::kProfLaunches) return -1;
+    const int i = (*T->used)++;
+    T->kid[i] = (int8_t)kid;
+    cudaEventRecord(T->ev[2 * i], s);
+    return i;
 }
 
-// Traced kernel slots: 0 key_setup, 1 hash_staged, 2 hash_direct,
-// 3 scatter2, 4 scan_counts, 5 sort, 6 scan_pairs, 7 match, 8 sortmatch,
-// 9 pairhash; event k+1 follows kernel k.
-//
-// Key setup, hashing + bucketing, Table-1 offsets (slots 0..4).
-cudaError_t launch_front(const LaunchSet &L, cudaStream_t s, cudaEvent_t *ev)
+void tr_end(const vx::Trace *T, int i, cudaStream_t s)
 {
-    cudaError_t e;
-    rec(ev, 0, s);
-    if ((e = vx::launch_key_setup(L.descs, L.n, s)) != cudaSuccess) return e;
-    rec(ev, 1, s);
-    if ((e = vx::launch_hash_scatter(L.descs, L.n, L.t_hash, L.n_hash, vx::HashCfg{L.agg}, s)) !=
-        cudaSuccess)
-        return e;
-    rec(ev, 2, s);
-    if ((e = vx::launch_hash_direct(L.descs, L.n, L.t_direct, L.n_direct, s)) != cudaSuccess) return e;
-    rec(ev, 3, s);
-    if (L.n_s2 && (e = vx::launch_scatter2(L.descs, L.n, L.t_s2, L.n_s2, s)) != cudaSuccess) return e;
-    rec(ev, 4, s);
-    if ((e = vx::launch_scan_counts(L.descs, L.n, L.t_scan, L.n_scan, s)) != cudaSuccess) return e;
-    rec(ev, 5, s);
+    if (T && i >= 0) cudaEventRecord(T->ev[2 * i + 1], s);
+}
+
+#define VX_LAUNCH(kid, st, call)                 \
+    do {                                         \
+        const int i_ = tr_begin(T, kid, st);     \
+        const cudaError_t e_ = (call);           \
+        tr_end(T, i_, st);                       \
+        if (e_ != cudaSuccess) return e_;        \
+    } while (0)
+
+// Key setup, hashing + bucketing, Table-1 offsets.  With an aux stream the
+// second scatter level of nonce chunk g runs on it while chunk g+1 hashes.
+cudaError_t launch_front(const LaunchSet &L, const vx::Lanes &ln, const vx::Trace *T)
+{
+    const cudaStream_t A = ln.main, B = ln.aux;
+    VX_LAUNCH(KID_SETUP, A, vx::launch_key_setup(L.descs, L.n, A));
+    bool any_s2 = false;
+    for (int g = 0; g < L.G; ++g) any_s2 = any_s2 || L.n_s2[g] > 0;
+    const bool ov = B && L.G > 1 && any_s2;
+    for (int g = 0; g < L.G; ++g) {
+        if (L.n_staged[g])
+            VX_LAUNCH(KID_STAGED, A, vx::launch_hash_scatter(L.descs, L.n, L.t_staged[g], L.n_staged[g],
+                                                             vx::HashCfg{L.agg}, g, A));
+        if (L.n_direct[g])
+            VX_LAUNCH(KID_DIRECT, A, vx::launch_hash_direct(L.descs, L.n, L.t_direct[g], L.n_direct[g], g, A));
+        if (L.n_s2[g]) {
+            if (ov) {
+                cudaEventRecord(ln.sync[g], A);
+                cudaStreamWaitEvent(B, ln.sync[g], 0);
+                VX_LAUNCH(KID_S2, B, vx::launch_scatter2(L.descs, L.n, L.t_s2[g], L.n_s2[g], g, B));
+            } else {
+                VX_LAUNCH(KID_S2, A, vx::launch_scatter2(L.descs, L.n, L.t_s2[g], L.n_s2[g], g, A));
+            }
+        }
+    }
+    if (ov) {
+        cudaEventRecord(ln.sync[vx::kMaxChunks], B);
+        cudaStreamWaitEvent(A, ln.sync[vx::kMaxChunks], 0);
+    }
+    VX_LAUNCH(KID_SCAN, A, vx::launch_scan_counts(L.descs, L.n, L.t_scan, L.n_scan, A));
     return cudaSuccess;
 }
 
-// Split path, Table 1: front + partition sort (slot 5).
-cudaError_t launch_table1(const LaunchSet &L, cudaStream_t s, cudaEvent_t *ev = nullptr)
+// Split path, Table 1: front + partition sort (Table 1 and pair counts).
+cudaError_t launch_table1(const LaunchSet &L, const vx::Lanes &ln, const vx::Trace *T)
 {
-    cudaError_t e = launch_front(L, s, ev);
+    const cudaError_t e = launch_front(L, ln, T);
     if (e != cudaSuccess) return e;
-    e = vx::launch_sort(L.descs, L.n, L.t_part, L.n_part, s, L.max_cap2, L.max_dbits);
-    rec(ev, 6, s);
-    return e;
+    const cudaStream_t A = ln.main;
+    VX_LAUNCH(KID_SORT, A, vx::launch_sort(L.descs, L.n, L.t_part, L.n_part, A, L.max_cap2, L.max_dbits));
+    return cudaSuccess;
 }
 
-// Split path, Table 2: pair-offset scan + match (slots 6, 7).
-cudaError_t launch_match_seq(const LaunchSet &L, cudaStream_t s, cudaEvent_t *ev = nullptr)
+// Split path, Table 2: pair-offset scan + match.
+cudaError_t launch_match_seq(const LaunchSet &L, cudaStream_t A, const vx::Trace *T)
 {
-    cudaError_t e;
-    if ((e = vx::launch_scan_pairs(L.descs, L.n, s)) != cudaSuccess) return e;
-    rec(ev, 7, s);
-    e = vx::launch_match(L.descs, L.n, L.t_part, L.n_part, s, L.max_cap2);
-    rec(ev, 8, s);
-    rec(ev, 9, s);
-    rec(ev, 10, s);
-    return e;
+    VX_LAUNCH(KID_SCANP, A, vx::launch_scan_pairs(L.descs, L.n, A));
+    VX_LAUNCH(KID_MATCH, A, vx::launch_match(L.descs, L.n, L.t_part, L.n_part, A, L.max_cap2));
+    return cudaSuccess;
 }
 
-// One-pass path: front + sort+match (slot 8) + streaming pair hash (slot 9).
-cudaError_t launch_fused(const LaunchSet &L, cudaStream_t s, cudaEvent_t *ev = nullptr)
+// One-pass path: front, then sort + match per partition chunk (ticket order
+// chains the chunks' Table-2 offsets), and the pair hash of chunk c on the
+// aux stream while chunk c+1 sorts.
+cudaError_t launch_fused(const LaunchSet &L, const vx::Lanes &ln, const vx::Trace *T)
 {
-    cudaError_t e = launch_front(L, s, ev);
+    cudaError_t e = launch_front(L, ln, T);
     if (e != cudaSuccess) return e;
-    rec(ev, 6, s);
-    rec(ev, 7, s);
-    rec(ev, 8, s);
-    e = vx::launch_sortmatch(L.descs, L.n, L.t_part, L.n_part, s, L.max_cap2, L.max_dbits,
-                             L.fuse_pair_hash);
-    if (e != cudaSuccess) return e;
-    rec(ev, 9, s);
-    if (!L.fuse_pair_hash) e = vx::launch_t2_hash(L.descs, L.n, L.t_t2h, L.n_t2h, s);
-    rec(ev, 10, s);
-    return e;
+    const cudaStream_t A = ln.main, B = ln.aux_lo;
+    const bool ph = !L.fuse_pair_hash;
+    const bool ov = B && L.C > 1 && ph;
+    for (int c = 0; c < L.C; ++c) {
+        if (L.n_pchunk[c])
+            VX_LAUNCH(KID_SORTMATCH, A, vx::launch_sortmatch(L.descs, L.n, L.t_pchunk[c], L.n_pchunk[c], A,
+                                                             L.max_cap2, L.max_dbits, L.fuse_pair_hash));
+        if (ph && L.n_t2h[c]) {
+            if (ov) {
+                cudaEventRecord(ln.sync[vx::kMaxChunks + 1 + c], A);
+                cudaStreamWaitEvent(B, ln.sync[vx::kMaxChunks + 1 + c], 0);
+                VX_LAUNCH(KID_PAIRHASH, B, vx::launch_t2_hash(L.descs, L.n, L.t_t2h[c], L.n_t2h[c], c, B));
+            } else {
+                VX_LAUNCH(KID_PAIRHASH, A, vx::launch_t2_hash(L.descs, L.n, L.t_t2h[c], L.n_t2h[c], c, A));
+            }
+        }
+    }
+    if (ov) {
+        cudaEventRecord(ln.sync[2 * vx::kMaxChunks + 1], B);
+        cudaStreamWaitEvent(A, ln.sync[2 * vx::kMaxChunks + 1], 0);
+    }
+    return cudaSuccess;
 }
 
-LaunchSet single_set(vx_plot *p)
+// Lanes of a single plot: its aux stream when its plan pipelines.
+int plot_lanes(vx_plot *p, cudaStream_t s, vx::Lanes *ln)
 {
-    LaunchSet L;
-    L.descs = dev_desc(p);
-    L.n = 1;
-    uint32_t *t = dev_tiles(p);
-    L.t_hash = t;
-    L.t_direct = t + 2;
-    L.t_s2 = t + 4;
-    L.t_part = t + 6;
-    L.t_scan = t + 8;
-    L.t_t2h = t + 10;
-    L.n_hash = p->plan.tiles_staged;
-    L.n_direct = p->plan.tiles_direct;
-    L.n_scan = p->plan.tiles_scan;
-    L.fuse_pair_hash = p->plan.fuse_pair_hash;
-    L.n_t2h = pairhash_tiles(p);
-    L.n_s2 = p->plan.tiles_s2;
-    L.n_part = p->plan.tiles_part;
-    L.agg = p->plan.agg;
-    L.max_cap2 = p->plan.cap2;
-    L.max_dbits = p->plan.dbits;
-    return L;
+    ln->main = s;
+    ln->aux = ln->aux_lo = nullptr;
+    ln->sync = p->sync_ev;
+    if (p->plan.hchunks > 1 || p->plan.pchunks > 1) {
+        if (!p->aux) VX_TRY(p, vx::make_lanes(&p->aux, &p->aux_lo, p->sync_ev));
+        ln->aux = p->aux;
+        ln->aux_lo = p->aux_lo;
+    }
+    return VX_OK;
+}
+
+// Trace of the plot's next run, if tracing is on and a slot is left.
+vx::Trace *next_trace(vx_plot *p, vx::Trace *T)
+{
+    if (p->prof_slots <= 0 || p->prof_runs >= p->prof_slots) return nullptr;
+    const int r = p->prof_runs;
+    T->ev = p->prof_ev + (size_t)r * vx::kProfLaunches * 2;
+    T->kid = p->prof_kid + (size_t)r * vx::kProfLaunches;
+    T->used = p->prof_used + r;
+    return T;
 }
 
 }  // namespace
@@ -436,13 +545,11 @@ int vx_table1(vx_plot *p, void *stream)
     int rc = ensure_memory(p);
     if (rc) return rc;
     if ((rc = upload_desc(p, s))) return rc;
-    cudaEvent_t *ev = nullptr;
-    p->prof_cur = -1;
-    if (p->prof_slots > 0 && p->prof_runs < p->prof_slots) {
-        p->prof_cur = p->prof_next++;
-        ev = p->prof_ev + (size_t)p->prof_cur * vx::kProfEvents;
-    }
-    cudaError_t e = launch_table1(single_set(p), s, ev);
+    vx::Trace tr;
+    const vx::Trace *T = next_trace(p, &tr);
+    p->prof_cur = T ? p->prof_runs : -1;  // vx_match closes this traced run
+    vx::Lanes ln{s, nullptr, nullptr, p->sync_ev};
+    cudaError_t e = launch_table1(p->single, ln, T);
     if (e != cudaSuccess) return cuda_fail(p, "Table-1 launch", e);
     p->stage = 1;
     p->t2_known = false;
@@ -461,13 +568,14 @@ int vx_match(vx_plot *p, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     int rc = upload_desc(p, s);
     if (rc) return rc;
-    cudaEvent_t *ev = nullptr;
-    if (p->prof_cur >= 0) {
-        ev = p->prof_ev + (size_t)p->prof_cur * vx::kProfEvents;
-        p->prof_cur = -1;
+    vx::Trace tr;
+    const vx::Trace *T = nullptr;
+    if (p->prof_cur >= 0 && p->prof_cur == p->prof_runs) {
+        T = next_trace(p, &tr);
         p->prof_runs += 1;
     }
-    cudaError_t e = launch_match_seq(single_set(p), s, ev);
+    p->prof_cur = -1;
+    cudaError_t e = launch_match_seq(p->single, s, T);
     if (e != cudaSuccess) return cuda_fail(p, "match launch", e);
     p->stage = 2;
     p->t2_known = false;
@@ -483,13 +591,13 @@ int vx_plot_run(vx_plot *p, void *stream)
     int rc = ensure_memory(p);
     if (rc) return rc;
     if ((rc = upload_desc(p, s))) return rc;
-    cudaEvent_t *ev = nullptr;
+    vx::Lanes ln;
+    if ((rc = plot_lanes(p, s, &ln))) return rc;
+    vx::Trace tr;
+    const vx::Trace *T = next_trace(p, &tr);
+    if (T) p->prof_runs += 1;
     p->prof_cur = -1;
-    if (p->prof_slots > 0 && p->prof_runs < p->prof_slots) {
-        ev = p->prof_ev + (size_t)p->prof_next++ * vx::kProfEvents;
-        p->prof_runs += 1;
-    }
-    cudaError_t e = launch_fused(single_set(p), s, ev);
+    cudaError_t e = launch_fused(p->single, ln, T);
     if (e != cudaSuccess) return cuda_fail(p, "plot launch", e);
     p->stage = 2;
     p->t2_known = false;
@@ -574,6 +682,7 @@ void vx_plot_destroy(vx_plot *p)
     if (p->h_stage) cudaFreeHost(p->h_stage);
     if (p->ev_stage) cudaEventDestroy(p->ev_stage);
     vx_plot_profile(p, 0);
+    if (p->aux) vx::free_lanes(p->aux, p->aux_lo, p->sync_ev);
     delete p;
 }
 
@@ -602,24 +711,43 @@ int vx_plot_kernel_mask(const vx_plot *p, int split, uint32_t *mask)
 
 int vx_plot_profile(vx_plot *p, int runs)
 {
-    if (!p || runs < 0 || runs > 100000) return VX_EINVAL;
+    if (!p || runs < 0 || runs > 10000) return VX_EINVAL;
     if (p->prof_ev) {
         if (p->have_last) cudaStreamSynchronize(p->last);
-        for (int i = 0; i < p->prof_slots * vx::kProfEvents; ++i) cudaEventDestroy(p->prof_ev[i]);
+        for (int i = 0; i < p->prof_slots * vx::kProfLaunches * 2; ++i) cudaEventDestroy(p->prof_ev[i]);
         delete[] p->prof_ev;
+        delete[] p->prof_kid;
+        delete[] p->prof_used;
         p->prof_ev = nullptr;
+        p->prof_kid = nullptr;
+        p->prof_used = nullptr;
     }
-    p->prof_slots = p->prof_next = p->prof_runs = 0;
+    p->prof_slots = p->prof_runs = 0;
     p->prof_cur = -1;
     if (runs == 0) return VX_OK;
-    p->prof_ev = new (std::nothrow) cudaEvent_t[(size_t)runs * vx::kProfEvents]();
-    if (!p->prof_ev) return VX_ENOMEM;
-    for (int i = 0; i < runs * vx::kProfEvents; ++i) {
+    const size_t nev = (size_t)runs * vx::kProfLaunches * 2;
+    p->prof_ev = new (std::nothrow) cudaEvent_t[nev]();
+    p->prof_kid = new (std::nothrow) int8_t[(size_t)runs * vx::kProfLaunches];
+    p->prof_used = new (std::nothrow) int[runs]();
+    if (!p->prof_ev || !p->prof_kid || !p->prof_used) {
+        delete[] p->prof_ev;
+        delete[] p->prof_kid;
+        delete[] p->prof_used;
+        p->prof_ev = nullptr;
+        p->prof_kid = nullptr;
+        p->prof_used = nullptr;
+        return VX_ENOMEM;
+    }
+    for (size_t i = 0; i < nev; ++i) {
         cudaError_t e = cudaEventCreate(&p->prof_ev[i]);
         if (e != cudaSuccess) {
-            for (int j = 0; j < i; ++j) cudaEventDestroy(p->prof_ev[j]);
+            for (size_t j = 0; j < i; ++j) cudaEventDestroy(p->prof_ev[j]);
             delete[] p->prof_ev;
+            delete[] p->prof_kid;
+            delete[] p->prof_used;
             p->prof_ev = nullptr;
+            p->prof_kid = nullptr;
+            p->prof_used = nullptr;
             return cuda_fail(p, "cudaEventCreate", e);
         }
     }
@@ -634,12 +762,13 @@ int vx_plot_profile_read(vx_plot *p, double *ms, int cap, int *nkernels, int *nr
     if (nkernels) *nkernels = vx::kProfKernels;
     if (nruns) *nruns = p->prof_runs;
     for (int r = 0; r < p->prof_runs; ++r) {
-        cudaEvent_t *ev = p->prof_ev + (size_t)r * vx::kProfEvents;
-        for (int k = 0; k < vx::kProfKernels; ++k) {
-            VX_TRY(p, cudaEventSynchronize(ev[k + 1]));
+        const cudaEvent_t *ev = p->prof_ev + (size_t)r * vx::kProfLaunches * 2;
+        const int8_t *kid = p->prof_kid + (size_t)r * vx::kProfLaunches;
+        for (int i = 0; i < p->prof_used[r]; ++i) {
+            VX_TRY(p, cudaEventSynchronize(ev[2 * i + 1]));
             float t = 0.f;
-            VX_TRY(p, cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
-            ms[k] += t;
+            VX_TRY(p, cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]));
+            if (kid[i] >= 0 && kid[i] < vx::kProfKernels) ms[kid[i]] += t;
         }
     }
     return VX_OK;
@@ -693,6 +822,8 @@ struct BatchEntry {
     size_t ws_bytes = 0;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t aux = nullptr, aux_lo = nullptr;  // other branches of the recorded graph
+    cudaEvent_t sync[vx::kSyncEvents] = {};
 };
 
 std::mutex g_batch_mu;
@@ -714,6 +845,7 @@ void drop_batch(BatchEntry *b)
 {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    vx::free_lanes(b->aux, b->aux_lo, b->sync);
     cudaFree(b->d_ws);
     cudaFreeHost(b->h_ws);
     delete b;
@@ -726,67 +858,48 @@ namespace vx {
 size_t batch_ws_bytes(int n)
 {
     const size_t o_tiles = ((size_t)n * sizeof(Desc) + 255) & ~(size_t)255;
-    return o_tiles + 6 * (size_t)(n + 1) * 4;
+    return o_tiles + (size_t)kTileArrays * (size_t)(n + 1) * 4;
 }
 
 int batch_prepare(vx_plot *const *plots, int n, uint8_t *h_ws, uint8_t *d_ws, LaunchSet *L)
 {
     const size_t o_tiles = ((size_t)n * sizeof(Desc) + 255) & ~(size_t)255;
     Desc *hd = reinterpret_cast<Desc *>(h_ws);
-    uint32_t *th = reinterpret_cast<uint32_t *>(h_ws + o_tiles);
-    uint32_t *tdir = th + (n + 1), *ts = tdir + (n + 1), *tp = ts + (n + 1);
-    uint32_t *tsc = tp + (n + 1), *tt2 = tsc + (n + 1);
-    th[0] = tdir[0] = ts[0] = tp[0] = tsc[0] = tt2[0] = 0;
-    bool fuse = true;
-    for (int i = 0; i < n; ++i)
-        if (!plots[i] || !plots[i]->plan.fuse_pair_hash) fuse = false;
-    L->max_cap2 = 0;
-    L->max_dbits = 1;
-    int min_bits = 64;
-    uint64_t sh = 0, sd = 0, ss = 0, sp = 0, ssc = 0, st2 = 0;
     for (int i = 0; i < n; ++i) {
         if (!plots[i] || !plots[i]->d_t1) return VX_EINVAL;
-        const Plan &pl = plots[i]->plan;
         fill_desc(plots[i], hd + i);
-        sh += pl.tiles_staged;
-        sd += pl.tiles_direct;
-        ss += pl.tiles_s2;
-        sp += pl.tiles_part;
-        ssc += pl.tiles_scan;
-        st2 += fuse ? 0u : pairhash_tiles(plots[i]);
-        if (sh > 0x7FFFFFFFull || sd > 0x7FFFFFFFull || ss > 0x7FFFFFFFull || sp > 0x7FFFFFFFull ||
-            ssc > 0x7FFFFFFFull || st2 > 0x7FFFFFFFull)
-            return VX_EINVAL;
-        tsc[i + 1] = (uint32_t)ssc;
-        tt2[i + 1] = (uint32_t)st2;
-        th[i + 1] = (uint32_t)sh;
-        tdir[i + 1] = (uint32_t)sd;
-        ts[i + 1] = (uint32_t)ss;
-        tp[i + 1] = (uint32_t)sp;
-        L->max_cap2 = std::max(L->max_cap2, pl.cap2);
-        L->max_dbits = std::max(L->max_dbits, pl.dbits);
-        if (pl.mode == kScatterStaged) min_bits = std::min(min_bits, pl.p2 > 0 ? pl.p1 : pl.p);
     }
-    L->agg = min_bits <= kAggMaxBits;
+    const int rc = build_tiles(plots, n, reinterpret_cast<uint32_t *>(h_ws + o_tiles),
+                               reinterpret_cast<const uint32_t *>(d_ws + o_tiles), L);
     L->descs = reinterpret_cast<Desc *>(d_ws);
-    L->n = n;
-    L->t_hash = reinterpret_cast<uint32_t *>(d_ws + o_tiles);
-    L->t_direct = L->t_hash + (n + 1);
-    L->t_s2 = L->t_direct + (n + 1);
-    L->t_part = L->t_s2 + (n + 1);
-    L->t_scan = L->t_part + (n + 1);
-    L->t_t2h = L->t_scan + (n + 1);
-    L->n_hash = th[n];
-    L->n_direct = tdir[n];
-    L->n_scan = tsc[n];
-    L->n_t2h = tt2[n];
-    L->fuse_pair_hash = fuse;
-    L->n_s2 = ts[n];
-    L->n_part = tp[n];
-    return VX_OK;
+    return rc;
 }
 
-cudaError_t launch_plot_seq(const LaunchSet &L, cudaStream_t s) { return launch_fused(L, s); }
+cudaError_t launch_plot_seq(const LaunchSet &L, const Lanes &lanes)
+{
+    return launch_fused(L, lanes, nullptr);
+}
+
+cudaError_t make_lanes(cudaStream_t *aux, cudaStream_t *aux_lo, cudaEvent_t *sync)
+{
+    int lo = 0, hi = 0;  // numerically lower = higher priority
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(aux, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(aux_lo, cudaStreamNonBlocking, lo);
+    for (int i = 0; i < kSyncEvents && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&sync[i], cudaEventDisableTiming);
+    return e;
+}
+
+void free_lanes(cudaStream_t aux, cudaStream_t aux_lo, cudaEvent_t *sync)
+{
+    if (aux) cudaStreamSynchronize(aux);
+    if (aux_lo) cudaStreamSynchronize(aux_lo);
+    for (int i = 0; i < kSyncEvents; ++i)
+        if (sync[i]) cudaEventDestroy(sync[i]);
+    if (aux) cudaStreamDestroy(aux);
+    if (aux_lo) cudaStreamDestroy(aux_lo);
+}
 
 void mark_issued(vx_plot *const *plots, int n, cudaStream_t s)
 {
@@ -833,10 +946,12 @@ extern "C" int vx_plot_batch(vx_plot *const *plots, int n, void *stream)
         // The workspace is uploaded once; replays of the graph reuse it.
         cudaError_t e = cudaMemcpy(b->d_ws, b->h_ws, b->ws_bytes, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = vx::make_lanes(&b->aux, &b->aux_lo, b->sync);
         cudaGraph_t g = nullptr;
         if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e1 = vx::launch_plot_seq(L, b->cap_stream);
+            const vx::Lanes ln{b->cap_stream, b->aux, b->aux_lo, b->sync};
+            cudaError_t e1 = vx::launch_plot_seq(L, ln);
             e = cudaStreamEndCapture(b->cap_stream, &g);
             if (e == cudaSuccess) e = e1;
         }

@@ -16,7 +16,7 @@ constexpr int kMaxK = 32;                // u32 nonces
 constexpr int kMaxCoarseBits = 10;       // first scatter level, <= 1024 bins
 constexpr int kMaxFineBits = 10;         // second scatter level, <= 1024 bins
 constexpr int kScatterTile = 4096;       // records per CTA in the second scatter level
-constexpr int kScatterThreads = 512;
+constexpr int kScatterThreads = 256;
 constexpr int kSortThreads = 256;
 constexpr int kMatchThreads = 256;
 constexpr int kMaxSortDigitBits = 13;    // counting-sort digit of the partition sort
@@ -47,13 +47,16 @@ struct Desc {
     uint32_t cap1;       // records per level-1 slot (p2 > 0 only)
     uint32_t cap2;       // records per level-2 slot (final partitions)
     uint32_t chunks1;    // scatter-2 CTAs per level-1 slot = ceil(cap1 / tile)
+                         // level-1 slots: [hchunks][2^p1] of cap1 records each
     uint32_t spin_limit; // polls before a device-side wait gives up
     uint32_t test_flags; // vx_opts.test_flags (fault injection)
-    uint64_t *a_keys;    // level-1 slots, SoA: key64 [2^p1 * cap1]
-    uint32_t *a_nonces;  //                      nonce [2^p1 * cap1]
+    int32_t hchunks;     // nonce chunks (hash / second-scatter pipeline); level-1 slots per chunk
+    int32_t pchunks;     // partition chunks (sort / pair-hash pipeline)
+    uint64_t *a_keys;    // level-1 slots, SoA: key64 [hchunks * 2^p1 * cap1]
+    uint32_t *a_nonces;  //                      nonce [hchunks * 2^p1 * cap1]
     uint64_t *b_keys;    // level-2 slots, SoA: key64 [2^p * cap2]
     uint32_t *b_nonces;  //                      nonce [2^p * cap2]
-    uint32_t *cnt1;      // [2^p1] level-1 fill counters
+    uint32_t *cnt1;      // [hchunks * 2^p1] level-1 fill counters
     uint32_t *cnt2;      // [2^p]  level-2 fill counters
     uint64_t *t1off;     // [2^p + 1] Table-1 record offset of each partition
     uint64_t *pairs;     // [2^p] Table-2 pairs of each partition
@@ -69,6 +72,13 @@ struct Desc {
     uint32_t pre1[16];   // Table-1 hash state after round-1 columns 1..3
     uint32_t pre2[16];   // pair-hash state after round-1 columns 1..3
 };
+
+// Nonces [lo, hi) of chunk `chunk` of a plot (chunks split 2^K evenly).
+__device__ __forceinline__ void nonce_chunk(const Desc &d, int chunk, uint64_t &lo, uint64_t &hi)
+{
+    lo = d.N / (uint64_t)d.hchunks * (uint64_t)chunk;
+    hi = d.N / (uint64_t)d.hchunks * (uint64_t)(chunk + 1);
+}
 
 // Maps a CTA's global tile index to (plot, local tile) through an exclusive
 // prefix of per-plot tile counts (batch launches group many plots).
@@ -434,20 +444,22 @@ struct HashCfg {
     bool agg;     // warp-aggregated histogram (few first-level bins)
 };
 cudaError_t launch_key_setup(Desc *descs, int nplots, cudaStream_t s);
+// Hash kernels and the second scatter level take one nonce chunk (of
+// Desc::hchunks); the pair hash takes one partition chunk (of Desc::pchunks).
 cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *tile_start,
-                                uint32_t total_tiles, HashCfg cfg, cudaStream_t s);
+                                uint32_t total_tiles, HashCfg cfg, int chunk, cudaStream_t s);
 cudaError_t launch_hash_direct(const Desc *descs, int nplots, const uint32_t *tile_start,
-                               uint32_t total_tiles, cudaStream_t s);
+                               uint32_t total_tiles, int chunk, cudaStream_t s);
 cudaError_t launch_sortmatch(const Desc *descs, int nplots, const uint32_t *tile_start,
                              uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits,
                              bool fused_hash);
 cudaError_t launch_t2_hash(const Desc *descs, int nplots, const uint32_t *tile_start,
-                           uint32_t total_tiles, cudaStream_t s);
+                           uint32_t total_tiles, int chunk, cudaStream_t s);
 constexpr uint64_t kT2HashTile = 256 * 8;  // Table-2 records per pair-hash CTA
 size_t sortmatch_smem_bytes(uint32_t cap, int dbits);
 uint32_t sortmatch_max_cap();  // largest slot the sort keeps in registers
 cudaError_t launch_scatter2(const Desc *descs, int nplots, const uint32_t *tile_start,
-                            uint32_t total_tiles, cudaStream_t s);
+                            uint32_t total_tiles, int chunk, cudaStream_t s);
 cudaError_t launch_scan_counts(const Desc *descs, int nplots, const uint32_t *tile_start,
                                uint32_t total_tiles, cudaStream_t s);
 constexpr uint32_t kScanChunk = 4096;      // counters per CTA of the Table-1 offset scan

@@ -36,6 +36,8 @@ struct Plan {
     int mode;                              // kScatterStaged or kScatterDirect
     uint32_t test_flags, spin_limit;
     bool fuse_pair_hash;
+    int hchunks;                           // nonce chunks of the hash / second-scatter pipeline
+    int pchunks;                           // partition chunks of the sort / pair-hash pipeline
     uint64_t N, D, t2cap;
     uint32_t cap1, cap2, chunks1;
     bool agg;
@@ -102,12 +104,17 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, std::string *why, 
         return VX_EINVAL;
     }
     P.test_flags = opts.test_flags;
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 6; ++i)
         if (opts.reserved[i]) {
             *why = "reserved vx_opts fields must be zero";
             return VX_EINVAL;
         }
     P.fuse_pair_hash = opts.fuse_pair_hash != 0;
+    const uint32_t pc = opts.pipeline_chunks;
+    if (pc != 0 && pc != 1 && pc != 2 && pc != 4 && pc != 8) {
+        *why = "pipeline_chunks must be 0, 1, 2, 4 or 8";
+        return VX_EINVAL;
+    }
     // ~1 us per poll: ~4 s in normal use (never reached unless a partition
     // fails to publish), ~4 ms when a test withholds a prefix on purpose.
     P.spin_limit = opts.test_flags ? (1u << 12) : (1u << 22);
@@ -133,6 +140,17 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, std::string *why, 
         *why = "coarse_bits leaves a scatter level wider than 10 bits";
         return VX_EINVAL;
     }
+    // Pipeline chunks, only where a second kernel exists to overlap (the
+    // second scatter level; the separate pair hash).  Off unless asked for:
+    // measured on GB300 at K=31 it does not pay, because each kernel of a
+    // pair alone fills an SM's register file (the latency-bound sort needs
+    // four resident CTAs, the ALU-bound hashes need ~24 warps), so the two
+    // streams take turns instead of sharing SMs.
+    const int want = pc == 0 ? 1 : (int)pc;
+    P.hchunks = (P.mode == kScatterStaged && P.p2 > 0) ? want : 1;
+    while (P.hchunks > 1 && ((1ull << K) < (uint64_t)P.hchunks)) P.hchunks >>= 1;
+    P.pchunks = P.fuse_pair_hash ? 1 : want;
+    while (P.pchunks > 1 && (1ull << P.p) < (uint64_t)P.pchunks) P.pchunks >>= 1;
     const double avg2 = (double)P.N / (double)(1ull << P.p);
     uint64_t cap2 = P.p == 0 ? round_up(P.N, 4) : slot_capacity(avg2, slack);
     if (cap2 > round_up(P.N, 4)) cap2 = round_up(P.N, 4);
@@ -142,9 +160,9 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, std::string *why, 
     }
     P.cap2 = (uint32_t)cap2;
     if (P.p2 > 0) {
-        const double avg1 = (double)P.N / (double)(1ull << P.p1);
+        const double avg1 = (double)P.N / (double)P.hchunks / (double)(1ull << P.p1);
         uint64_t cap1 = P.p1 == 0 ? round_up(P.N, 4) : slot_capacity(avg1, slack);
-        if (cap1 > round_up(P.N, 4)) cap1 = round_up(P.N, 4);
+        if (cap1 > round_up(P.N / P.hchunks, 4)) cap1 = round_up(P.N / P.hchunks, 4);
         if (cap1 > 0xFFFFFF00ull) {
             *why = "first-level slot too large";
             return VX_EINVAL;
@@ -165,17 +183,19 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, std::string *why, 
         P.t2cap = round_up((uint64_t)std::ceil(E + 24.0 * std::sqrt(E) + 4096.0), 256);
     }
     // Grids (tile sizes are the kernels' compile-time tiles).
-    P.tiles_hash = (uint32_t)((P.N + kPlanHashTile - 1) / kPlanHashTile);
+    // Grids per chunk (a chunk of the hash covers 2^K / hchunks nonces).
+    P.tiles_hash = (uint32_t)((P.N / P.hchunks + kPlanHashTile - 1) / kPlanHashTile);
     P.tiles_staged = P.mode == kScatterStaged ? P.tiles_hash : 0u;
     P.tiles_direct = P.mode == kScatterDirect ? P.tiles_hash : 0u;
     P.tiles_s2 = P.p2 > 0 ? (uint32_t)(((uint64_t)1 << P.p1) * P.chunks1) : 0u;
     P.tiles_part = (uint32_t)(1ull << P.p);
     P.tiles_scan = (uint32_t)(((1ull << P.p) + kPlanScanChunk - 1) / kPlanScanChunk);
-    P.tiles_t2h = (uint32_t)((P.t2cap + kPlanT2HashTile - 1) / kPlanT2HashTile);
+    P.tiles_t2h = (uint32_t)((P.t2cap / P.pchunks + kPlanT2HashTile - 1) / kPlanT2HashTile);
+    if (P.tiles_t2h == 0) P.tiles_t2h = 1;
 
     // Slot regions (SoA: key64 array, then nonce array).
     if (P.p2 > 0) {
-        const uint64_t recs = ((uint64_t)1 << P.p1) * P.cap1;
+        const uint64_t recs = ((uint64_t)P.hchunks << P.p1) * P.cap1;
         P.regionA_keys = recs * 8;
         P.regionA_bytes = recs * 12;
     }
@@ -199,7 +219,7 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, std::string *why, 
     P.o_ticket = at + 64;
     P.o_ticket_s = at + 128;
     at += 256;
-    P.o_cnt1 = at; at = round_up(at + 4 * ((uint64_t)1 << P.p1), 256);
+    P.o_cnt1 = at; at = round_up(at + 4 * ((uint64_t)P.hchunks << P.p1), 256);
     P.o_cnt2 = at; at = round_up(at + 4 * np, 256);
     P.o_t1off = at; at = round_up(at + 8 * (np + 1), 256);
     P.o_pairs = at; at = round_up(at + 8 * np, 256);
@@ -207,7 +227,7 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, std::string *why, 
     P.o_lb = at; at = round_up(at + 8 * np, 256);
     P.o_lbs = at; at = round_up(at + 8 * (uint64_t)P.tiles_scan, 256);
     P.o_desc = at; at = round_up(at + desc_bytes, 256);
-    P.o_tiles = at; at = round_up(at + 64, 256);
+    P.o_tiles = at; at = round_up(at + 512, 256);
     P.o_regionB = at; at = round_up(at + P.regionB_bytes, 256);
     P.scratch_bytes = at;
     *pl = P;

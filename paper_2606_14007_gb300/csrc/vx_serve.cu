@@ -62,8 +62,10 @@ struct Req {
 
 struct Wave;
 
-struct Lane {  // one stream with at most one wave in flight
+struct Lane {  // one stream (plus its pipeline's second stream), one wave at a time
     cudaStream_t stream = nullptr;
+    cudaStream_t aux = nullptr, aux_lo = nullptr;
+    cudaEvent_t sync[vx::kSyncEvents] = {};
     uint8_t *h_ws = nullptr, *d_ws = nullptr;
     Wave *wave = nullptr;
 };
@@ -216,7 +218,7 @@ void launch(vx_server *S)
         if (e == cudaSuccess && rc == VX_OK)
             e = cudaMemcpyAsync(L.d_ws, L.h_ws, vx::batch_ws_bytes((int)n), cudaMemcpyHostToDevice,
                                 L.stream);
-        if (e == cudaSuccess && rc == VX_OK) e = vx::launch_plot_seq(LS, L.stream);
+        if (e == cudaSuccess && rc == VX_OK) e = vx::launch_plot_seq(LS, vx::Lanes{L.stream, L.aux, L.aux_lo, L.sync});
         if (e == cudaSuccess && rc == VX_OK) e = cudaLaunchHostFunc(L.stream, on_wave_done, w);
         if (e != cudaSuccess || rc != VX_OK) {
             cudaGetLastError();
@@ -284,6 +286,7 @@ int vx_serve_create(const vx_serve_opts *o, vx_server **out)
     S->lanes.resize(opts.streams);
     for (Lane &L : S->lanes) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = vx::make_lanes(&L.aux, &L.aux_lo, L.sync);
         if (e == cudaSuccess) e = cudaMallocHost((void **)&L.h_ws, ws);
         if (e == cudaSuccess) e = cudaMalloc((void **)&L.d_ws, ws);
     }
@@ -378,6 +381,7 @@ void vx_serve_destroy(vx_server *S)
     }
     for (Lane &L : S->lanes) {
         if (L.wave) delete L.wave;
+        vx::free_lanes(L.aux, L.aux_lo, L.sync);
         if (L.stream) cudaStreamDestroy(L.stream);
         if (L.h_ws) cudaFreeHost(L.h_ws);
         if (L.d_ws) cudaFree(L.d_ws);

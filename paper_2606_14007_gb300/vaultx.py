@@ -48,7 +48,8 @@ class vx_opts(ctypes.Structure):
         ("scatter_mode", ctypes.c_uint32),
         ("t2_capacity", ctypes.c_uint64),
         ("fuse_pair_hash", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 7),
+        ("pipeline_chunks", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 6),
     ]
 
 

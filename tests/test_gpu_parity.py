@@ -84,6 +84,12 @@ CASES = [
     (1, 0, DIRECT), (5, 3, DIRECT), (12, 6, DIRECT), (17, 18, DIRECT), (22, 0, DIRECT),
     (20, 20, dict(DIRECT, partition_log2=6)),
     (1, 0, FUSED), (9, 21, FUSED), (16, 22, FUSED), (22, 0, FUSED),
+    # two-stream pipeline forced at sizes the oracle covers
+    (20, 24, dict(partition_log2=8, pipeline_chunks=8)),
+    (22, 25, dict(pipeline_chunks=8)),
+    (21, 26, dict(partition_log2=9, pipeline_chunks=2)),
+    (18, 27, dict(DIRECT, partition_log2=7, pipeline_chunks=4)),
+    (3, 28, dict(pipeline_chunks=8)),
     (19, 23, dict(FUSED, scatter_mode=2, partition_log2=7)),
     (16, 12, dict(STAGED, partition_log2=6, coarse_bits=4)),   # two levels, 1024 partitions
     (20, 13, dict(STAGED, partition_log2=8)),                  # two levels (auto)
@@ -256,7 +262,8 @@ def test_split_and_fused_agree_mid_size(vx):
     key = plot_key(91)
     outs = []
     for kw, split in [({}, False), ({}, True), (DIRECT, False), (dict(partition_log2=12), False),
-                      (FUSED, False)]:
+                      (FUSED, False), (dict(pipeline_chunks=1), False),
+                      (dict(pipeline_chunks=2), False)]:
         p = vx.Plot(24, key, vx.make_opts(**kw) if kw else None)
         p.run_split() if split else p.run()
         p.sync()
