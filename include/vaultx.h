@@ -201,6 +201,40 @@ int vx_plot_batch(vx_plot *const *plots, int n, void *stream);
 /* Frees library-owned memory and the handle.  NULL is a no-op. */
 void vx_plot_destroy(vx_plot *plot);
 
+/* ------------------------------------------------- no-allocation path */
+
+/* Bytes of the library's static device scratch array (64 MiB). */
+#define VX_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+/* vx_plot_run without any allocation, for callers that cannot call
+ * cudaMalloc: callers whose device memory belongs to another allocator
+ * under a fixed budget (a framework's caching allocator, a pre-reserved
+ * pool) that must not be bypassed, and latency-critical callers that must
+ * not take the implicit device-wide synchronisation cudaMalloc can cause.
+ * The paper has no counterpart.
+ *
+ * The caller passes the key (32 host bytes) and both table buffers: d_t1 and
+ * d_t2 (device, 256-byte aligned) of at least the t1_bytes / t2_bytes that
+ * vx_plot_required_bytes(K, opts) reports; t2_capacity is d_t2's record
+ * capacity (0 = the planned one).  Everything else -- partition slots,
+ * counters, offsets, the plot descriptor -- lives in one static device array
+ * of VX_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits; plots whose scratch (vx_plot_required_bytes'
+ * scratch_bytes) does not fit, e.g. K > 22 with default options, are
+ * rejected with VX_EINVAL.  No cudaMalloc, cudaFree, pinned or library
+ * allocation is made.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device; make that first call before any stream capture).  All calls share
+ * the one array, which keeps the last call's contents (each run clears what
+ * it reads before use): calls that overlap on the GPU -- on other streams
+ * or other host threads -- race and corrupt each other.  The kernels run one
+ * after the other on `stream`; the call then waits for them and returns
+ * VX_OK / VX_EOVERFLOW / VX_ENOMEM / VX_ETIMEDOUT like vx_sync, with the
+ * Table-2 record count in *t2_count (if not NULL).  Synchronous. */
+int vx_plot_run_noalloc(int K, const uint8_t key[32], const vx_opts *opts, void *d_t1, void *d_t2,
+                        uint64_t t2_capacity, void *stream, uint64_t *t2_count);
+
 /* ------------------------------------------------------------ tracing */
 
 /* Records CUDA events around every kernel of this plot's next `runs` runs

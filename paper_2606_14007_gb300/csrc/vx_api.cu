@@ -36,7 +36,7 @@ static_assert(kPlanHashTile == (uint64_t)kHashTile, "planner and hash kernel til
 static_assert(kPlanScanChunk == (uint64_t)kScanChunk, "planner and scan kernel chunks differ");
 static_assert(kPlanT2HashTile == kT2HashTile, "planner and pair-hash kernel tiles differ");
 static_assert(sizeof(Desc) + 64 <= kStageTilesOffset, "descriptor overlaps staged tiles");
-inline int make_plan(int K, const vx_opts *o, Plan *pl, std::string *why)
+int make_plan(int K, const vx_opts *o, Plan *pl, const char **why)
 {
     int rc = make_plan_sized(K, o, pl, why, sizeof(Desc));
     if (rc != VX_OK) return rc;
@@ -462,7 +462,7 @@ int vx_plot_required_bytes(int K, const vx_opts *opts, uint64_t *t1, uint64_t *t
                            uint64_t *scratch)
 {
     vx::Plan pl;
-    std::string why;
+    const char *why = nullptr;
     if (vx::make_plan(K, opts, &pl, &why) != VX_OK) return VX_EINVAL;
     if (t1) *t1 = pl.t1_bytes;
     if (t2) *t2 = pl.t2_bytes;
@@ -475,7 +475,7 @@ int vx_plot_create(int K, const uint8_t key[32], const vx_opts *opts, vx_plot **
     if (!out || !key) return VX_EINVAL;
     *out = nullptr;
     vx::Plan pl;
-    std::string why;
+    const char *why = nullptr;
     if (vx::make_plan(K, opts, &pl, &why) != VX_OK) return VX_EINVAL;
     vx_plot *p = new (std::nothrow) vx_plot();
     if (!p) return VX_ENOMEM;
@@ -854,6 +854,15 @@ void drop_batch(BatchEntry *b)
 }  // namespace
 
 namespace vx {
+
+void fill_desc_ext(const vx_plot *p, Desc *d) { fill_desc(p, d); }
+
+int build_tiles_ext(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, LaunchSet *L)
+{
+    return build_tiles(plots, n, h, d, L);
+}
+
+int map_status_ext(uint32_t st) { return map_status(st); }
 
 size_t batch_ws_bytes(int n)
 {

@@ -111,5 +111,12 @@ void free_lanes(cudaStream_t aux, cudaStream_t aux_lo, cudaEvent_t *sync);
 // Marks plots as issued on stream s (vx_sync waits on it).
 void mark_issued(vx_plot *const *plots, int n, cudaStream_t s);
 int ensure_memory_ext(vx_plot *p);
+// Planner with the descriptor size of this build; *why gets a static text.
+int make_plan(int K, const vx_opts *o, Plan *pl, const char **why);
+// Descriptor of a bound plot; tile prefixes + launch set of plots[0..n)
+// (kTileArrays arrays of n + 1 entries at h, read on the device from d).
+void fill_desc_ext(const vx_plot *p, Desc *d);
+int build_tiles_ext(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, LaunchSet *L);
+int map_status_ext(uint32_t st);
 
 }  // namespace vx

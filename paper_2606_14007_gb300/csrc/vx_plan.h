@@ -72,7 +72,7 @@ inline double expected_pairs(uint64_t N, uint64_t D)
     return 16777216.0 * lam * lam / 2.0 * q;
 }
 
-inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, std::string *why, size_t desc_bytes)
+inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, size_t desc_bytes)
 {
     if (K < 1 || K > 32) {
         *why = "K must be in 1..32";

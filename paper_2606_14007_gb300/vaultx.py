@@ -100,6 +100,7 @@ def lib():
             "vx_plot_write": (c_int, [vp, ctypes.c_char_p, P(ctypes.c_double), P(ctypes.c_double)]),
             "vx_plot_batch": (c_int, [P(vp), c_int, vp]),
             "vx_plot_destroy": (None, [vp]),
+            "vx_plot_run_noalloc": (c_int, [c_int, u8p, P(vx_opts), vp, vp, u64, vp, P(u64)]),
             "vx_hash_nonces": (c_int, [u8p, u64, u64, vp, vp]),
             "vx_pair_hash": (c_int, [u8p, vp, u64, vp, vp]),
             "vx_test_fail_next_allocs": (c_int, [c_int]),
@@ -236,6 +237,18 @@ def vx_plot_batch(plots, stream=None):
 def vx_plot_destroy(plot):
     if plot:
         lib().vx_plot_destroy(plot)
+
+
+def vx_plot_run_noalloc(K: int, key: bytes, d_t1: int, d_t2: int, t2_capacity: int = 0,
+                        opts: vx_opts | None = None, stream=None, check: bool = True):
+    """Whole plot with the library's static scratch array (no allocation);
+    synchronous.  Returns (status, Table-2 record count)."""
+    n = ctypes.c_uint64()
+    rc = lib().vx_plot_run_noalloc(K, _key(key), ctypes.byref(opts) if opts else None, d_t1, d_t2,
+                                   t2_capacity, _stream(stream), ctypes.byref(n))
+    if check:
+        _check(rc, "vx_plot_run_noalloc")
+    return rc, n.value
 
 
 def vx_hash_nonces(key: bytes, nonce0: int, count: int, d_out: int, stream=None):
