@@ -115,6 +115,25 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
+def reduce_max(value: float, world: int, device) -> float:
+    """Max of `value` over the ranks of the default process group (the
+    bench's only collective: its timing)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(nonces_per_rank: int, steps: int, ms_total_local: float, world: int, device):
+    """(value in nonces/s, ms per step): every rank plots its own keys (weak
+    scaling), the job's time is the slowest rank's."""
+    ms_total = reduce_max(ms_total_local, world, device)
+    return nonces_per_rank * steps * world / (ms_total / 1000.0), ms_total / steps
+
+
 def source_digest(files) -> str:
     h = hashlib.sha256()
     for f in files:
@@ -218,11 +237,23 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "large", "serve"],
+                    help="plain: the K=31 headline; batch: 64 mixed-K plots batched vs plain; "
+                         "large: 4 x K=29 + 8 x K=27 batched vs plain; serve: Poisson requests "
+                         "through the continuous-batching server vs one at a time")
+    ap.add_argument("--partition-log2", type=int, default=0)
+    ap.add_argument("--scatter-mode", type=int, default=0)
+    ap.add_argument("--fuse-pair-hash", type=int, default=0)
+    ap.add_argument("--pipeline-chunks", type=int, default=0)
+    ap.add_argument("--rate", type=float, default=20.0, help="serve: requests per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode != "plain":
+        return run_mode(args)
 
     import torch
     import torch.distributed as dist
@@ -247,7 +278,7 @@ def main():
     N = 1 << K
     key = plot_key(K + 1000 * rank)
     stream = torch.cuda.current_stream()
-    plot = vx.Plot(K, key)
+    plot = vx.Plot(K, key, plot_opts(vx, args))
 
     def barrier():
         if world > 1:
@@ -271,16 +302,11 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
+    ms_local = ev0.elapsed_time(ev1)
     n2 = plot.sync()          # raises on any device-side status error
     per_kernel, runs = vx.vx_plot_profile_read(plot.handle)
     vx.vx_plot_profile(plot.handle, 0)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    ms_step = ms_total / args.steps
-    value = N * args.steps * world / (ms_total / 1000.0)
+    value, ms_step = aggregate(N, args.steps, ms_local, world, "cuda")
 
     # Per-kernel figures (CUDA events on the launching stream, timed region).
     pk = {}
@@ -392,6 +418,169 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+    return 0
+
+
+def plot_opts(vx, args):
+    return vx.make_opts(partition_log2=args.partition_log2, scatter_mode=args.scatter_mode,
+                        fuse_pair_hash=args.fuse_pair_hash, pipeline_chunks=args.pipeline_chunks)
+
+
+def _timed(fn, stream):
+    """Milliseconds of fn() on the device (CUDA events on `stream`)."""
+    import torch
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def run_batch_compare(vx, mix, steps, warmup, name, label):
+    """The same plots plotted one vx_plot_run after the other (plain) and as
+    one vx_plot_batch (grouped launches in a recorded CUDA graph); every
+    plot's tables must be identical both ways."""
+    import torch
+    stream = torch.cuda.current_stream()
+    plots = [vx.Plot(K, key) for K, key in mix]
+    handles = [p.handle for p in plots]
+    nonces = sum(1 << K for K, _ in mix)
+
+    def plain():
+        for p in plots:
+            vx.vx_plot_run(p.handle, stream)
+
+    def batched():
+        vx.vx_plot_batch(handles, stream)
+
+    for _ in range(warmup):
+        plain()
+    ms_plain = _timed(lambda: [plain() for _ in range(steps)], stream) / steps
+    ref = []
+    for p in plots:
+        p.sync()
+        ref.append((p.t1.clone(), p.t2.clone()) if label == "batch" else None)
+    for _ in range(warmup):
+        batched()
+    ms_batch = _timed(lambda: [batched() for _ in range(steps)], stream) / steps
+    equal = True
+    for i, p in enumerate(plots):
+        p.sync()
+        if ref[i] is not None:
+            equal = equal and torch.equal(p.t1, ref[i][0]) and torch.equal(p.t2, ref[i][1])
+    if label == "large":
+        # one plot at a time alone, in a separate buffer set, against the batch's tables
+        for (K, key), p in zip(mix, plots):
+            q = vx.Plot(K, key)
+            q.run()
+            q.sync()
+            equal = equal and torch.equal(q.t1, p.t1) and torch.equal(q.t2, p.t2)
+            q.close()
+            del q
+            torch.cuda.empty_cache()
+    for p in plots:
+        p.close()
+    return {"mode": label, "metric": name, "unit": "nonces/s", "plots": len(mix),
+            "nonces_per_step": nonces,
+            "plain": {"value": nonces / (ms_plain / 1e3), "ms_per_step": ms_plain,
+                      "how": "one vx_plot_run after the other on one stream"},
+            "batched": {"value": nonces / (ms_batch / 1e3), "ms_per_step": ms_batch,
+                        "how": "vx_plot_batch: grouped launches recorded into a CUDA graph"},
+            "batched_over_plain": ms_plain / ms_batch, "equal_output": bool(equal),
+            "steps": steps, "warmup": warmup, "data": "synthetic"}
+
+
+def run_serve(vx, args):
+    """Poisson plot requests through the continuous-batching server, and the
+    same requests plotted one at a time on one preallocated buffer set."""
+    import numpy as np
+    import torch
+    from paper_2606_14007_gb300.inputs import poisson_arrivals
+    arrivals = poisson_arrivals(args.rate, args.duration, 22, 29, 7)
+
+    def pct(xs, q):
+        return float(np.percentile(np.array(xs), q)) if xs else None
+
+    # -- server
+    srv = vx.vx_serve_create()
+    lat, done_nonces, failed = [], 0, 0
+    pending = {}
+    i = 0
+    t0 = time.perf_counter()
+    while i < len(arrivals) or pending:
+        now = time.perf_counter() - t0
+        while i < len(arrivals) and arrivals[i][0] <= now:
+            _, K, key = arrivals[i]
+            pending[vx.vx_serve_submit(srv, K, key)] = K
+            i += 1
+        for t in list(pending):
+            st, h = vx.vx_serve_poll(srv, t)
+            if st == vx.VX_DONE:
+                lat.append(vx.vx_serve_latency(srv, t))
+                done_nonces += 1 << pending.pop(t)
+                vx.vx_plot_destroy(h)
+            elif st == vx.VX_FAILED:
+                failed += 1
+                pending.pop(t)
+        if not pending and i < len(arrivals):
+            time.sleep(max(0.0, min(0.002, arrivals[i][0] - (time.perf_counter() - t0))))
+    served_s = time.perf_counter() - t0
+    vx.vx_serve_destroy(srv)
+
+    # -- one at a time, first come first served, on one buffer set sized for K=29
+    t1b, t2b, sb = vx.vx_plot_required_bytes(29)
+    b1 = torch.empty(t1b, dtype=torch.uint8, device="cuda")
+    b2 = torch.empty(t2b, dtype=torch.uint8, device="cuda")
+    bs = torch.empty(sb, dtype=torch.uint8, device="cuda")
+    plain_lat, plain_nonces = [], 0
+    t0 = time.perf_counter()
+    for (t_arr, K, key) in arrivals:
+        now = time.perf_counter() - t0
+        if now < t_arr:
+            time.sleep(t_arr - now)
+        h = vx.vx_plot_create(K, key)
+        vx.vx_plot_bind(h, b1.data_ptr(), b2.data_ptr(), bs.data_ptr(), 0)
+        vx.vx_plot_run(h)
+        vx.vx_sync(h)
+        vx.vx_plot_destroy(h)
+        plain_lat.append(time.perf_counter() - t0 - t_arr)
+        plain_nonces += 1 << K
+    plain_s = time.perf_counter() - t0
+    return {"mode": "serve", "metric": "plot-request latency and aggregate nonces/s",
+            "unit": "nonces/s", "rate_per_s": args.rate, "duration_s": args.duration,
+            "requests": len(arrivals), "K_range": [22, 29],
+            "served": {"value": done_nonces / served_s, "p50_s": pct(lat, 50), "p99_s": pct(lat, 99),
+                       "completed": len(lat), "failed": failed, "wall_s": served_s,
+                       "how": "vx_serve_submit/poll: admission by HBM footprint, waves on 2 streams"},
+            "one_at_a_time": {"value": plain_nonces / plain_s, "p50_s": pct(plain_lat, 50),
+                              "p99_s": pct(plain_lat, 99), "completed": len(plain_lat),
+                              "wall_s": plain_s,
+                              "how": "arrival order, vx_plot_run + vx_sync per request"},
+            "data": "synthetic"}
+
+
+def run_mode(args):
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_14007_gb300 import vaultx as vx
+    from paper_2606_14007_gb300.inputs import batch_mix, plot_key
+    if args.mode == "batch":
+        mix = batch_mix(64, 20, 26, 2026, 1000)
+        out = run_batch_compare(vx, mix, args.steps, args.warmup,
+                                "aggregate nonces/s, 64 plots, K uniform in 20..26", "batch")
+    elif args.mode == "large":
+        mix = [(29, plot_key(3000 + i)) for i in range(4)] + [(27, plot_key(4000 + i)) for i in range(8)]
+        out = run_batch_compare(vx, mix, args.steps, args.warmup,
+                                "aggregate nonces/s, 4 x K=29 + 8 x K=27 sharing HBM", "large")
+    else:
+        out = run_serve(vx, args)
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps(out), flush=True)
     return 0
 
 
