@@ -16,7 +16,7 @@ constexpr int kMaxK = 32;                // u32 nonces
 constexpr int kMaxCoarseBits = 10;       // first scatter level, <= 1024 bins
 constexpr int kMaxFineBits = 10;         // second scatter level, <= 1024 bins
 constexpr int kScatterTile = 4096;       // records per CTA in the second scatter level
-constexpr int kScatterThreads = 256;
+constexpr int kScatterThreads = 512;
 constexpr int kSortThreads = 256;
 constexpr int kMatchThreads = 256;
 constexpr int kMaxSortDigitBits = 13;    // counting-sort digit of the partition sort
