@@ -235,7 +235,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--K", type=int, default=31)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=6)
+    ap.add_argument("--e2e-copy-streams", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="plain", choices=["plain", "batch", "large", "serve"],
                     help="plain: the K=31 headline; batch: 64 mixed-K plots batched vs plain; "
@@ -245,6 +246,8 @@ def main():
     ap.add_argument("--scatter-mode", type=int, default=0)
     ap.add_argument("--fuse-pair-hash", type=int, default=0)
     ap.add_argument("--pipeline-chunks", type=int, default=0)
+    ap.add_argument("--t2-placement", type=int, default=0,
+                    help="0 automatic, 1 look-back, 2 pair slots")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: requests per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     args = ap.parse_args()
@@ -316,12 +319,17 @@ def main():
     # Algorithmic work per launch: a hash kernel does one compression per
     # nonce and writes 12 B per record; the second scatter level reads and
     # writes 12 B per record; sort+match reads 12 B and writes 12 B per
-    # record and writes 16 B per pair, and hashes the pairs unless the
-    # separate pair-hash pass (read + write 16 B per pair) does.
-    separate = "pairhash" in vx.vx_plot_kernel_mask(plot.handle)
+    # record and writes 16 B per pair (8 B with the pair slots), and hashes
+    # the pairs unless the separate pair-hash pass does (it reads 16 B, or
+    # 8 B from the pair slots, and writes 16 B per pair); the pair-count
+    # scan reads 8 B and writes 8 B per partition.
+    mask = vx.vx_plot_kernel_mask(plot.handle)
+    separate = "pairhash" in mask
+    slots = "scan_pairs" in mask
+    pair_out = 8 if slots else 16
     algo_bytes = {"scatter2": 24 * N, "sort": 24 * N, "match": 12 * N + 16 * n2,
-                  "sortmatch": 24 * N + 16 * n2, "hash_direct": 12 * N, "hash_staged": 12 * N,
-                  "pairhash": 32 * n2}
+                  "sortmatch": 24 * N + pair_out * n2, "hash_direct": 12 * N, "hash_staged": 12 * N,
+                  "pairhash": (pair_out + 16) * n2}
     algo_ops = {"hash_staged": INT_OPS_PER_COMPRESSION * N, "hash_direct": INT_OPS_PER_COMPRESSION * N,
                 "match": INT_OPS_PER_COMPRESSION * n2, "pairhash": INT_OPS_PER_COMPRESSION * n2}
     if not separate:
@@ -356,40 +364,72 @@ def main():
 
     # End to end through the C ABI with host buffers: per step the key goes
     # host -> device (plot descriptor upload from pinned memory) and Table 2
-    # comes back device -> host (pinned), all inside the timed region.
+    # comes back device -> host (pinned), all inside the timed region.  Two
+    # Table-2 buffers let plot i+1 compute while Table 2 of plot i is copied
+    # out on a copy stream (Table 1 and scratch are reused plot after plot
+    # on the compute stream); vx_sync waits for one plot only.
     e2e = None
     if args.e2e_steps > 0:
-        t2_bytes = 16 * n2
         chunk = 1 << 30
-        ring = torch.empty(2 * chunk, dtype=torch.uint8).pin_memory()
-        handles = []
-        barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for i in range(args.e2e_steps):
-            h = vx.vx_plot_create(K, plot_key(K + 1000 * rank + 1 + i))
-            vx.vx_plot_bind(h, plot._t1.data_ptr(), plot._t2.data_ptr(), plot._scratch.data_ptr(), 0)
-            vx.vx_plot_run(h, stream)
-            vx.vx_sync(h)
+        nring = max(1, args.e2e_copy_streams)
+        ring = torch.empty(nring * chunk, dtype=torch.uint8).pin_memory()
+        t2_bufs = [plot._t2, torch.empty_like(plot._t2)]
+        t2_cap = plot._t2.numel() // 16
+        copy_streams = [torch.cuda.Stream() for _ in range(nring)]
+        copy_done = [torch.cuda.Event(), torch.cuda.Event()]
+        opts = plot_opts(vx, args)
+
+        def copy_out(h, slot):
             _, m, _, _ = vx.vx_table_info(h, vx.VX_TABLE2)
             off, k = 0, 0
             while off < 16 * m:
                 nb = min(chunk, 16 * m - off)
-                vx.vx_table_copy(h, vx.VX_TABLE2, ring.data_ptr() + (k % 2) * chunk, nb, stream, offset=off)
+                cs = copy_streams[k % nring]
+                vx.vx_table_copy(h, vx.VX_TABLE2, ring.data_ptr() + (k % nring) * chunk, nb, cs,
+                                 offset=off)
                 off += nb
                 k += 1
-            stream.synchronize()
+            for cs in copy_streams[1:]:
+                copy_streams[0].wait_stream(cs)
+            copy_done[slot].record(copy_streams[0])
+            return m
+
+        handles, counts = [], []
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prev = None
+        for i in range(args.e2e_steps):
+            slot = i % 2
+            h = vx.vx_plot_create(K, plot_key(K + 1000 * rank + 1 + i), opts)
+            vx.vx_plot_bind(h, plot._t1.data_ptr(), t2_bufs[slot].data_ptr(),
+                            plot._scratch.data_ptr(), t2_cap)
+            if i >= 2:
+                stream.wait_event(copy_done[slot])
+            vx.vx_plot_run(h, stream)
+            if prev is not None:
+                vx.vx_sync(prev)
+                counts.append(copy_out(prev, (i - 1) % 2))
             handles.append(h)
+            prev = h
+        vx.vx_sync(prev)
+        counts.append(copy_out(prev, (args.e2e_steps - 1) % 2))
+        for cs in copy_streams:
+            cs.synchronize()
         dt = time.perf_counter() - t0
         barrier()
         for h in handles:
             vx.vx_plot_destroy(h)
+        del t2_bufs
         desc_bytes = 512
         e2e = {"value": N * args.e2e_steps * world / dt, "unit": UNIT,
-               "h2d_bytes_per_step": desc_bytes, "d2h_bytes_per_step": t2_bytes + 12,
+               "h2d_bytes_per_step": desc_bytes,
+               "d2h_bytes_per_step": int(16 * sum(counts) / len(counts)) + 12,
                "steps": args.e2e_steps,
-               "note": "vx_plot_create from a host key, vx_plot_run, vx_sync, then Table 2 "
-                       "copied to pinned host memory through a 2 x 1 GiB ring"}
+               "note": "per step: vx_plot_create from a host key, vx_plot_bind, vx_plot_run, "
+                       "vx_sync, Table 2 copied to pinned host memory with vx_table_copy "
+                       "(1 GiB pieces on %d copy stream(s)); the copy of plot i overlaps plot "
+                       "i+1 (two Table-2 buffers)" % nring}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -423,7 +463,8 @@ def main():
 
 def plot_opts(vx, args):
     return vx.make_opts(partition_log2=args.partition_log2, scatter_mode=args.scatter_mode,
-                        fuse_pair_hash=args.fuse_pair_hash, pipeline_chunks=args.pipeline_chunks)
+                        fuse_pair_hash=args.fuse_pair_hash, pipeline_chunks=args.pipeline_chunks,
+                        t2_placement=args.t2_placement)
 
 
 def _timed(fn, stream):

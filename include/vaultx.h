@@ -69,10 +69,12 @@ typedef struct vx_opts {
     uint32_t size;              /* sizeof(vx_opts)                                   */
     uint32_t test_flags;        /* fault injection for tests, 0 in normal use:
                                    VX_TEST_WITHHOLD_PREFIX makes partition 0 of the
-                                   fused sort + match never publish its Table-2
-                                   prefix, so every later partition's bounded wait
-                                   runs out (short limit) and vx_sync returns
-                                   VX_ETIMEDOUT; the paper has no counterpart       */
+                                   fused sort + match (look-back placement), or
+                                   chunk 0 of the pair-count scan (slot placement),
+                                   never publish its Table-2 prefix, so every later
+                                   bounded wait runs out (short limit) and vx_sync
+                                   returns VX_ETIMEDOUT; the paper has no
+                                   counterpart                                       */
     uint64_t match_distance;    /* D of the match predicate; 0 = 2^(64-K)            */
     int32_t partition_log2;     /* log2 of the mean records per physical partition
                                    (6..13); 0 = default (11).  Partitions are runs
@@ -102,7 +104,22 @@ typedef struct vx_opts {
                                    GB300 the kernel pairs take turns on the SMs
                                    rather than share them), 1 = no overlap; else
                                    2, 4 or 8                                          */
-    uint32_t reserved[6];       /* must be zero                                      */
+    uint32_t t2_placement;      /* vx_plot_run / batches (not fused, not pipelined):
+                                   how each partition's pairs reach their Table-2
+                                   offset.  1 = the sort + match kernel chains the
+                                   partitions by a decoupled look-back and writes
+                                   {a, b} records at their final offsets; 2 = it
+                                   writes each partition's {a, b} pairs into that
+                                   partition's own sort slot (1.5x its record
+                                   capacity), a scan of the per-partition pair
+                                   counts gives the offsets, and the pair hash
+                                   moves the pairs to Table 2 (no waiting between
+                                   partitions; more pairs than the slot holds fail
+                                   the plot with VX_EOVERFLOW: at K >= 26 with the
+                                   default D a partition expects ~2040 +- 100 pairs
+                                   against 3910 places); 0 = automatic = 1 (the
+                                   faster on GB300 at K=31)                        */
+    uint32_t reserved[5];       /* must be zero                                      */
 } vx_opts;
 
 typedef struct vx_plot vx_plot;
@@ -165,9 +182,15 @@ int vx_match(vx_plot *plot, void *stream);
  * Allocates if nothing is bound.  Asynchronous. */
 int vx_plot_run(vx_plot *plot, void *stream);
 
-/* Waits for the plot's last stream, reads its device status word and the
- * Table-2 count, and maps the status to VX_OK / VX_EOVERFLOW / VX_ENOMEM /
- * VX_ETIMEDOUT.  Synchronous. */
+/* Waits for the plot's work, reads its status word and Table-2 count, and
+ * maps the status to VX_OK / VX_EOVERFLOW / VX_ENOMEM / VX_ETIMEDOUT.
+ * Synchronous.  After vx_plot_run it waits on an event recorded behind that
+ * run (vx_plot_run ends with a 12-byte device-to-host copy of the status and
+ * count into the handle's pinned block), so work queued later on the same
+ * stream is not waited for, and the values are this run's even when a later
+ * plot on the stream reuses the same Table-1 and scratch buffers.  After
+ * vx_table1, vx_match or vx_plot_batch it synchronises the whole stream and
+ * reads the scratch buffer. */
 int vx_sync(vx_plot *plot);
 
 /* Zero-copy view of a table: device pointer, record count, record size.

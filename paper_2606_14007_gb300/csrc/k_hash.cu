@@ -280,14 +280,14 @@ cudaError_t launch_hash_direct(const Desc *descs, int nplots, const uint32_t *ti
 // plot's CTAs stride over its range.  Skips plots whose Table 2 is invalid
 // (capacity exceeded, a wait timed out).
 constexpr int kT2HashThreads = 256;
-constexpr int kT2HashPer = 8;
+constexpr int kT2HashPer = 8;  // records per thread of the look-back pair hash's grid
 
 __global__ void __launch_bounds__(kT2HashThreads) k_t2_hash(const Desc *__restrict__ descs,
                                                             int nplots,
                                                             const uint32_t *__restrict__ tile_start,
                                                             int chunk)
 {
-    constexpr int NT = kT2HashThreads, PER = kT2HashPer;
+    constexpr int NT = kT2HashThreads;
     const int plot = find_plot(tile_start, nplots, blockIdx.x);
     const Desc &d = descs[plot];
     if (*d.status & (kStT2Capacity | kStTimeout | kStBadTicket)) return;
@@ -308,26 +308,16 @@ __global__ void __launch_bounds__(kT2HashThreads) k_t2_hash(const Desc *__restri
 #pragma unroll
     for (int i = 0; i < 16; ++i) g[i] = d.pre2[i];
     uint4 *__restrict__ t2 = reinterpret_cast<uint4 *>(d.t2);
-    for (uint64_t base = lo + (uint64_t)me * (NT * PER); base < hi;
-         base += (uint64_t)ctas * (NT * PER)) {
-        uint2 ab[PER];
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const uint64_t q = base + (uint64_t)j * NT + threadIdx.x;
-            if (q < hi) {
-                const uint4 v = t2[q];
-                ab[j] = make_uint2(v.x, v.y);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const uint64_t q = base + (uint64_t)j * NT + threadIdx.x;
-            if (q < hi) {
-                uint32_t h0, h1;
-                b3_finish<true>(g, ab[j].x, ab[j].y, h0, h1);
-                t2[q] = make_uint4(ab[j].x, ab[j].y, h0, h1);
-            }
-        }
+    // One record per iteration, loop kept rolled: the body is one
+    // compression, small enough for the instruction cache even when the
+    // warps (no barrier here) drift apart; unrolling several compressions
+    // made the warps stall on instruction fetch.
+#pragma unroll 1
+    for (uint64_t q = lo + (uint64_t)me * NT + threadIdx.x; q < hi; q += (uint64_t)ctas * NT) {
+        const uint4 v = t2[q];
+        uint32_t h0, h1;
+        b3_finish<true>(g, v.x, v.y, h0, h1);
+        t2[q] = make_uint4(v.x, v.y, h0, h1);
     }
 }
 
@@ -336,6 +326,71 @@ cudaError_t launch_t2_hash(const Desc *descs, int nplots, const uint32_t *tile_s
 {
     if (total_tiles == 0) return cudaSuccess;
     k_t2_hash<<<total_tiles, kT2HashThreads, 0, s>>>(descs, nplots, tile_start, chunk);
+    return cudaGetLastError();
+}
+
+// Pair hash of the slot placement (Sec. III-A, Table 2): CTA b takes
+// partitions [8b, 8b + 8) of one plot, whose pairs the sort left in the
+// partitions' level-2 slots (pair k of partition f: key array of slot f
+// for k < cap2, nonce array for k >= cap2) and whose Table-2 offsets the
+// pair-count scan wrote; the CTA walks the group's pairs as one run, so
+// every warp reads consecutive pairs and writes consecutive records.
+__global__ void __launch_bounds__(kT2HashThreads) k_t2_hash_slots(const Desc *__restrict__ descs,
+                                                                  int nplots,
+                                                                  const uint32_t *__restrict__ tile_start)
+{
+    constexpr int NT = kT2HashThreads;
+    constexpr uint32_t G = kT2SlotGroup;
+    static_assert(G == 8, "the search below is written for groups of 8");
+    __shared__ uint32_t s_rel[G + 1];  // pair offsets relative to the group's first
+    __shared__ uint64_t s_base;
+    const int plot = find_plot(tile_start, nplots, blockIdx.x);
+    const Desc &d = descs[plot];
+    if (*d.status & (kStT2Capacity | kStTimeout | kStBadTicket | kStPairSlot)) return;
+    const uint64_t np = 1ull << d.p;
+    const uint64_t fa = (uint64_t)(blockIdx.x - tile_start[plot]) * G;
+    if (fa >= np) return;
+    // The offsets exist only if the scan's chain reached its last chunk
+    // (a broken chain has set a status bit, except for a withheld chunk 0
+    // in a one-chunk scan).
+    const uint64_t nchunks = (np + kScanChunk - 1) / kScanChunk;
+    if ((ld_acquire_u64(d.lb + (nchunks - 1)) & ~kLbMask) != kLbIncl) return;
+    const uint32_t ng = (uint32_t)(np - fa < G ? np - fa : G);
+    if (threadIdx.x == 0) s_base = d.t2off[fa];
+    __syncthreads();
+    if (threadIdx.x <= G) {
+        // partitions past the plot's last read as "never reached"
+        s_rel[threadIdx.x] = threadIdx.x <= ng ? (uint32_t)(d.t2off[fa + threadIdx.x] - s_base)
+                                               : 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    const uint32_t total = s_rel[ng];
+    const uint32_t cap = d.cap2;
+    uint32_t g[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) g[i] = d.pre2[i];
+    uint4 *__restrict__ t2 = reinterpret_cast<uint4 *>(d.t2) + s_base;
+#pragma unroll 1
+    for (uint32_t q = threadIdx.x; q < total; q += NT) {  // one compression per iteration
+        // partition of pair q: the last t with s_rel[t] <= q
+        uint32_t t = s_rel[4] <= q ? 4u : 0u;
+        t += s_rel[t + 2] <= q ? 2u : 0u;
+        t += s_rel[t + 1] <= q ? 1u : 0u;
+        const uint32_t k = q - s_rel[t];
+        const uint64_t f = fa + t;
+        const uint2 ab = k < cap ? reinterpret_cast<const uint2 *>(d.b_keys + f * cap)[k]
+                                 : reinterpret_cast<const uint2 *>(d.b_nonces + f * cap)[k - cap];
+        uint32_t h0, h1;
+        b3_finish<true>(g, ab.x, ab.y, h0, h1);
+        t2[q] = make_uint4(ab.x, ab.y, h0, h1);
+    }
+}
+
+cudaError_t launch_t2_hash_slots(const Desc *descs, int nplots, const uint32_t *tile_start,
+                                 uint32_t total_tiles, cudaStream_t s)
+{
+    if (total_tiles == 0) return cudaSuccess;
+    k_t2_hash_slots<<<total_tiles, kT2HashThreads, 0, s>>>(descs, nplots, tile_start);
     return cudaGetLastError();
 }
 

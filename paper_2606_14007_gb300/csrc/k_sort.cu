@@ -138,13 +138,21 @@ cudaError_t launch_scatter2(const Desc *descs, int nplots, const uint32_t *tile_
     return cudaGetLastError();
 }
 
-// ------------------------------------------- Table-1 offsets (counts scan)
-// Exclusive prefix of the 2^p final-partition fill counts (clipped to the
-// slot capacity) in chunks of kScanChunk counters, one CTA per chunk, the
-// chunks chained by decoupled look-back.  The last chunk checks that every
-// nonce arrived.
+// ------------------------------- Table-1 / Table-2 offsets (counts scan)
+// Exclusive prefix of 2^p per-partition counts in chunks of kScanChunk
+// counters, one CTA per chunk (taken in ticket order), the chunks chained by
+// decoupled look-back.
 constexpr int kScanCtaThreads = 256;
 
+// SRC 0: level-2 fill counters (clipped to the slot) -> Table-1 offsets,
+// chunk ticket ticket_s, look-back words lbs; the last chunk checks that
+// every nonce arrived.
+// SRC 1: per-partition pair counts of the slot placement -> Table-2
+// offsets, chunk ticket `ticket` and look-back words `lb` (both unused by
+// the slot sort, zeroed by the key setup); counts are clipped to one more
+// than a pair slot holds (a larger count has already failed the plot), and
+// the last chunk checks the Table-2 capacity.
+template <int SRC>
 __global__ void __launch_bounds__(kScanCtaThreads) k_scan_counts(const Desc *__restrict__ descs,
                                                                  int nplots,
                                                                  const uint32_t *__restrict__ tile_start)
@@ -157,7 +165,10 @@ __global__ void __launch_bounds__(kScanCtaThreads) k_scan_counts(const Desc *__r
     __shared__ int s_ok;
     const int plot = find_plot(tile_start, nplots, blockIdx.x);
     const Desc &d = descs[plot];
-    if (threadIdx.x == 0) s_c = atomicAdd(d.ticket_s, 1u);
+    uint32_t *ticket = SRC == 0 ? d.ticket_s : d.ticket;
+    uint64_t *lb = SRC == 0 ? d.lbs : d.lb;
+    uint64_t *out = SRC == 0 ? d.t1off : d.t2off;
+    if (threadIdx.x == 0) s_c = atomicAdd(ticket, 1u);
     __syncthreads();
     const uint32_t c = s_c;
     const uint64_t n = 1ull << d.p;
@@ -166,19 +177,32 @@ __global__ void __launch_bounds__(kScanCtaThreads) k_scan_counts(const Desc *__r
         if (threadIdx.x == 0) atomicOr(d.status, kStBadTicket);
         return;
     }
+    const uint32_t clip = SRC == 0 ? d.cap2 : d.cap2 + d.cap2 / 2u + 1u;
     const uint64_t b0 = (uint64_t)c * kScanChunk + (uint64_t)threadIdx.x * PER;
     uint32_t v[PER];
     uint32_t loc = 0;
 #pragma unroll
     for (uint32_t k = 0; k < PER; ++k) {
-        v[k] = b0 + k < n ? min(d.cnt2[b0 + k], d.cap2) : 0u;
-        loc += v[k];
+        uint32_t x = 0;
+        if (b0 + k < n) {
+            if (SRC == 0) {
+                x = min(d.cnt2[b0 + k], clip);
+            } else {
+                const uint64_t y = d.pairs[b0 + k];
+                x = y < clip ? (uint32_t)y : clip;
+            }
+        }
+        v[k] = x;
+        loc += x;
     }
     uint32_t total;
     uint32_t run = block_exclusive_scan_u32<NT>(loc, ws, &total);
     if (threadIdx.x < 32) {
         uint64_t excl = 0;
-        const int ok = lookback_warp(d.lbs, c, total, d.status, d.spin_limit, false, &excl) ? 1 : 0;
+        // VX_TEST_WITHHOLD_PREFIX: chunk 0 of the pair-count scan never
+        // publishes, so every later chunk's bounded wait runs out.
+        const bool withhold = SRC == 1 && (d.test_flags & 1u) != 0;
+        const int ok = lookback_warp(lb, c, total, d.status, d.spin_limit, withhold, &excl) ? 1 : 0;
         if (threadIdx.x == 0) {
             s_ok = ok;
             s_base = excl;
@@ -189,20 +213,31 @@ __global__ void __launch_bounds__(kScanCtaThreads) k_scan_counts(const Desc *__r
     uint64_t at = s_base + run;
 #pragma unroll
     for (uint32_t k = 0; k < PER; ++k) {
-        if (b0 + k < n) d.t1off[b0 + k] = at;
+        if (b0 + k < n) out[b0 + k] = at;
         at += v[k];
     }
     if (c + 1 == nchunks && threadIdx.x == 0) {
         const uint64_t all = s_base + total;
-        d.t1off[n] = all;
-        if (all != d.N) atomicOr(d.status, kStCountMismatch);
+        out[n] = all;
+        if (SRC == 0) {
+            if (all != d.N) atomicOr(d.status, kStCountMismatch);
+        } else {
+            if (all > d.t2cap) atomicOr(d.status, kStT2Capacity);
+        }
     }
 }
 
 cudaError_t launch_scan_counts(const Desc *descs, int nplots, const uint32_t *tile_start,
                                uint32_t total_tiles, cudaStream_t s)
 {
-    k_scan_counts<<<total_tiles, kScanCtaThreads, 0, s>>>(descs, nplots, tile_start);
+    k_scan_counts<0><<<total_tiles, kScanCtaThreads, 0, s>>>(descs, nplots, tile_start);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_pair_counts(const Desc *descs, int nplots, const uint32_t *tile_start,
+                                    uint32_t total_tiles, cudaStream_t s)
+{
+    k_scan_counts<1><<<total_tiles, kScanCtaThreads, 0, s>>>(descs, nplots, tile_start);
     return cudaGetLastError();
 }
 

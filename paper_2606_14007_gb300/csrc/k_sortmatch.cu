@@ -21,11 +21,16 @@
 // {a, b, 0, 0} at its final offset; the streaming pair-hash kernel fills in
 // the hashes (no barriers, full occupancy: the ALU-bound part runs apart
 // from the latency-bound sort).
+// MODE kSortSlots: Table 1, then the partition's pairs {a, b} in (i, j)
+// order into the partition's own level-2 slot, which the kernel has already
+// read into shared memory: cap2 pairs in the key array, cap2 / 2 in the
+// nonce array.  No partition waits on another; a scan of the pair counts
+// and the slot pair hash place the records.
 #include "vx_internal.cuh"
 
 namespace vx {
 
-enum { kSortCount = 0, kSortHash = 1, kSortEmit = 2 };
+enum { kSortCount = 0, kSortHash = 1, kSortEmit = 2, kSortSlots = 3 };
 constexpr uint32_t kSMList = 2048;  // pair-list window (entries), kSortHash only
 constexpr int kSMThreads = 256;
 
@@ -50,7 +55,8 @@ template <int MODE>
 __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
     k_sortmatch(const Desc *__restrict__ descs, int nplots, const uint32_t *__restrict__ tile_start)
 {
-    constexpr bool EMIT = MODE != kSortCount;
+    constexpr bool EMIT = MODE == kSortHash || MODE == kSortEmit;  // look-back placement
+    constexpr bool SLOTS = MODE == kSortSlots;
     constexpr int NT = kSMThreads;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t s_f;
@@ -81,8 +87,12 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
 
     const uint32_t n = min(d.cnt2[f], cap);
     const uint64_t off = d.t1off[f];
-    const uint64_t *__restrict__ ikeys = d.b_keys + (uint64_t)f * cap;
-    const uint32_t *__restrict__ inonces = d.b_nonces + (uint64_t)f * cap;
+    // The slot is read through the read-only path unless this kernel later
+    // overwrites it with the partition's pairs.
+    const uint64_t *ikeys = d.b_keys + (uint64_t)f * cap;
+    const uint32_t *inonces = d.b_nonces + (uint64_t)f * cap;
+    auto key_at = [&](uint32_t i) -> uint64_t { return SLOTS ? ikeys[i] : __ldg(ikeys + i); };
+    auto nonce_at = [&](uint32_t i) -> uint32_t { return SLOTS ? inonces[i] : __ldg(inonces + i); };
     const int shift = 64 - d.p - dbits;
     const uint32_t dmask = ndig - 1u;
 
@@ -90,7 +100,7 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
     for (uint32_t i = threadIdx.x; i < ndig; i += NT) DC[i] = 0u;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < n; i += NT) {
-        const uint32_t dg = (uint32_t)(__ldg(ikeys + i) >> shift) & dmask;
+        const uint32_t dg = (uint32_t)(key_at(i) >> shift) & dmask;
         RK[i] = (uint16_t)atomicAdd(&DC[dg], 1u);
     }
     __syncthreads();
@@ -99,10 +109,10 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
     // 3. place records at their digit position (the second read of the
     //    slot hits L1/L2)
     for (uint32_t i = threadIdx.x; i < n; i += NT) {
-        const uint64_t k = __ldg(ikeys + i);
+        const uint64_t k = key_at(i);
         const uint32_t pos = DC[(uint32_t)(k >> shift) & dmask] + RK[i];
         SK[pos] = k;
-        SN[pos] = __ldg(inonces + i);
+        SN[pos] = nonce_at(i);
     }
     __syncthreads();
     // 4. finish every digit run (about one record each) by insertion sort on
@@ -157,41 +167,13 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
         d.pairs[f] = P;  // lets vx_match re-run the match alone
         if (EMIT) lb_publish(d.lb, f, P, withhold);
     }
-    // 7. Table 1.  Records 12 B each: the head up to a 16-byte boundary and
-    //    the tail go word by word; the body goes as groups of 4 records =
-    //    three 16-byte stores per thread.
-    {
-        uint32_t *__restrict__ t1w = reinterpret_cast<uint32_t *>(d.t1) + 3 * off;
-        const uint32_t head = min(n, (uint32_t)((4u - (uint32_t)(off & 3u)) & 3u));
-        const uint32_t groups = (n - head) / 4u;
-        const uint32_t tail0 = head + 4u * groups;
-        for (uint32_t r = threadIdx.x; r < head + (n - tail0); r += NT) {
-            const uint32_t rr = r < head ? r : tail0 + (r - head);
-            const uint64_t k = SK[rr];
-            t1w[3 * rr] = SN[rr];
-            t1w[3 * rr + 1] = bswap32((uint32_t)(k >> 32));
-            t1w[3 * rr + 2] = bswap32((uint32_t)k);
-        }
-        uint4 *__restrict__ body = reinterpret_cast<uint4 *>(t1w + 3 * head);
-        for (uint32_t g = threadIdx.x; g < groups; g += NT) {
-            const uint32_t r = head + 4u * g;
-            uint32_t w[12];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint64_t k = SK[r + j];
-                w[3 * j] = SN[r + j];
-                w[3 * j + 1] = bswap32((uint32_t)(k >> 32));
-                w[3 * j + 2] = bswap32((uint32_t)k);
-            }
-            body[3 * g] = make_uint4(w[0], w[1], w[2], w[3]);
-            body[3 * g + 1] = make_uint4(w[4], w[5], w[6], w[7]);
-            body[3 * g + 2] = make_uint4(w[8], w[9], w[10], w[11]);
-        }
-    }
-    if (!EMIT) return;
-    // 8. Table-2 base: resolve the look-back (warp 0)
+    // 7. Table 1, and (EMIT) the Table-2 base at the same time: warp 0
+    //    resolves the look-back while the other warps write the records.
+    //    Records 12 B each: the head up to a 16-byte boundary and the tail
+    //    go word by word; the body goes as groups of 4 records = three
+    //    16-byte stores per thread.
     const uint64_t np = 1ull << d.p;
-    if (threadIdx.x < 32) {
+    if (EMIT && threadIdx.x < 32) {
         uint64_t excl = 0;
         int ok = lb_resolve(d.lb, f, P, d.status, d.spin_limit, withhold, &excl) ? 1 : 0;
         if (threadIdx.x == 0) {
@@ -206,7 +188,62 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
             s_base = excl;
             s_ok = ok;
         }
+    } else {
+        constexpr uint32_t T0 = EMIT ? 32u : 0u;  // first Table-1 writer
+        constexpr uint32_t NW = NT - T0;           // Table-1 writers
+        const uint32_t tw = threadIdx.x - T0;
+        uint32_t *__restrict__ t1w = reinterpret_cast<uint32_t *>(d.t1) + 3 * off;
+        const uint32_t head = min(n, (uint32_t)((4u - (uint32_t)(off & 3u)) & 3u));
+        const uint32_t groups = (n - head) / 4u;
+        const uint32_t tail0 = head + 4u * groups;
+        for (uint32_t r = tw; r < head + (n - tail0); r += NW) {
+            const uint32_t rr = r < head ? r : tail0 + (r - head);
+            const uint64_t k = SK[rr];
+            t1w[3 * rr] = SN[rr];
+            t1w[3 * rr + 1] = bswap32((uint32_t)(k >> 32));
+            t1w[3 * rr + 2] = bswap32((uint32_t)k);
+        }
+        uint4 *__restrict__ body = reinterpret_cast<uint4 *>(t1w + 3 * head);
+        for (uint32_t g = tw; g < groups; g += NW) {
+            const uint32_t r = head + 4u * g;
+            uint32_t w[12];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint64_t k = SK[r + j];
+                w[3 * j] = SN[r + j];
+                w[3 * j + 1] = bswap32((uint32_t)(k >> 32));
+                w[3 * j + 2] = bswap32((uint32_t)k);
+            }
+            body[3 * g] = make_uint4(w[0], w[1], w[2], w[3]);
+            body[3 * g + 1] = make_uint4(w[4], w[5], w[6], w[7]);
+            body[3 * g + 2] = make_uint4(w[8], w[9], w[10], w[11]);
+        }
     }
+    if (SLOTS) {
+        // 8. pairs into the slot (its records were read before the
+        //    barriers above)
+        const uint32_t capA = cap, capB = cap / 2u;
+        if (P > capA + capB) {
+            if (threadIdx.x == 0) atomicOr(d.status, kStPairSlot);
+            return;
+        }
+        uint2 *__restrict__ pa = reinterpret_cast<uint2 *>(d.b_keys + (uint64_t)f * cap);
+        uint2 *__restrict__ pb = reinterpret_cast<uint2 *>(d.b_nonces + (uint64_t)f * cap);
+        for (uint32_t r = threadIdx.x; r < n; r += NT) {
+            const uint32_t s0 = ST[r];
+            const uint32_t s1 = r + 1 < n ? ST[r + 1] : P;
+            const uint32_t a = SN[r];
+            for (uint32_t k = s0; k < s1; ++k) {
+                const uint2 v = make_uint2(a, SN[r + 1 + (k - s0)]);
+                if (k < capA)
+                    pa[k] = v;
+                else
+                    pb[k - capA] = v;
+            }
+        }
+        return;
+    }
+    if (!EMIT) return;
     __syncthreads();
     if (!s_ok) return;
     uint4 *__restrict__ out = reinterpret_cast<uint4 *>(d.t2) + s_base;
@@ -263,10 +300,12 @@ static cudaError_t launch_sm(const Desc *descs, int nplots, const uint32_t *tile
 
 cudaError_t launch_sortmatch(const Desc *descs, int nplots, const uint32_t *tile_start,
                              uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits,
-                             bool fused_hash)
+                             SortMatchOut out)
 {
-    if (fused_hash)
+    if (out == kOutLookbackHashed)
         return launch_sm<kSortHash>(descs, nplots, tile_start, total_tiles, s, max_cap, max_dbits);
+    if (out == kOutSlots)
+        return launch_sm<kSortSlots>(descs, nplots, tile_start, total_tiles, s, max_cap, max_dbits);
     return launch_sm<kSortEmit>(descs, nplots, tile_start, total_tiles, s, max_cap, max_dbits);
 }
 

@@ -36,6 +36,9 @@ static_assert(kPlanHashTile == (uint64_t)kHashTile, "planner and hash kernel til
 static_assert(kPlanScanChunk == (uint64_t)kScanChunk, "planner and scan kernel chunks differ");
 static_assert(kPlanT2HashTile == kT2HashTile, "planner and pair-hash kernel tiles differ");
 static_assert(sizeof(Desc) + 64 <= kStageTilesOffset, "descriptor overlaps staged tiles");
+static_assert(kStageTilesOffset + kTileArrays * 2 * sizeof(uint32_t) <= kStageResultOffset &&
+                  kStageResultOffset + 16 <= kStageBytes,
+              "staged tiles overlap the result block");
 int make_plan(int K, const vx_opts *o, Plan *pl, const char **why)
 {
     int rc = make_plan_sized(K, o, pl, why, sizeof(Desc));
@@ -166,7 +169,7 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
     const int W = n + 1;
     enum { A_STG = 0, A_DIR = 8, A_S2 = 16, A_PC = 24, A_T2H = 32, A_SCAN = 40, A_PART = 41 };
     static_assert(A_PART + 1 == vx::kTileArrays, "tile arrays");
-    bool fuse = true;
+    bool fuse = true, slots = true;
     L->G = L->C = 1;
     L->max_cap2 = 0;
     L->max_dbits = 1;
@@ -175,6 +178,7 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
         if (!plots[i] || !plots[i]->d_t1) return VX_EINVAL;
         const Plan &pl = plots[i]->plan;
         fuse = fuse && pl.fuse_pair_hash;
+        slots = slots && pl.pair_slots;
         L->G = std::max(L->G, pl.hchunks);
         L->C = std::max(L->C, pl.pchunks);
         L->max_cap2 = std::max(L->max_cap2, pl.cap2);
@@ -194,7 +198,9 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
         const uint64_t np = 1ull << pl.p;
         for (int c = 0; c < vx::kMaxChunks && c < pl.pchunks; ++c) {
             cnt[A_PC + c] = np * (c + 1) / pl.pchunks - np * c / pl.pchunks;
-            if (!fuse) {
+            if (slots) {
+                cnt[A_T2H + c] = pl.tiles_t2s;  // pchunks == 1
+            } else if (!fuse) {
                 const uint64_t per = (plots[i]->t2cap / pl.pchunks + kPlanT2HashTile - 1) / kPlanT2HashTile;
                 cnt[A_T2H + c] = per ? per : 1;
             }
@@ -210,6 +216,7 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
     L->n = n;
     L->agg = min_bits <= kAggMaxBits;
     L->fuse_pair_hash = fuse;
+    L->pair_slots = slots;
     for (int g = 0; g < vx::kMaxChunks; ++g) {
         L->t_staged[g] = d + (A_STG + g) * W;
         L->t_direct[g] = d + (A_DIR + g) * W;
@@ -272,7 +279,7 @@ int map_status(uint32_t st)
     if (st & vx::kStTimeout) return VX_ETIMEDOUT;
     if (st & vx::kStBadTicket) return VX_ECUDA;
     if (st & (vx::kStSlot1Overflow | vx::kStSlot2Overflow | vx::kStCountMismatch |
-              vx::kStPartitionTooBig))
+              vx::kStPartitionTooBig | vx::kStPairSlot))
         return VX_EOVERFLOW;
     if (st & vx::kStT2Capacity) return VX_ENOMEM;
     return VX_OK;
@@ -286,6 +293,7 @@ std::string status_text(uint32_t st)
     if (st & vx::kStCountMismatch) s += "records lost before the sort (count mismatch); ";
     if (st & vx::kStPartitionTooBig) s += "partition larger than shared memory; ";
     if (st & vx::kStT2Capacity) s += "Table 2 exceeds its capacity; ";
+    if (st & vx::kStPairSlot) s += "a partition's pairs exceed its pair slot (use t2_placement 1); ";
     if (st & vx::kStTimeout) s += "device wait timed out; ";
     if (st & vx::kStBadTicket) s += "work ticket out of range (state not reset); ";
     return s;
@@ -377,12 +385,22 @@ cudaError_t launch_fused(const LaunchSet &L, const vx::Lanes &ln, const vx::Trac
     cudaError_t e = launch_front(L, ln, T);
     if (e != cudaSuccess) return e;
     const cudaStream_t A = ln.main, B = ln.aux_lo;
+    if (L.pair_slots) {
+        // slot placement: sort + match, pair-count scan, slot pair hash
+        VX_LAUNCH(KID_SORTMATCH, A, vx::launch_sortmatch(L.descs, L.n, L.t_pchunk[0], L.n_pchunk[0], A,
+                                                         L.max_cap2, L.max_dbits, vx::kOutSlots));
+        VX_LAUNCH(KID_SCANP, A, vx::launch_scan_pair_counts(L.descs, L.n, L.t_scan, L.n_scan, A));
+        VX_LAUNCH(KID_PAIRHASH, A, vx::launch_t2_hash_slots(L.descs, L.n, L.t_t2h[0], L.n_t2h[0], A));
+        return cudaSuccess;
+    }
     const bool ph = !L.fuse_pair_hash;
     const bool ov = B && L.C > 1 && ph;
     for (int c = 0; c < L.C; ++c) {
         if (L.n_pchunk[c])
             VX_LAUNCH(KID_SORTMATCH, A, vx::launch_sortmatch(L.descs, L.n, L.t_pchunk[c], L.n_pchunk[c], A,
-                                                             L.max_cap2, L.max_dbits, L.fuse_pair_hash));
+                                                             L.max_cap2, L.max_dbits,
+                                                             L.fuse_pair_hash ? vx::kOutLookbackHashed
+                                                                              : vx::kOutLookback));
         if (ph && L.n_t2h[c]) {
             if (ov) {
                 cudaEventRecord(ln.sync[vx::kMaxChunks + 1 + c], A);
@@ -555,6 +573,7 @@ int vx_table1(vx_plot *p, void *stream)
     p->t2_known = false;
     p->last = s;
     p->have_last = true;
+    p->res_pending = false;
     return VX_OK;
 }
 
@@ -581,8 +600,27 @@ int vx_match(vx_plot *p, void *stream)
     p->t2_known = false;
     p->last = s;
     p->have_last = true;
+    p->res_pending = false;
     return VX_OK;
 }
+
+namespace {
+// Copies the plot's status word and Table-2 count into its pinned result
+// block behind its kernels and records ev_done, so that vx_sync waits for
+// this plot alone and reads what this plot produced, even when a plot
+// queued later on the same stream reuses the scratch buffer.
+int record_result(vx_plot *p, cudaStream_t s)
+{
+    uint8_t *h = reinterpret_cast<uint8_t *>(p->h_stage) + vx::kStageResultOffset;
+    if (!p->ev_done) VX_TRY(p, cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming));
+    VX_TRY(p, cudaMemcpyAsync(h, p->d_scratch + p->plan.o_status, 4, cudaMemcpyDeviceToHost, s));
+    VX_TRY(p, cudaMemcpyAsync(h + 8, p->d_scratch + p->plan.o_t2off + 8 * (1ull << p->plan.p), 8,
+                              cudaMemcpyDeviceToHost, s));
+    VX_TRY(p, cudaEventRecord(p->ev_done, s));
+    p->res_pending = true;
+    return VX_OK;
+}
+}  // namespace
 
 int vx_plot_run(vx_plot *p, void *stream)
 {
@@ -603,13 +641,28 @@ int vx_plot_run(vx_plot *p, void *stream)
     p->t2_known = false;
     p->last = s;
     p->have_last = true;
-    return VX_OK;
+    p->res_pending = false;
+    return record_result(p, s);
 }
 
 int vx_sync(vx_plot *p)
 {
     if (!p) return VX_EINVAL;
     if (p->stage == 0) return VX_ENOTREADY;
+    if (p->res_pending) {
+        VX_TRY(p, cudaEventSynchronize(p->ev_done));
+        const uint8_t *h = reinterpret_cast<const uint8_t *>(p->h_stage) + vx::kStageResultOffset;
+        uint32_t st = 0;
+        uint64_t total = 0;
+        memcpy(&st, h, 4);
+        memcpy(&total, h + 8, 8);
+        p->status = st;
+        p->t2_count = total;
+        p->t2_known = true;
+        const int rc = map_status(st);
+        if (rc != VX_OK) set_err(p, status_text(st));
+        return rc;
+    }
     if (p->have_last) VX_TRY(p, cudaStreamSynchronize(p->last));
     uint32_t st = 0;
     VX_TRY(p, cudaMemcpy(&st, p->d_scratch + p->plan.o_status, 4, cudaMemcpyDeviceToHost));
@@ -675,12 +728,16 @@ void vx_plot_destroy(vx_plot *p)
 {
     if (!p) return;
     forget_batches(p);
-    if (p->have_last) cudaStreamSynchronize(p->last);
+    if (p->res_pending)
+        cudaEventSynchronize(p->ev_done);
+    else if (p->have_last)
+        cudaStreamSynchronize(p->last);
     if (p->ev_pending) cudaEventSynchronize(p->ev_stage);
     if (p->release) p->release(p->release_ctx, p);
     free_owned(p);
     if (p->h_stage) cudaFreeHost(p->h_stage);
     if (p->ev_stage) cudaEventDestroy(p->ev_stage);
+    if (p->ev_done) cudaEventDestroy(p->ev_done);
     vx_plot_profile(p, 0);
     if (p->aux) vx::free_lanes(p->aux, p->aux_lo, p->sync_ev);
     delete p;
@@ -704,7 +761,8 @@ int vx_plot_kernel_mask(const vx_plot *p, int split, uint32_t *mask)
     m |= pl.mode == vx::kScatterStaged ? 1u << 1 : 1u << 2;  // hash_staged / hash_direct
     if (pl.mode == vx::kScatterStaged && pl.p2 > 0) m |= 1u << 3;  // scatter2
     if (split) m |= 1u << 5 | 1u << 6 | 1u << 7;           // sort, scan_pairs, match
-    else m |= 1u << 8 | (pl.fuse_pair_hash ? 0u : 1u << 9);  // sortmatch, pairhash
+    else m |= 1u << 8 | (pl.fuse_pair_hash ? 0u : 1u << 9) |  // sortmatch, pairhash
+              (pl.pair_slots ? 1u << 6 : 0u);                  // scan_pairs (pair-count scan)
     *mask = m;
     return VX_OK;
 }
@@ -918,6 +976,7 @@ void mark_issued(vx_plot *const *plots, int n, cudaStream_t s)
         p->t2_known = false;
         p->last = s;
         p->have_last = true;
+        p->res_pending = false;
     }
 }
 

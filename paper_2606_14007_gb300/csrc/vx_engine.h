@@ -37,6 +37,7 @@ struct LaunchSet {
     uint32_t n_scan, n_part;          // total CTAs
     bool agg;
     bool fuse_pair_hash;
+    bool pair_slots;   // every plot uses the slot placement (t_t2h[0] = slot pair-hash grid)
     uint32_t max_cap2;
     int max_dbits;
 };
@@ -75,6 +76,8 @@ struct vx_plot {
     bool ev_pending = false;
     cudaStream_t last = nullptr;
     bool have_last = false;
+    cudaEvent_t ev_done = nullptr;  // behind vx_plot_run's kernels and result copy
+    bool res_pending = false;       // vx_sync reads the pinned result block after ev_done
     int stage = 0;                 // 0 created, 1 Table 1 issued, 2 match issued
     bool t2_known = false;
     uint64_t t2_count = 0;

@@ -31,6 +31,7 @@ constexpr uint32_t kStT2Capacity = 1u << 3;
 constexpr uint32_t kStPartitionTooBig = 1u << 4;
 constexpr uint32_t kStTimeout = 1u << 5;
 constexpr uint32_t kStBadTicket = 1u << 6;
+constexpr uint32_t kStPairSlot = 1u << 7;     // a partition's pairs exceed its pair slot
 
 // ------------------------------------------------------ plot descriptor
 // One plot's plan and buffers.  The host fills everything but pre1/pre2,
@@ -450,11 +451,20 @@ cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *t
                                 uint32_t total_tiles, HashCfg cfg, int chunk, cudaStream_t s);
 cudaError_t launch_hash_direct(const Desc *descs, int nplots, const uint32_t *tile_start,
                                uint32_t total_tiles, int chunk, cudaStream_t s);
+// Sort + match variants: Table-2 records at final offsets found by a
+// look-back ({a, b, 0, 0}, hashed later by launch_t2_hash; or hashed in the
+// kernel), or pairs {a, b} written into each partition's own slot.
+enum SortMatchOut { kOutLookback = 0, kOutLookbackHashed = 1, kOutSlots = 2 };
 cudaError_t launch_sortmatch(const Desc *descs, int nplots, const uint32_t *tile_start,
                              uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits,
-                             bool fused_hash);
+                             SortMatchOut out);
 cudaError_t launch_t2_hash(const Desc *descs, int nplots, const uint32_t *tile_start,
                            uint32_t total_tiles, int chunk, cudaStream_t s);
+// Pair hash of the slot placement: kT2SlotGroup partitions per CTA, pairs
+// read from the partition slots, records written at the scanned offsets.
+constexpr uint32_t kT2SlotGroup = 8;
+cudaError_t launch_t2_hash_slots(const Desc *descs, int nplots, const uint32_t *tile_start,
+                                 uint32_t total_tiles, cudaStream_t s);
 constexpr uint64_t kT2HashTile = 256 * 8;  // Table-2 records per pair-hash CTA
 size_t sortmatch_smem_bytes(uint32_t cap, int dbits);
 uint32_t sortmatch_max_cap();  // largest slot the sort keeps in registers
@@ -462,6 +472,10 @@ cudaError_t launch_scatter2(const Desc *descs, int nplots, const uint32_t *tile_
                             uint32_t total_tiles, int chunk, cudaStream_t s);
 cudaError_t launch_scan_counts(const Desc *descs, int nplots, const uint32_t *tile_start,
                                uint32_t total_tiles, cudaStream_t s);
+// Same chunked look-back scan over the per-partition pair counts (slot
+// placement) -> Table-2 offsets, with the Table-2 capacity check.
+cudaError_t launch_scan_pair_counts(const Desc *descs, int nplots, const uint32_t *tile_start,
+                                    uint32_t total_tiles, cudaStream_t s);
 constexpr uint32_t kScanChunk = 4096;      // counters per CTA of the Table-1 offset scan
 cudaError_t launch_sort(const Desc *descs, int nplots, const uint32_t *tile_start,
                         uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits);

@@ -23,19 +23,23 @@ constexpr int kMaxPartBits = 20;           // two scatter levels of <= 10 bits e
 constexpr int kAggMaxBits = 6;             // warp-aggregate ranks up to 64 bins
 constexpr size_t kStageBytes = 4096;       // pinned staging: Desc + tile prefixes
 constexpr size_t kStageTilesOffset = 3584;
+constexpr size_t kStageResultOffset = 4064;  // status u32 at +0, Table-2 count u64 at +8
 constexpr uint64_t kWriteStageBytes = 256ull << 20;  // Sec. III-B: 256 MB pinned staging
 constexpr uint64_t kWriteChunkBytes = 4ull << 20;    // Sec. III-A: 4 MB sequential chunks
 constexpr uint64_t kPlanHashTile = 2048;   // nonces per hash CTA (threads x nonces/thread)
 constexpr uint64_t kPlanScanChunk = 4096;  // counters per Table-1 offset-scan CTA
 constexpr uint64_t kPlanT2HashTile = 2048; // Table-2 records per pair-hash CTA
+constexpr uint64_t kPlanT2SlotGroup = 8;   // partitions per pair-hash CTA reading pair slots
 
 enum { kScatterAuto = 0, kScatterStaged = 1, kScatterDirect = 2 };
+enum { kPlaceAuto = 0, kPlaceLookback = 1, kPlaceSlots = 2 };
 
 struct Plan {
     int K, s, p, p1, p2, dbits;
     int mode;                              // kScatterStaged or kScatterDirect
     uint32_t test_flags, spin_limit;
     bool fuse_pair_hash;
+    bool pair_slots;                       // pairs staged in the partition slots (t2_placement 2)
     int hchunks;                           // nonce chunks of the hash / second-scatter pipeline
     int pchunks;                           // partition chunks of the sort / pair-hash pipeline
     uint64_t N, D, t2cap;
@@ -44,6 +48,7 @@ struct Plan {
     uint32_t tiles_hash, tiles_s2, tiles_part;
     uint32_t tiles_staged, tiles_direct;   // tiles_hash of the kernel the mode uses, 0 for the other
     uint32_t tiles_scan, tiles_t2h;        // Table-1 offset scan chunks, pair-hash CTAs
+    uint32_t tiles_t2s;                    // pair-hash CTAs reading pair slots
     uint64_t regionA_keys, regionB_keys;   // byte offset of the nonce array in each slot region
     uint64_t regionA_bytes, regionB_bytes;
     uint64_t t1_bytes, t2_bytes, scratch_bytes;
@@ -104,7 +109,7 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
         return VX_EINVAL;
     }
     P.test_flags = opts.test_flags;
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 5; ++i)
         if (opts.reserved[i]) {
             *why = "reserved vx_opts fields must be zero";
             return VX_EINVAL;
@@ -176,6 +181,20 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     P.dbits = db;
     P.agg = (P.p2 > 0 ? P.p1 : P.p) <= kAggMaxBits;
 
+    // Table-2 placement.  Automatic = look-back: measured on GB300 at K=31
+    // the slot placement's sort runs slower (its slot reads cannot take the
+    // read-only path, and the look-back waits it removes were already hidden
+    // by the other resident CTAs), 164.3 vs 162.2 ms per plot.
+    if (opts.t2_placement > kPlaceSlots) {
+        *why = "t2_placement must be 0 (auto), 1 (look-back) or 2 (slots)";
+        return VX_EINVAL;
+    }
+    if (opts.t2_placement == kPlaceSlots && (P.fuse_pair_hash || P.pchunks != 1)) {
+        *why = "t2_placement 2 (slots) needs fuse_pair_hash 0 and pipeline_chunks 0 or 1";
+        return VX_EINVAL;
+    }
+    P.pair_slots = opts.t2_placement == kPlaceSlots;
+
     if (opts.t2_capacity) {
         P.t2cap = opts.t2_capacity;
     } else {
@@ -192,6 +211,7 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     P.tiles_scan = (uint32_t)(((1ull << P.p) + kPlanScanChunk - 1) / kPlanScanChunk);
     P.tiles_t2h = (uint32_t)((P.t2cap / P.pchunks + kPlanT2HashTile - 1) / kPlanT2HashTile);
     if (P.tiles_t2h == 0) P.tiles_t2h = 1;
+    P.tiles_t2s = (uint32_t)(((1ull << P.p) + kPlanT2SlotGroup - 1) / kPlanT2SlotGroup);
 
     // Slot regions (SoA: key64 array, then nonce array).
     if (P.p2 > 0) {

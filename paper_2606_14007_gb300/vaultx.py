@@ -49,7 +49,8 @@ class vx_opts(ctypes.Structure):
         ("t2_capacity", ctypes.c_uint64),
         ("fuse_pair_hash", ctypes.c_uint32),
         ("pipeline_chunks", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 6),
+        ("t2_placement", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 5),
     ]
 
 
@@ -125,6 +126,10 @@ def lib():
 
 def strerror(code: int) -> str:
     return lib().vx_strerror(code).decode()
+
+
+def last_error(plot) -> str:
+    return lib().vx_last_error(plot).decode()
 
 
 def _check(rc: int, what: str, plot=None):

@@ -83,7 +83,8 @@ def test_required_bytes_rejects_bad_arguments(vx):
         assert ei.value.code == vx.VX_EINVAL
     for kw in [dict(partition_log2=5), dict(partition_log2=14),
                dict(coarse_bits=11, scatter_mode=1), dict(scatter_mode=3),
-               dict(slack_sigma=400, partition_log2=12)]:
+               dict(slack_sigma=400, partition_log2=12), dict(t2_placement=3),
+               dict(t2_placement=2, pipeline_chunks=2), dict(t2_placement=2, fuse_pair_hash=1)]:
         with pytest.raises(vx.VxError):
             vx.vx_plot_required_bytes(31, vx.make_opts(**kw))
     bad = vx.make_opts()
@@ -111,6 +112,10 @@ def test_kernel_mask_follows_plan(vx):
     h = vx.vx_plot_create(31, bytes(32))
     assert vx.vx_plot_kernel_mask(h) == ["key_setup", "hash_staged", "scatter2", "scan_counts",
                                          "sortmatch", "pairhash"]
+    vx.vx_plot_destroy(h)
+    h = vx.vx_plot_create(31, bytes(32), vx.make_opts(t2_placement=2))
+    assert vx.vx_plot_kernel_mask(h) == ["key_setup", "hash_staged", "scatter2", "scan_counts",
+                                         "scan_pairs", "sortmatch", "pairhash"]
     vx.vx_plot_destroy(h)
     h = vx.vx_plot_create(20, bytes(32), vx.make_opts(scatter_mode=2, fuse_pair_hash=1))
     assert vx.vx_plot_kernel_mask(h) == ["key_setup", "hash_direct", "scan_counts", "sortmatch"]

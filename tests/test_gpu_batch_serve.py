@@ -39,10 +39,11 @@ def copy_table(vx, h, which):
     return host[: n * rb].numpy().reshape(n, rb)
 
 
-def test_batch_mixed_k_equals_oracle(vx):
+@pytest.mark.parametrize("placement", [0, 2], ids=["lookback", "slots"])
+def test_batch_mixed_k_equals_oracle(vx, placement):
     mix = [(10, 101), (14, 102), (16, 103), (18, 104), (20, 105), (12, 106), (22, 107), (17, 108),
            (1, 109), (24, 110)]
-    plots = [vx.Plot(K, plot_key(s)) for K, s in mix]
+    plots = [vx.Plot(K, plot_key(s), vx.make_opts(t2_placement=placement)) for K, s in mix]
     handles = [p.handle for p in plots]
     for rep in range(2):  # the second launch replays the recorded graph
         vx.vx_plot_batch(handles)

@@ -74,6 +74,8 @@ def test_pair_hash_row_matches_oracle(vx):
 STAGED = dict(scatter_mode=1)
 DIRECT = dict(scatter_mode=2)
 FUSED = dict(fuse_pair_hash=1)
+LOOKBACK = dict(t2_placement=1)   # partitions chained by look-back, records at final offsets
+SLOTS = dict(t2_placement=2)      # pairs staged in the partition slots, offsets by a scan
 # (K, seed, opts) -- sizes from one record to the small configuration;
 # opts exercise both bucketing strategies, both scatter levels and the sort
 # digit widths.
@@ -98,6 +100,14 @@ CASES = [
     (18, 14, dict(partition_log2=13)),                         # large partitions, 13-bit digits
     (19, 17, dict(partition_log2=9, slack_sigma=40)),          # roomy slots
     (20, 19, dict(partition_log2=6)),                          # 2^14 tiny partitions
+    # both Table-2 placements forced (automatic = look-back)
+    (1, 0, LOOKBACK), (12, 6, LOOKBACK), (20, 11, LOOKBACK), (22, 0, LOOKBACK),
+    (17, 18, dict(DIRECT, t2_placement=1)), (19, 29, dict(partition_log2=13, t2_placement=1)),
+    (1, 0, SLOTS), (5, 3, SLOTS), (14, 8, SLOTS), (22, 0, SLOTS),
+    (20, 19, dict(partition_log2=6, t2_placement=2)),          # 2^14 groups of 8 partitions
+    (11, 30, dict(partition_log2=6, t2_placement=2)),          # 32 partitions: a ragged last group
+    (18, 14, dict(partition_log2=13, t2_placement=2)),
+    (17, 31, dict(DIRECT, t2_placement=2)),
 ]
 
 
@@ -148,6 +158,39 @@ def test_deterministic_repeat(vx):
         assert np.array_equal(a[0], outs[0][0]) and np.array_equal(a[1], outs[0][1])
 
 
+@pytest.mark.parametrize("placement", [1, 2], ids=["lookback", "slots"])
+@pytest.mark.parametrize("K,seed,D", [(16, 20, 1 << 34), (15, 23, (1 << 64) - 1)])
+def test_custom_match_distance_both_placements(vx, K, seed, D, placement):
+    key = plot_key(seed)
+    t1, t2, n2, _ = run_plot(vx, K, key, vx.make_opts(match_distance=D, t2_placement=placement))
+    r1, r2 = oracle_plot(K, key, D)
+    assert np.array_equal(t2, r2)
+
+
+def test_pair_slot_overflow_is_reported(vx):
+    # K=26 with every pair of a logical bucket matching: ~4096 pairs per
+    # partition, more than a pair slot (1.5 x 2607) holds.  Forced slots
+    # must fail with VX_EOVERFLOW; the look-back placement (automatic)
+    # agrees with the split path, which places pairs by a plain scan.
+    K, key, D = 26, plot_key(65), (1 << 64) - 1
+    p = vx.Plot(K, key, vx.make_opts(match_distance=D, t2_placement=2))
+    p.run()
+    assert vx.vx_sync(p.handle, check=False) == vx.VX_EOVERFLOW
+    assert "pair slot" in vx.last_error(p.handle)
+    p.close()
+    p = vx.Plot(K, key, vx.make_opts(match_distance=D))
+    assert vx.vx_plot_kernel_mask(p.handle)[-2:] == ["sortmatch", "pairhash"]
+    assert "scan_pairs" not in vx.vx_plot_kernel_mask(p.handle)
+    p.run()
+    n_auto = p.sync()
+    t2_auto = p.t2.cpu().numpy()
+    p.run_split()
+    n_split = p.sync()
+    assert n_auto == n_split > 2 ** 26
+    assert np.array_equal(t2_auto, p.t2.cpu().numpy())
+    p.close()
+
+
 @pytest.mark.parametrize("mode", [1, 2], ids=["staged", "direct"])
 def test_slot_overflow_is_reported(vx, mode):
     # Slots of mean + 1 sd (+16) overflow in many partitions: the plot must
@@ -181,12 +224,43 @@ def test_table2_capacity_then_rebind(vx, split):
     p.close()
 
 
-def test_lookback_wait_times_out(vx):
-    # Partition 0 withholds its Table-2 prefix: every later partition's wait
-    # must run out (bounded), the plot must report VX_ETIMEDOUT, and the
-    # context must stay usable for the next plot.
-    p = vx.Plot(16, plot_key(61), vx.make_opts(partition_log2=8,
-                                                test_flags=vx.VX_TEST_WITHHOLD_PREFIX))
+def test_sync_reads_its_own_plot_when_buffers_are_reused(vx):
+    # Two plots on one stream share Table 1 and scratch, each with its own
+    # Table 2: vx_sync on the first, issued after both, must report the first
+    # plot's count (not the second's, whose kernels overwrote the scratch),
+    # and both Table 2 buffers must hold their own plot.
+    K = 16
+    ka, kb = plot_key(63), plot_key(64)
+    t1b, t2b, scb = vx.vx_plot_required_bytes(K)
+    t1 = torch.empty(t1b, dtype=torch.uint8, device="cuda")
+    sc = torch.empty(scb, dtype=torch.uint8, device="cuda")
+    t2 = [torch.empty(t2b, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    hs = []
+    for key, buf in [(ka, t2[0]), (kb, t2[1])]:
+        h = vx.vx_plot_create(K, key)
+        vx.vx_plot_bind(h, t1.data_ptr(), buf.data_ptr(), sc.data_ptr(), t2b // 16)
+        vx.vx_plot_run(h)
+        hs.append(h)
+    refs = [oracle_plot(K, ka)[1], oracle_plot(K, kb)[1]]
+    assert refs[0].shape[0] != refs[1].shape[0]
+    for h, buf, r2 in zip(hs, t2, refs):
+        vx.vx_sync(h)
+        _, n2, _, _ = vx.vx_table_info(h, vx.VX_TABLE2)
+        assert n2 == r2.shape[0]
+        assert np.array_equal(buf[: 16 * n2].view(n2, 16).cpu().numpy(), r2)
+    for h in hs:
+        vx.vx_plot_destroy(h)
+
+
+@pytest.mark.parametrize("K,s,placement", [(16, 8, 0), (20, 6, 2)], ids=["lookback", "slots"])
+def test_lookback_wait_times_out(vx, K, s, placement):
+    # Partition 0 (look-back placement) or chunk 0 of the pair-count scan
+    # (slot placement: 2^14 partitions = 4 scan chunks) withholds its
+    # Table-2 prefix: every later wait must run out (bounded), the plot must
+    # report VX_ETIMEDOUT, and the context must stay usable for the next plot.
+    p = vx.Plot(K, plot_key(61), vx.make_opts(partition_log2=s, t2_placement=placement,
+                                               test_flags=vx.VX_TEST_WITHHOLD_PREFIX))
+    assert ("scan_pairs" in vx.vx_plot_kernel_mask(p.handle)) == (placement == 2)
     p.run()
     assert vx.vx_sync(p.handle, check=False) == vx.VX_ETIMEDOUT
     p.close()
