@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__rest
     }
     for (int b = threadIdx.x; b < nbins; b += NT) sm.hist[b] = 0u;
     __syncthreads();
-    if (!mbar_wait(&sm.bar, 0, d.spin_limit)) {
+    if (!__syncthreads_and(mbar_wait(&sm.bar, 0, d.spin_limit))) {  // one answer for all threads
         // The copy did not land in time: report, give it one more bounded
         // wait so it does not write into a successor's shared memory, stop.
         if (threadIdx.x == 0) atomicOr(d.status, kStTimeout);
@@ -79,21 +79,26 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__rest
         rank[j] = valid ? atomicAdd(&sm.hist[bin], 1u) : 0u;
     }
     __syncthreads();
+    constexpr int PB = ((1 << kMaxFineBits) + NT - 1) / NT;  // most bins a thread owns
+    const int per = (nbins + NT - 1) / NT;
+    const int b0 = threadIdx.x * per;
+    uint32_t claim[PB];
     {
-        const int per = (nbins + NT - 1) / NT;
-        const int b0 = threadIdx.x * per;
         uint32_t loc = 0;
         for (int k = 0; k < per; ++k)
             if (b0 + k < nbins) loc += sm.hist[b0 + k];
         uint32_t total;
         uint32_t run = block_exclusive_scan_u32<NT>(loc, sm.ws, &total);
-        for (int k = 0; k < per; ++k) {
+#pragma unroll
+        for (int k = 0; k < PB; ++k) {
             const int b = b0 + k;
-            if (b < nbins) {
+            claim[k] = 0u;
+            if (k < per && b < nbins) {
                 const uint32_t h = sm.hist[b];
                 sm.loff[b] = run;
                 run += h;
-                sm.gbase[b] = h ? atomicAdd(&d.cnt2[((uint64_t)c << p2) + b], h) : 0u;
+                // the claim's result is first needed after the restage below
+                if (h) claim[k] = atomicAdd(&d.cnt2[((uint64_t)c << p2) + b], h);
             }
         }
     }
@@ -108,6 +113,9 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__rest
             sm.nonces[pos] = nonce[j];
         }
     }
+#pragma unroll
+    for (int k = 0; k < PB; ++k)
+        if (k < per && b0 + k < nbins) sm.gbase[b0 + k] = claim[k];
     __syncthreads();
     const uint32_t cap = d.cap2;
     bool overflow = false;

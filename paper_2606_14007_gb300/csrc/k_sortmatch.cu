@@ -35,8 +35,10 @@ constexpr uint32_t kSMList = 2048;  // pair-list window (entries), kSortHash onl
 constexpr int kSMThreads = 256;
 
 // Shared layout: sorted key64 [cap] | sorted nonce [cap] | rank within the
-// digit, u16 [cap] | digit counters [2^dbits] | per-record pair count ->
-// Table-2 offset [cap] | pair list (kSortHash) | scan workspace.
+// digit, u16 [cap] + digit counters [2^dbits], later overlaid by the
+// per-record pair count -> Table-2 offset [cap] | pair list (kSortHash) |
+// scan workspace.  The latency-bound sort runs five CTAs per SM (48
+// registers): measured 41.0 ms at K=31 against 44.8 ms with four.
 struct SMLayout {
     size_t sn, rank, dcnt, start, list, ws, bytes;
     __host__ __device__ SMLayout(uint32_t cap, int dbits, bool with_list)
@@ -44,15 +46,20 @@ struct SMLayout {
         sn = (size_t)cap * 8;
         rank = sn + (size_t)cap * 4;
         dcnt = rank + (size_t)((cap + 1) & ~1u) * 2;
-        start = dcnt + ((size_t)1 << dbits) * 4;
-        list = start + (size_t)cap * 4;
+        // The per-record pair counts (step 5 on) reuse the rank and digit-
+        // counter space, dead after step 4: 43.8 KiB at the default 2608-
+        // record slot, so five CTAs fit an SM's 228 KiB.
+        start = rank;
+        const size_t rd_end = dcnt + ((size_t)1 << dbits) * 4;
+        const size_t st_end = start + (size_t)cap * 4;
+        list = rd_end > st_end ? rd_end : st_end;
         ws = list + (with_list ? (size_t)kSMList * 4 : 0);
         bytes = ws + 40 * 4;
     }
 };
 
 template <int MODE>
-__global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
+__global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 5)
     k_sortmatch(const Desc *__restrict__ descs, int nplots, const uint32_t *__restrict__ tile_start)
 {
     constexpr bool EMIT = MODE == kSortHash || MODE == kSortEmit;  // look-back placement
@@ -167,31 +174,15 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
         d.pairs[f] = P;  // lets vx_match re-run the match alone
         if (EMIT) lb_publish(d.lb, f, P, withhold);
     }
-    // 7. Table 1, and (EMIT) the Table-2 base at the same time: warp 0
-    //    resolves the look-back while the other warps write the records.
-    //    Records 12 B each: the head up to a 16-byte boundary and the tail
-    //    go word by word; the body goes as groups of 4 records = three
-    //    16-byte stores per thread.
+    // 7. Table 1.  Records 12 B each: the head up to a 16-byte boundary and
+    //    the tail go word by word; the body goes as groups of 4 records =
+    //    three 16-byte stores per thread.  (Resolving the look-back in warp 0
+    //    while the other warps write Table 1 measured slower than this
+    //    order: 45.2 vs 44.8 ms at K=31.)
     const uint64_t np = 1ull << d.p;
-    if (EMIT && threadIdx.x < 32) {
-        uint64_t excl = 0;
-        int ok = lb_resolve(d.lb, f, P, d.status, d.spin_limit, withhold, &excl) ? 1 : 0;
-        if (threadIdx.x == 0) {
-            if (ok) {
-                d.t2off[f] = excl;
-                if (f + 1 == np) d.t2off[np] = excl + P;
-                if (excl + P > d.t2cap) {
-                    atomicOr(d.status, kStT2Capacity);
-                    ok = 0;
-                }
-            }
-            s_base = excl;
-            s_ok = ok;
-        }
-    } else {
-        constexpr uint32_t T0 = EMIT ? 32u : 0u;  // first Table-1 writer
-        constexpr uint32_t NW = NT - T0;           // Table-1 writers
-        const uint32_t tw = threadIdx.x - T0;
+    {
+        constexpr uint32_t NW = NT;  // Table-1 writers
+        const uint32_t tw = threadIdx.x;
         uint32_t *__restrict__ t1w = reinterpret_cast<uint32_t *>(d.t1) + 3 * off;
         const uint32_t head = min(n, (uint32_t)((4u - (uint32_t)(off & 3u)) & 3u));
         const uint32_t groups = (n - head) / 4u;
@@ -244,6 +235,23 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 4)
         return;
     }
     if (!EMIT) return;
+    // 8. Table-2 base: resolve the look-back (warp 0)
+    if (threadIdx.x < 32) {
+        uint64_t excl = 0;
+        int ok = lb_resolve(d.lb, f, P, d.status, d.spin_limit, withhold, &excl) ? 1 : 0;
+        if (threadIdx.x == 0) {
+            if (ok) {
+                d.t2off[f] = excl;
+                if (f + 1 == np) d.t2off[np] = excl + P;
+                if (excl + P > d.t2cap) {
+                    atomicOr(d.status, kStT2Capacity);
+                    ok = 0;
+                }
+            }
+            s_base = excl;
+            s_ok = ok;
+        }
+    }
     __syncthreads();
     if (!s_ok) return;
     uint4 *__restrict__ out = reinterpret_cast<uint4 *>(d.t2) + s_base;
