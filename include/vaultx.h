@@ -83,10 +83,10 @@ typedef struct vx_opts {
                                    -1 = automatic                                     */
     uint32_t slack_sigma;       /* partition-slot slack in standard deviations of a
                                    Poisson count; 0 = default (12)                   */
-    uint32_t hash_block;        /* threads per block of the hash kernel (64..1024,
-                                   multiple of 32); 0 = default                      */
-    uint32_t nonces_per_thread; /* nonces each hash thread handles (2..64, even);
-                                   0 = default                                        */
+    uint32_t hash_block;        /* threads per block of the hash kernels: 0 or 256
+                                   (the one shape built; others are VX_EINVAL)      */
+    uint32_t nonces_per_thread; /* nonces each hash thread handles: 0 or 8 (the one
+                                   shape built; others are VX_EINVAL)               */
     uint32_t scatter_mode;      /* bucketing of hashed records: 0 = automatic
                                    (staged), 1 = staged (shared-memory histogram per CTA, one
                                    claim per (CTA, bin), two levels), 2 = direct

@@ -35,6 +35,8 @@ namespace vx {
 static_assert(kPlanHashTile == (uint64_t)kHashTile, "planner and hash kernel tiles differ");
 static_assert(kPlanScanChunk == (uint64_t)kScanChunk, "planner and scan kernel chunks differ");
 static_assert(kPlanT2HashTile == kT2HashTile, "planner and pair-hash kernel tiles differ");
+static_assert(kPlanT2SlotGroup == (uint64_t)kT2SlotGroup, "planner and slot pair-hash groups differ");
+static_assert(kHashThreads == 256 && kHashNoncesPerThread == 8, "hash shape the planner accepts");
 static_assert(sizeof(Desc) + 64 <= kStageTilesOffset, "descriptor overlaps staged tiles");
 static_assert(kStageTilesOffset + kTileArrays * 2 * sizeof(uint32_t) <= kStageResultOffset &&
                   kStageResultOffset + 16 <= kStageBytes,

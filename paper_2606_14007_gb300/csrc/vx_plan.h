@@ -114,6 +114,12 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
             *why = "reserved vx_opts fields must be zero";
             return VX_EINVAL;
         }
+    // The hash kernels are compiled for one shape (256 threads x 8 nonces).
+    if ((opts.hash_block != 0 && opts.hash_block != 256) ||
+        (opts.nonces_per_thread != 0 && opts.nonces_per_thread != 8)) {
+        *why = "hash_block must be 0 or 256 and nonces_per_thread 0 or 8";
+        return VX_EINVAL;
+    }
     P.fuse_pair_hash = opts.fuse_pair_hash != 0;
     const uint32_t pc = opts.pipeline_chunks;
     if (pc != 0 && pc != 1 && pc != 2 && pc != 4 && pc != 8) {

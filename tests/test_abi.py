@@ -84,9 +84,11 @@ def test_required_bytes_rejects_bad_arguments(vx):
     for kw in [dict(partition_log2=5), dict(partition_log2=14),
                dict(coarse_bits=11, scatter_mode=1), dict(scatter_mode=3),
                dict(slack_sigma=400, partition_log2=12), dict(t2_placement=3),
-               dict(t2_placement=2, pipeline_chunks=2), dict(t2_placement=2, fuse_pair_hash=1)]:
+               dict(t2_placement=2, pipeline_chunks=2), dict(t2_placement=2, fuse_pair_hash=1),
+               dict(hash_block=128), dict(nonces_per_thread=4)]:
         with pytest.raises(vx.VxError):
             vx.vx_plot_required_bytes(31, vx.make_opts(**kw))
+    vx.vx_plot_required_bytes(31, vx.make_opts(hash_block=256, nonces_per_thread=8))
     bad = vx.make_opts()
     bad.size = 8
     with pytest.raises(vx.VxError):
