@@ -238,10 +238,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--e2e-copy-streams", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "large", "serve"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "large", "serve", "write"],
                     help="plain: the K=31 headline; batch: 64 mixed-K plots batched vs plain; "
                          "large: 4 x K=29 + 8 x K=27 batched vs plain; serve: Poisson requests "
-                         "through the continuous-batching server vs one at a time")
+                         "through the continuous-batching server vs one at a time; write: plots "
+                         "written to flat Table-2 files, serial vs overlapped with the next plot")
     ap.add_argument("--partition-log2", type=int, default=0)
     ap.add_argument("--scatter-mode", type=int, default=0)
     ap.add_argument("--fuse-pair-hash", type=int, default=0)
@@ -250,6 +251,9 @@ def main():
                     help="0 automatic, 1 look-back, 2 pair slots")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: requests per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--write-K", type=int, default=28, help="write: K of every plot")
+    ap.add_argument("--write-plots", type=int, default=6, help="write: plots per leg")
+    ap.add_argument("--write-dir", default=None, help="write: directory for the plot files")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -603,6 +607,100 @@ def run_serve(vx, args):
             "data": "synthetic"}
 
 
+def run_write(vx, args):
+    """NEXT-1: plots of one K written as flat Table-2 files (vx_plot_write:
+    D2H through pinned staging, 4 MB sequential writes), serial against
+    overlapped with the next plot's kernels (two Table-2 buffers, a writer
+    thread; Table 1 and scratch shared on the compute stream)."""
+    import concurrent.futures as cf
+    import shutil
+    import tempfile
+    import numpy as np
+    import torch
+    from paper_2606_14007_gb300.inputs import plot_key
+    K, nplots = args.write_K, args.write_plots
+    stream = torch.cuda.current_stream()
+    t1b, t2b, sb = vx.vx_plot_required_bytes(K)
+    t1 = torch.empty(t1b, dtype=torch.uint8, device="cuda")
+    sc = torch.empty(sb, dtype=torch.uint8, device="cuda")
+    t2 = [torch.empty(t2b, dtype=torch.uint8, device="cuda") for _ in range(2)]
+    wdir = tempfile.mkdtemp(prefix="vx_plots_", dir=args.write_dir)
+    paths = [os.path.join(wdir, "plot%d.bin" % i) for i in range(2)]
+
+    def make(i):
+        h = vx.vx_plot_create(K, plot_key(5000 + i))
+        vx.vx_plot_bind(h, t1.data_ptr(), t2[i % 2].data_ptr(), sc.data_ptr(), t2b // 16)
+        return h
+
+    def write(h, i):
+        d2h, total = vx.vx_plot_write(h, paths[i % 2])
+        c0 = time.perf_counter()
+        fd = os.open(paths[i % 2], os.O_RDONLY)
+        os.fsync(fd)
+        os.close(fd)
+        return d2h, total, time.perf_counter() - c0
+
+    try:
+        # warm-up: one plot, written and checked against Table 2 on the device
+        h = make(0)
+        vx.vx_plot_run(h, stream)
+        write(h, 0)
+        _, n2, _, _ = vx.vx_table_info(h, vx.VX_TABLE2)
+        got = np.fromfile(paths[0], dtype=np.uint8)
+        equal = got.size == 16 * n2 and bool(
+            (torch.from_numpy(got).cuda() == t2[0][: 16 * n2]).all().item())
+        vx.vx_plot_destroy(h)
+        file_bytes = 16 * n2
+
+        # serial: plot, then write, one after the other
+        stats = []
+        t0 = time.perf_counter()
+        for i in range(nplots):
+            h = make(i)
+            vx.vx_plot_run(h, stream)
+            stats.append(write(h, i))
+            vx.vx_plot_destroy(h)
+        serial_s = time.perf_counter() - t0
+
+        # overlapped: plot i+1 computes while plot i is written
+        ostats = []
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(max_workers=1) as ex:
+            futs = []
+            for i in range(nplots):
+                if i >= 2:
+                    ostats.append(futs[i - 2][0].result())  # frees Table-2 buffer i % 2
+                    vx.vx_plot_destroy(futs[i - 2][1])
+                h = make(i)
+                vx.vx_plot_run(h, stream)
+                futs.append((ex.submit(write, h, i), h))
+            for f, h in futs[max(0, nplots - 2):]:
+                ostats.append(f.result())
+                vx.vx_plot_destroy(h)
+        overlap_s = time.perf_counter() - t0
+    finally:
+        shutil.rmtree(wdir, ignore_errors=True)
+
+    def mean(xs, k):
+        return float(np.mean([x[k] for x in xs]))
+
+    nonces = nplots * (1 << K)
+    return {"mode": "write", "metric": "plots written to flat Table-2 files, nonces/s end to end",
+            "unit": "nonces/s", "K": K, "plots": nplots, "file_bytes": int(file_bytes),
+            "dir_fs": wdir.rsplit("/", 1)[0],
+            "serial": {"value": nonces / serial_s, "s_per_plot": serial_s / nplots,
+                       "d2h_s": mean(stats, 0), "write_s": mean(stats, 1), "fsync_s": mean(stats, 2),
+                       "file_GBps": file_bytes / mean(stats, 1) / 1e9,
+                       "how": "vx_plot_run, vx_plot_write (+ fsync), next plot"},
+            "overlapped": {"value": nonces / overlap_s, "s_per_plot": overlap_s / nplots,
+                           "d2h_s": mean(ostats, 0), "write_s": mean(ostats, 1),
+                           "fsync_s": mean(ostats, 2),
+                           "how": "writer thread runs vx_plot_write (+ fsync) of plot i while "
+                                  "plot i+1 runs; two Table-2 buffers"},
+            "overlapped_over_serial": serial_s / overlap_s, "equal_output": bool(equal),
+            "data": "synthetic"}
+
+
 def run_mode(args):
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -618,6 +716,8 @@ def run_mode(args):
         mix = [(29, plot_key(3000 + i)) for i in range(4)] + [(27, plot_key(4000 + i)) for i in range(8)]
         out = run_batch_compare(vx, mix, args.steps, args.warmup,
                                 "aggregate nonces/s, 4 x K=29 + 8 x K=27 sharing HBM", "large")
+    elif args.mode == "write":
+        out = run_write(vx, args)
     else:
         out = run_serve(vx, args)
     if int(os.environ.get("RANK", "0")) == 0:

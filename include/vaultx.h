@@ -210,8 +210,12 @@ int vx_table_copy(vx_plot *plot, int which, uint64_t offset, void *host_dst, uin
                   void *stream);
 
 /* Writes Table 2 as a flat binary file (Sec. III-A / III-B: D2H through a
- * pinned staging buffer, sequential 4 MB chunks; no header).  Returns after
- * the file is written.  Synchronous. */
+ * 256 MB pinned staging buffer on the library's own copy stream, sequential
+ * 4 MB chunks; no header).  The device copy of one 128 MB half overlaps the
+ * write of the other.  Waits for the plot's own work first (vx_sync), so it
+ * may run on a host thread while later plots compute.  Returns after the
+ * data is handed to the file system (no fsync); seconds_d2h = time spent
+ * waiting for device copies, seconds_total = the whole call.  Synchronous. */
 int vx_plot_write(vx_plot *plot, const char *path, double *seconds_d2h, double *seconds_total);
 
 /* Runs vx_table1 + vx_match for n plots as one batch: every stage is one
