@@ -78,6 +78,12 @@ def lib():
             L.orc_match_bruteforce.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64, u32p,
                                                ctypes.c_uint64]
             L.orc_match_bruteforce.restype = ctypes.c_int64
+            L.orc_match_global.argtypes = [u8p, u8p, ctypes.c_uint64, ctypes.c_uint64, u8p,
+                                           ctypes.c_uint64]
+            L.orc_match_global.restype = ctypes.c_int64
+            L.orc_match_global_bruteforce.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64, u32p,
+                                                      ctypes.c_uint64]
+            L.orc_match_global_bruteforce.restype = ctypes.c_int64
             _lib = L
     return _lib
 
@@ -205,6 +211,30 @@ def match_bruteforce(recs_unsorted: np.ndarray, D: int) -> np.ndarray:
     out = np.zeros((n, 2), dtype=np.uint32)
     L.orc_match_bruteforce(_p(recs, ctypes.c_uint8), recs.shape[0], D,
                            _p(out, ctypes.c_uint32), n)
+    return out
+
+
+def match_global(key: bytes, t1: np.ndarray, D: int) -> np.ndarray:
+    """Table 2 of the cross-bucket variant: every pair i < j of the whole
+    Table-1 order with key64_j - key64_i < D, in i / j order."""
+    t1 = np.ascontiguousarray(t1, dtype=np.uint8)
+    L = lib()
+    kp, tp = _p(_key_arr(key), ctypes.c_uint8), _p(t1, ctypes.c_uint8)
+    n = int(L.orc_match_global(kp, tp, t1.shape[0], D, None, 0))
+    out = np.zeros((n, T2_BYTES), dtype=np.uint8)
+    got = L.orc_match_global(kp, tp, t1.shape[0], D, _p(out, ctypes.c_uint8), n)
+    assert got == n
+    return out
+
+
+def match_global_bruteforce(recs_unsorted: np.ndarray, D: int) -> np.ndarray:
+    """Cross-bucket pairs (a, b) by an O(n^2) scan of the unsorted records."""
+    recs = np.ascontiguousarray(recs_unsorted, dtype=np.uint8)
+    L = lib()
+    n = int(L.orc_match_global_bruteforce(_p(recs, ctypes.c_uint8), recs.shape[0], D, None, 0))
+    out = np.zeros((n, 2), dtype=np.uint32)
+    L.orc_match_global_bruteforce(_p(recs, ctypes.c_uint8), recs.shape[0], D,
+                                  _p(out, ctypes.c_uint32), n)
     return out
 
 

@@ -18,7 +18,9 @@
  *            with key64_j - key64_i < D, D = 2^(64-K) by default (R8, R9),
  *            emits {LE32 a, LE32 b, hash2[0..7]} where
  *            hash2 = BLAKE3-keyed(key, LE32(a) || LE32(b)) (R10), in bucket,
- *            then i, then j order (R11).
+ *            then i, then j order (R11).  A cross-bucket variant
+ *            (orc_match_global) takes every pair of the whole Table-1 order
+ *            under the same threshold.
  *
  * BLAKE3 here is the single-block, single-chunk case of the BLAKE3
  * specification (messages of at most 64 bytes), which is all the plotter
@@ -326,6 +328,61 @@ int64_t orc_match_bruteforce(const uint8_t *recs, uint64_t n, uint64_t D,
             int before = (kx < ky) || (kx == ky && nx < ny);
             if (!before) continue;
             if (!(ky - kx < D)) continue;
+            if (pairs && count < cap) {
+                pairs[2 * count] = nx;
+                pairs[2 * count + 1] = ny;
+            }
+            count++;
+        }
+    }
+    return (int64_t)count;
+}
+
+/* Cross-bucket variant of the match (the "global" scope): every pair i < j
+ * of the whole Table-1 order with key64_j - key64_i < D, whatever the
+ * logical buckets, emitted in i, then j order.  The paper's match compares
+ * pairs against the threshold (Sec. II-B) inside one bucket (the fused
+ * Sort+Match kernel, Sec. III-A); this variant drops the bucket edge. */
+int64_t orc_match_global(const uint8_t key[32], const uint8_t *t1, uint64_t n, uint64_t D,
+                         uint8_t *t2, uint64_t cap)
+{
+    uint64_t count = 0;
+    for (uint64_t x = 0; x < n; x++) {
+        uint64_t kx = rec_key64(t1 + 12 * x);
+        for (uint64_t y = x + 1; y < n; y++) {
+            uint64_t ky = rec_key64(t1 + 12 * y);
+            if (!(ky - kx < D)) break;
+            if (t2 && count < cap) {
+                uint8_t msg[8];
+                uint8_t *out = t2 + 16 * count;
+                memcpy(msg, t1 + 12 * x, 4);
+                memcpy(msg + 4, t1 + 12 * y, 4);
+                memcpy(out, msg, 8);
+                orc_keyed_hash(key, msg, 8, out + 8, 8);
+            }
+            count++;
+        }
+    }
+    return (int64_t)count;
+}
+
+/* Brute force of the cross-bucket variant: every ordered pair of the
+ * UNSORTED records, x before y in (key64, nonce) order, key64 gap < D. */
+int64_t orc_match_global_bruteforce(const uint8_t *recs, uint64_t n, uint64_t D,
+                                    uint32_t *pairs, uint64_t cap)
+{
+    uint64_t count = 0;
+    for (uint64_t x = 0; x < n; x++) {
+        const uint8_t *rx = recs + 12 * x;
+        uint64_t kx = rec_key64(rx);
+        uint32_t nx = rec_nonce(rx);
+        for (uint64_t y = 0; y < n; y++) {
+            if (y == x) continue;
+            const uint8_t *ry = recs + 12 * y;
+            uint64_t ky = rec_key64(ry);
+            uint32_t ny = rec_nonce(ry);
+            int before = (kx < ky) || (kx == ky && nx < ny);
+            if (!before || !(ky - kx < D)) continue;
             if (pairs && count < cap) {
                 pairs[2 * count] = nx;
                 pairs[2 * count + 1] = ny;

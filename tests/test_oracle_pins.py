@@ -236,3 +236,87 @@ def test_paper_numbers_fixture():
     assert abs(11 * 2 ** 31 / 1e9 - 24.7) > abs(t1_gb - 24.7)
     assert abs(13 * 2 ** 31 / 1e9 - 24.7) > abs(t1_gb - 24.7)
     assert orc.default_distance(31) == 2 ** 33
+
+
+# ---------------------------------------------------------------------------
+# Cross-bucket variant of the match (every pair of the whole Table-1 order
+# under the threshold; Sec. II-B's pairwise match without the bucket edge).
+
+def _numpy_pairs_global(recs: np.ndarray, D: int) -> set:
+    """O(n^2) numpy scan of the cross-bucket predicate over unsorted records."""
+    k = orc.key64(recs)
+    nz = orc.nonces(recs)
+    before = (k[:, None] < k[None, :]) | ((k[:, None] == k[None, :]) & (nz[:, None] < nz[None, :]))
+    with np.errstate(over="ignore"):
+        close = (k[None, :] - k[:, None]) < np.uint64(D)
+    xs, ys = np.nonzero(before & close)
+    return set(zip(nz[xs].tolist(), nz[ys].tolist()))
+
+
+@pytest.mark.parametrize("K,seed,shift", [(8, 20, 0), (11, 21, 0), (12, 22, 0), (12, 23, 30),
+                                          (10, 24, 36)])
+def test_match_global_equals_bruteforce(K, seed, shift):
+    key = plot_key(seed)
+    raw = orc.table1_unsorted(K, key)
+    if shift:
+        # squeeze the keys so that many pairs straddle logical buckets
+        k = orc.key64(raw) >> np.uint64(shift)
+        raw = _records(k << np.uint64(shift - 4), orc.nonces(raw))
+    t1 = orc.sort_table1(raw)
+    D = orc.default_distance(K) >> np.uint64(shift // 2) if shift else orc.default_distance(K)
+    D = int(D)
+    t2 = orc.match_global(key, t1, D)
+    got = set(zip(orc.nonces(t2[:, 0:4]).tolist(), orc.nonces(t2[:, 4:8]).tolist()))
+    assert len(got) == t2.shape[0]
+    ref = _numpy_pairs_global(raw, D)
+    assert got == ref
+    bf = orc.match_global_bruteforce(raw, D)
+    assert set(map(tuple, bf.tolist())) == ref
+    # i, then j order over the whole Table 1; hash2 recomputes (R10)
+    pos = {int(nv): i for i, nv in enumerate(orc.nonces(t1))}
+    ranks = [(pos[a], pos[b]) for a, b in zip(orc.nonces(t2[:, 0:4]).tolist(),
+                                               orc.nonces(t2[:, 4:8]).tolist())]
+    assert ranks == sorted(ranks)
+    for r in range(0, t2.shape[0], max(1, t2.shape[0] // 13)):
+        assert t2[r, 8:].tobytes() == orc.keyed_hash(key, t2[r, :8].tobytes(), 8)
+
+
+def test_match_global_contains_bucket_match():
+    # With D at most the bucket width the bucket-scope pairs are exactly the
+    # cross-bucket variant's pairs whose two keys share a logical bucket,
+    # in the same relative order.
+    key = plot_key(25)
+    t1 = orc.table1(16, key)
+    for D in [1 << 40, 1 << 38, 1 << 35]:
+        g = orc.match_global(key, t1, D)
+        b = orc.match(key, t1, D)
+        kg = {int(n): int(k) for n, k in zip(orc.nonces(t1), orc.key64(t1))}
+        same = [r for r in g if (kg[int(r[:4].view("<u4")[0])] >> 40) ==
+                (kg[int(r[4:8].view("<u4")[0])] >> 40)]
+        assert np.array_equal(np.array(same, dtype=np.uint8).reshape(-1, 16), b)
+
+
+def test_match_global_closed_form_pair_count():
+    # N uniform key64 values: a pair is within D with probability 2u - u^2,
+    # u = D / 2^64, so E|T2| = C(N,2)(2u - u^2) ~ N at the default distance
+    # 2^(64-K).  Each record's partner count is ~Poisson(1): Var ~ 3N/2.
+    for K, seed in [(16, 26), (18, 27)]:
+        N = 1 << K
+        got = orc.match_global(plot_key(seed), orc.table1(K, plot_key(seed)),
+                               orc.default_distance(K)).shape[0]
+        u = orc.default_distance(K) / 2.0 ** 64
+        E = N * (N - 1) / 2 * (2 * u - u * u)
+        assert abs(got - E) < 6 * math.sqrt(2 * N), (K, got, E)
+
+
+def test_match_global_all_pairs():
+    # D = 2^64 - 1 matches every pair except those exactly 2^64 - 1 apart:
+    # C(N, 2) records, (i, j) in lexicographic order of Table-1 ranks.
+    K, key = 7, plot_key(28)
+    t1 = orc.table1(K, key)
+    t2 = orc.match_global(key, t1, (1 << 64) - 1)
+    n = t1.shape[0]
+    assert t2.shape[0] == n * (n - 1) // 2
+    nz = orc.nonces(t1).tolist()
+    want = [(nz[i], nz[j]) for i in range(n) for j in range(i + 1, n)]
+    assert list(zip(orc.nonces(t2[:, 0:4]).tolist(), orc.nonces(t2[:, 4:8]).tolist())) == want
