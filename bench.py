@@ -249,6 +249,8 @@ def main():
     ap.add_argument("--pipeline-chunks", type=int, default=0)
     ap.add_argument("--t2-placement", type=int, default=0,
                     help="0 automatic, 1 look-back, 2 pair slots")
+    ap.add_argument("--match-scope", type=int, default=0,
+                    help="0 pairs inside a logical bucket, 1 cross-bucket")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: requests per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
     ap.add_argument("--write-K", type=int, default=28, help="write: K of every plot")
@@ -468,7 +470,7 @@ def main():
 def plot_opts(vx, args):
     return vx.make_opts(partition_log2=args.partition_log2, scatter_mode=args.scatter_mode,
                         fuse_pair_hash=args.fuse_pair_hash, pipeline_chunks=args.pipeline_chunks,
-                        t2_placement=args.t2_placement)
+                        t2_placement=args.t2_placement, match_scope=args.match_scope)
 
 
 def _timed(fn, stream):

@@ -119,7 +119,16 @@ typedef struct vx_opts {
                                    default D a partition expects ~2040 +- 100 pairs
                                    against 3910 places); 0 = automatic = 1 (the
                                    faster on GB300 at K=31)                        */
-    uint32_t reserved[5];       /* must be zero                                      */
+    uint32_t match_scope;       /* 0 = (default) pairs inside one logical bucket
+                                   (the fused Sort+Match kernel of Sec. III-A holds
+                                   one bucket); 1 = cross-bucket: every pair i < j
+                                   of the whole Table-1 order with key64_j - key64_i
+                                   < D.  The few records within D of the next
+                                   physical partition's lower edge (a "halo", mean
+                                   2^11 * D / 2^(64-p) records) are collected while
+                                   the partitions are filled; needs D <= 2^(64-p)
+                                   and a halo of at most 256 records             */
+    uint32_t reserved[4];       /* must be zero                                      */
 } vx_opts;
 
 typedef struct vx_plot vx_plot;

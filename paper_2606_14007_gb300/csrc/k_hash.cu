@@ -40,6 +40,7 @@ __global__ void k_key_setup(Desc *descs)
         if (i < n2) {
             d.cnt2[i] = 0u;
             d.lb[i] = 0ull;
+            if (d.hcap) d.halo_cnt[i] = 0u;
         }
         if (i < n1) d.cnt1[i] = 0u;
         if (i < nchunks) d.lbs[i] = 0ull;
@@ -109,7 +110,7 @@ __device__ __forceinline__ void scan_and_claim(uint32_t *hist, uint32_t *loff, u
     }
 }
 
-template <int NT, int NPT, bool AGG>
+template <int NT, int NPT, bool AGG, bool HALO>
 __global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ descs, int nplots,
                                                      const uint32_t *__restrict__ tile_start,
                                                      int chunk)
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ de
     }
     __syncthreads();
     const uint32_t count = (uint32_t)((N - base) < (uint64_t)T ? (N - base) : (uint64_t)T);
-    bool overflow = false;
+    bool overflow = false, hover = false;
     for (uint32_t i = threadIdx.x; i < count; i += NT) {
         const uint64_t k = sm.keys[i];
         const uint32_t bin = bits ? (uint32_t)(k >> (64 - bits)) : 0u;
@@ -180,16 +181,18 @@ __global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ de
         } else {
             overflow = true;
         }
+        if (HALO && !two_level) halo_add(d, bin, k, sm.nonces[i], hover);  // final partitions
     }
     if (overflow) atomicOr(d.status, two_level ? kStSlot1Overflow : kStSlot2Overflow);
+    if (hover) atomicOr(d.status, kStHaloOverflow);
 }
 
-template <int NT, int NPT, bool AGG>
+template <int NT, int NPT, bool AGG, bool HALO>
 static cudaError_t launch_hs(const Desc *descs, int nplots, const uint32_t *tile_start,
                              uint32_t total_tiles, int chunk, cudaStream_t s)
 {
     const size_t smem = sizeof(HashSmem<NT, NPT>);
-    auto fn = k_hash_scatter<NT, NPT, AGG>;
+    auto fn = k_hash_scatter<NT, NPT, AGG, HALO>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<total_tiles, NT, smem, s>>>(descs, nplots, tile_start, chunk);
@@ -198,15 +201,17 @@ static cudaError_t launch_hs(const Desc *descs, int nplots, const uint32_t *tile
 
 // AGG (warp-aggregated ranks) pays off when a warp's 32 records fall into
 // few bins; the host picks it from the smallest bin count in the launch.
+// HALO instances carry the cross-bucket halo code; plain launches do not.
 cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *tile_start,
                                 uint32_t total_tiles, HashCfg cfg, int chunk, cudaStream_t s)
 {
     if (total_tiles == 0) return cudaSuccess;
-    if (cfg.agg)
-        return launch_hs<kHashThreads, kHashNoncesPerThread, true>(descs, nplots, tile_start,
-                                                                   total_tiles, chunk, s);
-    return launch_hs<kHashThreads, kHashNoncesPerThread, false>(descs, nplots, tile_start,
-                                                                total_tiles, chunk, s);
+    constexpr int T = kHashThreads, P = kHashNoncesPerThread;
+    if (cfg.halo)
+        return cfg.agg ? launch_hs<T, P, true, true>(descs, nplots, tile_start, total_tiles, chunk, s)
+                       : launch_hs<T, P, false, true>(descs, nplots, tile_start, total_tiles, chunk, s);
+    return cfg.agg ? launch_hs<T, P, true, false>(descs, nplots, tile_start, total_tiles, chunk, s)
+                   : launch_hs<T, P, false, false>(descs, nplots, tile_start, total_tiles, chunk, s);
 }
 
 // ------------------------------------------------- hash + direct scatter
@@ -216,7 +221,7 @@ cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *t
 // a global atomic and stores key64 and nonce there.  No shared memory and
 // no second scatter pass; the claims and scattered stores run on the LSU
 // and L2 while the ALU pipe -- the kernel's bound -- keeps hashing.
-template <int NT, int NPT>
+template <int NT, int NPT, bool HALO>
 __global__ void __launch_bounds__(NT) k_hash_direct(const Desc *__restrict__ descs, int nplots,
                                                     const uint32_t *__restrict__ tile_start,
                                                     int chunk)
@@ -245,7 +250,7 @@ __global__ void __launch_bounds__(NT) k_hash_direct(const Desc *__restrict__ des
         const uint32_t bin = bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u;
         slot[j] = nonce < N ? atomicAdd(&d.cnt2[bin], 1u) : 0xffffffffu;
     }
-    bool overflow = false;
+    bool overflow = false, hover = false;
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
         const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
@@ -258,16 +263,22 @@ __global__ void __launch_bounds__(NT) k_hash_direct(const Desc *__restrict__ des
         } else {
             overflow = true;
         }
+        if (HALO) halo_add(d, bin, key[j], (uint32_t)nonce, hover);
     }
     if (overflow) atomicOr(d.status, kStSlot2Overflow);
+    if (hover) atomicOr(d.status, kStHaloOverflow);
 }
 
 cudaError_t launch_hash_direct(const Desc *descs, int nplots, const uint32_t *tile_start,
-                               uint32_t total_tiles, int chunk, cudaStream_t s)
+                               uint32_t total_tiles, int chunk, cudaStream_t s, bool halo)
 {
     if (total_tiles == 0) return cudaSuccess;
-    k_hash_direct<kHashThreads, kHashNoncesPerThread><<<total_tiles, kHashThreads, 0, s>>>(
-        descs, nplots, tile_start, chunk);
+    if (halo)
+        k_hash_direct<kHashThreads, kHashNoncesPerThread, true><<<total_tiles, kHashThreads, 0, s>>>(
+            descs, nplots, tile_start, chunk);
+    else
+        k_hash_direct<kHashThreads, kHashNoncesPerThread, false><<<total_tiles, kHashThreads, 0, s>>>(
+            descs, nplots, tile_start, chunk);
     return cudaGetLastError();
 }
 

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kMatchThreads) k_match(const Desc *__restrict_
     if (P == 0) return;
     const uint64_t off = d.t1off[f];
     const uint32_t n = (uint32_t)(d.t1off[f + 1] - off);
-    const MatchLayout L(d.cap2);
+    const MatchLayout L(d.cap2 + d.hcap);  // + the next partition's halo
     uint64_t *keys = reinterpret_cast<uint64_t *>(smem_raw);
     uint32_t *nonces = reinterpret_cast<uint32_t *>(smem_raw + L.nonces);
     uint32_t *start = reinterpret_cast<uint32_t *>(smem_raw + L.start);
@@ -60,10 +60,36 @@ __global__ void __launch_bounds__(kMatchThreads) k_match(const Desc *__restrict_
         if (q == 0) nonces[r] = v;
         else khalf[2 * r + (q == 1 ? 1 : 0)] = bswap32(v);
     }
+    // Cross-bucket match: the next partition's first records within D of
+    // its lower edge (a prefix of its sorted Table-1 run) follow this
+    // partition's records, so the pair scan runs on into them.
+    const uint64_t D = d.D;
+    uint32_t nt = n;
+    if (d.hcap && f + 1 < np) {
+        const uint64_t hoff = d.t1off[f + 1];
+        const uint64_t hrun = d.t1off[f + 2] - hoff;
+        const uint32_t hn = (uint32_t)(hrun < d.hcap ? hrun : d.hcap);
+        const uint64_t edge = (uint64_t)(f + 1) << (64 - d.p);
+        bool in = false;
+        uint32_t nv = 0;
+        uint64_t kv = 0;
+        if (threadIdx.x < hn) {
+            const uint32_t *w = reinterpret_cast<const uint32_t *>(d.t1) + 3 * (hoff + threadIdx.x);
+            nv = w[0];
+            kv = ((uint64_t)bswap32(w[1]) << 32) | bswap32(w[2]);
+            in = kv - edge < D;
+        }
+        const uint32_t hc = (uint32_t)__syncthreads_count(in);  // a prefix: keys ascend
+        if (in) {
+            keys[n + threadIdx.x] = kv;
+            nonces[n + threadIdx.x] = nv;
+        }
+        nt = n + hc;
+    }
     __syncthreads();
 
     // Per-record pair counts over a contiguous chunk of records per thread.
-    const uint64_t D = d.D;
+    const bool global = d.scope != 0;
     const uint32_t per = (n + NT - 1) / NT;
     const uint32_t r0 = min(n, threadIdx.x * per), r1 = min(n, r0 + per);
     uint32_t mine = 0;
@@ -71,9 +97,9 @@ __global__ void __launch_bounds__(kMatchThreads) k_match(const Desc *__restrict_
         const uint64_t k = keys[r];
         const uint64_t bucket = k >> 40;
         uint32_t c = 0;
-        for (uint32_t r2 = r + 1; r2 < n; ++r2) {
+        for (uint32_t r2 = r + 1; r2 < nt; ++r2) {
             const uint64_t k2 = keys[r2];
-            if ((k2 >> 40) != bucket || k2 - k >= D) break;
+            if ((!global && (k2 >> 40) != bucket) || k2 - k >= D) break;
             ++c;
         }
         start[r] = c;

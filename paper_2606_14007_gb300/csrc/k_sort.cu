@@ -25,6 +25,7 @@ struct Scatter2Smem {
     uint64_t bar;
 };
 
+template <bool HALO>
 __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__restrict__ descs,
                                                              int nplots,
                                                              const uint32_t *__restrict__ tile_start,
@@ -118,31 +119,34 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__rest
         if (k < per && b0 + k < nbins) sm.gbase[b0 + k] = claim[k];
     __syncthreads();
     const uint32_t cap = d.cap2;
-    bool overflow = false;
+    bool overflow = false, hover = false;
     for (uint32_t i = threadIdx.x; i < count; i += NT) {
         const uint64_t k = sm.keys[i];
         const uint32_t bin = (uint32_t)(k >> shift) & bin_mask;
         const uint32_t g = sm.gbase[bin] + (i - sm.loff[bin]);
+        const uint64_t part = ((uint64_t)c << p2) + bin;
         if (g < cap) {
-            const uint64_t at = (((uint64_t)c << p2) + bin) * cap + g;
+            const uint64_t at = part * cap + g;
             d.b_keys[at] = k;
             d.b_nonces[at] = sm.nonces[i];
         } else {
             overflow = true;
         }
+        if (HALO) halo_add(d, part, k, sm.nonces[i], hover);
     }
     if (overflow) atomicOr(d.status, kStSlot2Overflow);
+    if (hover) atomicOr(d.status, kStHaloOverflow);
 }
 
 cudaError_t launch_scatter2(const Desc *descs, int nplots, const uint32_t *tile_start,
-                            uint32_t total_tiles, int chunk, cudaStream_t s)
+                            uint32_t total_tiles, int chunk, cudaStream_t s, bool halo)
 {
     if (total_tiles == 0) return cudaSuccess;
     const size_t smem = sizeof(Scatter2Smem);
-    cudaError_t e = cudaFuncSetAttribute(k_scatter2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    auto fn = halo ? k_scatter2<true> : k_scatter2<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_scatter2<<<total_tiles, kScatterThreads, smem, s>>>(descs, nplots, tile_start, chunk);
+    fn<<<total_tiles, kScatterThreads, smem, s>>>(descs, nplots, tile_start, chunk);
     return cudaGetLastError();
 }
 

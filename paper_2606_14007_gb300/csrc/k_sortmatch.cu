@@ -62,7 +62,7 @@ struct SMLayout {
     }
 };
 
-template <int MODE>
+template <int MODE, bool HALO>
 __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 5)
     k_sortmatch(const Desc *__restrict__ descs, int nplots, const uint32_t *__restrict__ tile_start)
 {
@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 5)
         }
     }
     const uint32_t ndig = 1u << dbits;
-    const SMLayout L(cap, dbits, MODE == kSortHash);
+    const uint32_t hcap = HALO ? d.hcap : 0u;
+    const SMLayout L(cap + hcap, dbits, MODE == kSortHash);  // + the next partition's halo
     uint64_t *SK = reinterpret_cast<uint64_t *>(smem_raw);
     uint32_t *SN = reinterpret_cast<uint32_t *>(smem_raw + L.sn);
     uint16_t *RK = reinterpret_cast<uint16_t *>(smem_raw + L.rank);
@@ -161,22 +162,53 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 5)
         }
     }
     __syncthreads();
+    // 4b. cross-bucket match: the next partition's halo (its records within
+    //     D of its lower edge, collected while the slots were filled) goes
+    //     sorted right after this partition's records, so the pair scan
+    //     below runs on into it; records n .. nt - 1 start no pairs here.
+    uint32_t nt = n;
+    if (HALO && hcap) {
+        const uint64_t fn = (uint64_t)f + 1;
+        const uint32_t hc = fn < (1ull << d.p) ? min(d.halo_cnt[fn], hcap) : 0u;
+        for (uint32_t h = threadIdx.x; h < hc; h += NT) {
+            SK[n + h] = d.halo_keys[fn * hcap + h];
+            SN[n + h] = d.halo_nonces[fn * hcap + h];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {  // a few records (Poisson, mean 2^11 D / 2^(64-p))
+            for (uint32_t a = n + 1; a < n + hc; ++a) {
+                const uint64_t kx = SK[a];
+                const uint32_t nx = SN[a];
+                uint32_t b = a;
+                for (; b > n && (SK[b - 1] > kx || (SK[b - 1] == kx && SN[b - 1] > nx)); --b) {
+                    SK[b] = SK[b - 1];
+                    SN[b] = SN[b - 1];
+                }
+                SK[b] = kx;
+                SN[b] = nx;
+            }
+        }
+        __syncthreads();
+        nt = n + hc;
+    }
     // 5. pairs starting at each record r: the later records up to
-    //    lim = min(last key of r's logical bucket, key_r + D - 1); four
-    //    probes per step (key64 sorted ascending)
+    //    lim = min(last key of r's logical bucket, key_r + D - 1), or
+    //    key_r + D - 1 for the cross-bucket match; four probes per step
+    //    (key64 sorted ascending)
     const uint64_t D = d.D;
+    const bool global = HALO && d.scope != 0;
     for (uint32_t r = threadIdx.x; r < n; r += NT) {
         const uint64_t k = SK[r];
-        const uint64_t last_in_bucket = k | ((1ull << 40) - 1);
+        const uint64_t last_in_bucket = global ? ~0ull : (k | ((1ull << 40) - 1));
         uint64_t reach = k + (D - 1);
         if (reach < k) reach = ~0ull;  // saturate
         const uint64_t lim = reach < last_in_bucket ? reach : last_in_bucket;
         uint32_t c = 0;
-        for (uint32_t q = r + 1; q < n; q += 4) {
+        for (uint32_t q = r + 1; q < nt; q += 4) {
             const bool m0 = SK[q] <= lim;
-            const bool m1 = m0 && q + 1 < n && SK[q + 1] <= lim;
-            const bool m2 = m1 && q + 2 < n && SK[q + 2] <= lim;
-            const bool m3 = m2 && q + 3 < n && SK[q + 3] <= lim;
+            const bool m1 = m0 && q + 1 < nt && SK[q + 1] <= lim;
+            const bool m2 = m1 && q + 2 < nt && SK[q + 2] <= lim;
+            const bool m3 = m2 && q + 3 < nt && SK[q + 3] <= lim;
             c += (uint32_t)m0 + (uint32_t)m1 + (uint32_t)m2 + (uint32_t)m3;
             if (!m3) break;
         }
@@ -310,34 +342,45 @@ size_t sortmatch_smem_bytes(uint32_t cap, int dbits) { return SMLayout(cap, dbit
 
 uint32_t sortmatch_max_cap() { return 16384u; }
 
-template <int MODE>
+template <int MODE, bool HALO>
 static cudaError_t launch_sm(const Desc *descs, int nplots, const uint32_t *tile_start,
                              uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits)
 {
     if (total_tiles == 0) return cudaSuccess;
     const size_t smem = SMLayout(max_cap, max_dbits, MODE == kSortHash).bytes;
-    auto fn = k_sortmatch<MODE>;
+    auto fn = k_sortmatch<MODE, HALO>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<total_tiles, kSMThreads, smem, s>>>(descs, nplots, tile_start);
     return cudaGetLastError();
 }
 
+template <int MODE>
+static cudaError_t launch_sm2(const Desc *descs, int nplots, const uint32_t *tile_start,
+                              uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits,
+                              bool halo)
+{
+    // HALO instances carry the cross-bucket code; plain launches do not.
+    return halo ? launch_sm<MODE, true>(descs, nplots, tile_start, total_tiles, s, max_cap, max_dbits)
+                : launch_sm<MODE, false>(descs, nplots, tile_start, total_tiles, s, max_cap, max_dbits);
+}
+
 cudaError_t launch_sortmatch(const Desc *descs, int nplots, const uint32_t *tile_start,
                              uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits,
-                             SortMatchOut out)
+                             SortMatchOut out, bool halo)
 {
     if (out == kOutLookbackHashed)
-        return launch_sm<kSortHash>(descs, nplots, tile_start, total_tiles, s, max_cap, max_dbits);
+        return launch_sm2<kSortHash>(descs, nplots, tile_start, total_tiles, s, max_cap, max_dbits, halo);
     if (out == kOutSlots)
-        return launch_sm<kSortSlots>(descs, nplots, tile_start, total_tiles, s, max_cap, max_dbits);
-    return launch_sm<kSortEmit>(descs, nplots, tile_start, total_tiles, s, max_cap, max_dbits);
+        return launch_sm2<kSortSlots>(descs, nplots, tile_start, total_tiles, s, max_cap, max_dbits, halo);
+    return launch_sm2<kSortEmit>(descs, nplots, tile_start, total_tiles, s, max_cap, max_dbits, halo);
 }
 
 cudaError_t launch_sort(const Desc *descs, int nplots, const uint32_t *tile_start,
-                        uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits)
+                        uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits,
+                        bool halo)
 {
-    return launch_sm<kSortCount>(descs, nplots, tile_start, total_tiles, s, max_cap, max_dbits);
+    return launch_sm2<kSortCount>(descs, nplots, tile_start, total_tiles, s, max_cap, max_dbits, halo);
 }
 
 }  // namespace vx

@@ -37,6 +37,7 @@ static_assert(kPlanScanChunk == (uint64_t)kScanChunk, "planner and scan kernel c
 static_assert(kPlanT2HashTile == kT2HashTile, "planner and pair-hash kernel tiles differ");
 static_assert(kPlanT2SlotGroup == (uint64_t)kT2SlotGroup, "planner and slot pair-hash groups differ");
 static_assert(kHashThreads == 256 && kHashNoncesPerThread == 8, "hash shape the planner accepts");
+static_assert(kMatchThreads >= 256, "k_match loads a halo (<= 256 records) one per thread");
 static_assert(sizeof(Desc) + 64 <= kStageTilesOffset, "descriptor overlaps staged tiles");
 static_assert(kStageTilesOffset + kTileArrays * 2 * sizeof(uint32_t) <= kStageResultOffset &&
                   kStageResultOffset + 16 <= kStageBytes,
@@ -45,8 +46,9 @@ int make_plan(int K, const vx_opts *o, Plan *pl, const char **why)
 {
     int rc = make_plan_sized(K, o, pl, why, sizeof(Desc));
     if (rc != VX_OK) return rc;
-    if (pl->cap2 > sortmatch_max_cap() || sortmatch_smem_bytes(pl->cap2, pl->dbits) > kMaxSmemPerCta ||
-        match_smem_bytes(pl->cap2) > kMaxSmemPerCta) {
+    const uint32_t held = pl->cap2 + pl->hcap;  // a partition plus the next one's halo
+    if (held > sortmatch_max_cap() || sortmatch_smem_bytes(held, pl->dbits) > kMaxSmemPerCta ||
+        match_smem_bytes(held) > kMaxSmemPerCta) {
         *why = "partition slot too large for shared memory";
         return VX_EINVAL;
     }
@@ -133,6 +135,8 @@ void fill_desc(const vx_plot *p, Desc *d)
     d->test_flags = pl.test_flags;
     d->hchunks = pl.hchunks;
     d->pchunks = pl.pchunks;
+    d->scope = (uint32_t)pl.scope;
+    d->hcap = pl.hcap;
     if (pl.p2 > 0) {
         d->a_keys = reinterpret_cast<uint64_t *>(p->d_t1);
         d->a_nonces = reinterpret_cast<uint32_t *>(p->d_t1 + pl.regionA_keys);
@@ -150,6 +154,11 @@ void fill_desc(const vx_plot *p, Desc *d)
     d->ticket = reinterpret_cast<uint32_t *>(s + pl.o_ticket);
     d->lbs = reinterpret_cast<uint64_t *>(s + pl.o_lbs);
     d->ticket_s = reinterpret_cast<uint32_t *>(s + pl.o_ticket_s);
+    if (pl.hcap) {
+        d->halo_cnt = reinterpret_cast<uint32_t *>(s + pl.o_halo_cnt);
+        d->halo_keys = reinterpret_cast<uint64_t *>(s + pl.o_halo_keys);
+        d->halo_nonces = reinterpret_cast<uint32_t *>(s + pl.o_halo_nonces);
+    }
     d->t1 = p->d_t1;
     d->t2 = p->d_t2;
     key_words(p->key, d->key);
@@ -171,7 +180,7 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
     const int W = n + 1;
     enum { A_STG = 0, A_DIR = 8, A_S2 = 16, A_PC = 24, A_T2H = 32, A_SCAN = 40, A_PART = 41 };
     static_assert(A_PART + 1 == vx::kTileArrays, "tile arrays");
-    bool fuse = true, slots = true;
+    bool fuse = true, slots = true, halo = false;
     L->G = L->C = 1;
     L->max_cap2 = 0;
     L->max_dbits = 1;
@@ -181,9 +190,10 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
         const Plan &pl = plots[i]->plan;
         fuse = fuse && pl.fuse_pair_hash;
         slots = slots && pl.pair_slots;
+        halo = halo || pl.scope != 0;
         L->G = std::max(L->G, pl.hchunks);
         L->C = std::max(L->C, pl.pchunks);
-        L->max_cap2 = std::max(L->max_cap2, pl.cap2);
+        L->max_cap2 = std::max(L->max_cap2, pl.cap2 + pl.hcap);
         L->max_dbits = std::max(L->max_dbits, pl.dbits);
         if (pl.mode == kScatterStaged) min_bits = std::min(min_bits, pl.p2 > 0 ? pl.p1 : pl.p);
     }
@@ -219,6 +229,7 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
     L->agg = min_bits <= kAggMaxBits;
     L->fuse_pair_hash = fuse;
     L->pair_slots = slots;
+    L->halo = halo;
     for (int g = 0; g < vx::kMaxChunks; ++g) {
         L->t_staged[g] = d + (A_STG + g) * W;
         L->t_direct[g] = d + (A_DIR + g) * W;
@@ -281,7 +292,7 @@ int map_status(uint32_t st)
     if (st & vx::kStTimeout) return VX_ETIMEDOUT;
     if (st & vx::kStBadTicket) return VX_ECUDA;
     if (st & (vx::kStSlot1Overflow | vx::kStSlot2Overflow | vx::kStCountMismatch |
-              vx::kStPartitionTooBig | vx::kStPairSlot))
+              vx::kStPartitionTooBig | vx::kStPairSlot | vx::kStHaloOverflow))
         return VX_EOVERFLOW;
     if (st & vx::kStT2Capacity) return VX_ENOMEM;
     return VX_OK;
@@ -296,6 +307,7 @@ std::string status_text(uint32_t st)
     if (st & vx::kStPartitionTooBig) s += "partition larger than shared memory; ";
     if (st & vx::kStT2Capacity) s += "Table 2 exceeds its capacity; ";
     if (st & vx::kStPairSlot) s += "a partition's pairs exceed its pair slot (use t2_placement 1); ";
+    if (st & vx::kStHaloOverflow) s += "a partition's cross-bucket halo exceeds its capacity; ";
     if (st & vx::kStTimeout) s += "device wait timed out; ";
     if (st & vx::kStBadTicket) s += "work ticket out of range (state not reset); ";
     return s;
@@ -340,16 +352,17 @@ cudaError_t launch_front(const LaunchSet &L, const vx::Lanes &ln, const vx::Trac
     for (int g = 0; g < L.G; ++g) {
         if (L.n_staged[g])
             VX_LAUNCH(KID_STAGED, A, vx::launch_hash_scatter(L.descs, L.n, L.t_staged[g], L.n_staged[g],
-                                                             vx::HashCfg{L.agg}, g, A));
+                                                             vx::HashCfg{L.agg, L.halo}, g, A));
         if (L.n_direct[g])
-            VX_LAUNCH(KID_DIRECT, A, vx::launch_hash_direct(L.descs, L.n, L.t_direct[g], L.n_direct[g], g, A));
+            VX_LAUNCH(KID_DIRECT, A, vx::launch_hash_direct(L.descs, L.n, L.t_direct[g], L.n_direct[g], g, A,
+                                                            L.halo));
         if (L.n_s2[g]) {
             if (ov) {
                 cudaEventRecord(ln.sync[g], A);
                 cudaStreamWaitEvent(B, ln.sync[g], 0);
-                VX_LAUNCH(KID_S2, B, vx::launch_scatter2(L.descs, L.n, L.t_s2[g], L.n_s2[g], g, B));
+                VX_LAUNCH(KID_S2, B, vx::launch_scatter2(L.descs, L.n, L.t_s2[g], L.n_s2[g], g, B, L.halo));
             } else {
-                VX_LAUNCH(KID_S2, A, vx::launch_scatter2(L.descs, L.n, L.t_s2[g], L.n_s2[g], g, A));
+                VX_LAUNCH(KID_S2, A, vx::launch_scatter2(L.descs, L.n, L.t_s2[g], L.n_s2[g], g, A, L.halo));
             }
         }
     }
@@ -367,7 +380,8 @@ cudaError_t launch_table1(const LaunchSet &L, const vx::Lanes &ln, const vx::Tra
     const cudaError_t e = launch_front(L, ln, T);
     if (e != cudaSuccess) return e;
     const cudaStream_t A = ln.main;
-    VX_LAUNCH(KID_SORT, A, vx::launch_sort(L.descs, L.n, L.t_part, L.n_part, A, L.max_cap2, L.max_dbits));
+    VX_LAUNCH(KID_SORT, A, vx::launch_sort(L.descs, L.n, L.t_part, L.n_part, A, L.max_cap2, L.max_dbits,
+                                           L.halo));
     return cudaSuccess;
 }
 
@@ -390,7 +404,7 @@ cudaError_t launch_fused(const LaunchSet &L, const vx::Lanes &ln, const vx::Trac
     if (L.pair_slots) {
         // slot placement: sort + match, pair-count scan, slot pair hash
         VX_LAUNCH(KID_SORTMATCH, A, vx::launch_sortmatch(L.descs, L.n, L.t_pchunk[0], L.n_pchunk[0], A,
-                                                         L.max_cap2, L.max_dbits, vx::kOutSlots));
+                                                         L.max_cap2, L.max_dbits, vx::kOutSlots, L.halo));
         VX_LAUNCH(KID_SCANP, A, vx::launch_scan_pair_counts(L.descs, L.n, L.t_scan, L.n_scan, A));
         VX_LAUNCH(KID_PAIRHASH, A, vx::launch_t2_hash_slots(L.descs, L.n, L.t_t2h[0], L.n_t2h[0], A));
         return cudaSuccess;
@@ -402,7 +416,8 @@ cudaError_t launch_fused(const LaunchSet &L, const vx::Lanes &ln, const vx::Trac
             VX_LAUNCH(KID_SORTMATCH, A, vx::launch_sortmatch(L.descs, L.n, L.t_pchunk[c], L.n_pchunk[c], A,
                                                              L.max_cap2, L.max_dbits,
                                                              L.fuse_pair_hash ? vx::kOutLookbackHashed
-                                                                              : vx::kOutLookback));
+                                                                              : vx::kOutLookback,
+                                                             L.halo));
         if (ph && L.n_t2h[c]) {
             if (ov) {
                 cudaEventRecord(ln.sync[vx::kMaxChunks + 1 + c], A);

@@ -38,6 +38,7 @@ struct LaunchSet {
     bool agg;
     bool fuse_pair_hash;
     bool pair_slots;   // every plot uses the slot placement (t_t2h[0] = slot pair-hash grid)
+    bool halo;         // some plot matches across buckets: kernels with the halo code
     uint32_t max_cap2;
     int max_dbits;
 };

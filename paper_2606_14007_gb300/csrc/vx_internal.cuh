@@ -32,6 +32,7 @@ constexpr uint32_t kStPartitionTooBig = 1u << 4;
 constexpr uint32_t kStTimeout = 1u << 5;
 constexpr uint32_t kStBadTicket = 1u << 6;
 constexpr uint32_t kStPairSlot = 1u << 7;     // a partition's pairs exceed its pair slot
+constexpr uint32_t kStHaloOverflow = 1u << 8; // a partition's halo exceeds its capacity
 
 // ------------------------------------------------------ plot descriptor
 // One plot's plan and buffers.  The host fills everything but pre1/pre2,
@@ -53,6 +54,11 @@ struct Desc {
     uint32_t test_flags; // vx_opts.test_flags (fault injection)
     int32_t hchunks;     // nonce chunks (hash / second-scatter pipeline); level-1 slots per chunk
     int32_t pchunks;     // partition chunks (sort / pair-hash pipeline)
+    uint32_t scope;      // match: 0 = inside a logical bucket, 1 = cross-bucket
+    uint32_t hcap;       // halo records per partition (scope 1 with p > 0), else 0
+    uint32_t *halo_cnt;  // [2^p] halo fill counters
+    uint64_t *halo_keys; // [2^p * hcap] records of partition f within D of its
+    uint32_t *halo_nonces; //            lower edge (unsorted): f - 1's halo
     uint64_t *a_keys;    // level-1 slots, SoA: key64 [hchunks * 2^p1 * cap1]
     uint32_t *a_nonces;  //                      nonce [hchunks * 2^p1 * cap1]
     uint64_t *b_keys;    // level-2 slots, SoA: key64 [2^p * cap2]
@@ -387,6 +393,23 @@ __device__ __forceinline__ bool lookback_warp(uint64_t *lb, uint32_t f, uint64_t
     return lb_resolve(lb, f, agg, status, limit, withhold, excl_out);
 }
 
+// Cross-bucket match (scope 1): a record within D of its partition's lower
+// edge also belongs to the halo of the partition before (partition 0 has
+// no predecessor).  Called by every kernel that fills the final partitions.
+__device__ __forceinline__ void halo_add(const Desc &d, uint64_t part, uint64_t key, uint32_t nonce,
+                                         bool &overflow)
+{
+    if (d.hcap == 0 || part == 0) return;
+    if ((key & (~0ull >> d.p)) >= d.D) return;  // offset inside the partition (p >= 1)
+    const uint32_t h = atomicAdd(&d.halo_cnt[part], 1u);
+    if (h < d.hcap) {
+        d.halo_keys[part * d.hcap + h] = key;
+        d.halo_nonces[part * d.hcap + h] = nonce;
+    } else {
+        overflow = true;
+    }
+}
+
 // -------------------------------------------------- TMA bulk copy helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -443,6 +466,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
 namespace vx {
 struct HashCfg {
     bool agg;     // warp-aggregated histogram (few first-level bins)
+    bool halo;    // some plot of the launch matches across buckets (halo code)
 };
 cudaError_t launch_key_setup(Desc *descs, int nplots, cudaStream_t s);
 // Hash kernels and the second scatter level take one nonce chunk (of
@@ -450,14 +474,14 @@ cudaError_t launch_key_setup(Desc *descs, int nplots, cudaStream_t s);
 cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *tile_start,
                                 uint32_t total_tiles, HashCfg cfg, int chunk, cudaStream_t s);
 cudaError_t launch_hash_direct(const Desc *descs, int nplots, const uint32_t *tile_start,
-                               uint32_t total_tiles, int chunk, cudaStream_t s);
+                               uint32_t total_tiles, int chunk, cudaStream_t s, bool halo);
 // Sort + match variants: Table-2 records at final offsets found by a
 // look-back ({a, b, 0, 0}, hashed later by launch_t2_hash; or hashed in the
 // kernel), or pairs {a, b} written into each partition's own slot.
 enum SortMatchOut { kOutLookback = 0, kOutLookbackHashed = 1, kOutSlots = 2 };
 cudaError_t launch_sortmatch(const Desc *descs, int nplots, const uint32_t *tile_start,
                              uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits,
-                             SortMatchOut out);
+                             SortMatchOut out, bool halo);
 cudaError_t launch_t2_hash(const Desc *descs, int nplots, const uint32_t *tile_start,
                            uint32_t total_tiles, int chunk, cudaStream_t s);
 // Pair hash of the slot placement: kT2SlotGroup partitions per CTA, pairs
@@ -469,7 +493,7 @@ constexpr uint64_t kT2HashTile = 256 * 8;  // Table-2 records per pair-hash CTA
 size_t sortmatch_smem_bytes(uint32_t cap, int dbits);
 uint32_t sortmatch_max_cap();  // largest slot the sort keeps in registers
 cudaError_t launch_scatter2(const Desc *descs, int nplots, const uint32_t *tile_start,
-                            uint32_t total_tiles, int chunk, cudaStream_t s);
+                            uint32_t total_tiles, int chunk, cudaStream_t s, bool halo);
 cudaError_t launch_scan_counts(const Desc *descs, int nplots, const uint32_t *tile_start,
                                uint32_t total_tiles, cudaStream_t s);
 // Same chunked look-back scan over the per-partition pair counts (slot
@@ -478,7 +502,8 @@ cudaError_t launch_scan_pair_counts(const Desc *descs, int nplots, const uint32_
                                     uint32_t total_tiles, cudaStream_t s);
 constexpr uint32_t kScanChunk = 4096;      // counters per CTA of the Table-1 offset scan
 cudaError_t launch_sort(const Desc *descs, int nplots, const uint32_t *tile_start,
-                        uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits);
+                        uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits,
+                        bool halo);
 cudaError_t launch_scan_pairs(const Desc *descs, int nplots, cudaStream_t s);
 cudaError_t launch_match(const Desc *descs, int nplots, const uint32_t *tile_start,
                          uint32_t total_tiles, cudaStream_t s, uint32_t max_cap);

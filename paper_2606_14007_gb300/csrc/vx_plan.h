@@ -40,6 +40,8 @@ struct Plan {
     uint32_t test_flags, spin_limit;
     bool fuse_pair_hash;
     bool pair_slots;                       // pairs staged in the partition slots (t2_placement 2)
+    int scope;                             // 0 bucket-scope match, 1 cross-bucket
+    uint32_t hcap;                         // halo records per partition (scope 1, p > 0)
     int hchunks;                           // nonce chunks of the hash / second-scatter pipeline
     int pchunks;                           // partition chunks of the sort / pair-hash pipeline
     uint64_t N, D, t2cap;
@@ -55,6 +57,7 @@ struct Plan {
     uint64_t o_status, o_ticket, o_ticket_s, o_cnt1, o_cnt2, o_t1off, o_pairs, o_t2off, o_lb, o_lbs,
         o_desc, o_tiles;
     uint64_t o_regionB;                    // final-partition slots (scratch buffer)
+    uint64_t o_halo_cnt, o_halo_keys, o_halo_nonces;  // scope 1 halos (scratch buffer)
 };
 
 inline uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
@@ -75,6 +78,15 @@ inline double expected_pairs(uint64_t N, uint64_t D)
     const double u = (double)D / 1099511627776.0;
     const double q = u >= 1.0 ? 1.0 : 2.0 * u - u * u;
     return 16777216.0 * lam * lam / 2.0 * q;
+}
+
+// Expected pairs of the cross-bucket match: N uniform key64 values, a pair
+// within D with probability 2u - u^2, u = D / 2^64.
+inline double expected_pairs_global(uint64_t N, uint64_t D)
+{
+    const double u = (double)D / 18446744073709551616.0;
+    const double q = u >= 1.0 ? 1.0 : 2.0 * u - u * u;
+    return (double)N * ((double)N - 1.0) / 2.0 * q;
 }
 
 inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, size_t desc_bytes)
@@ -109,7 +121,7 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
         return VX_EINVAL;
     }
     P.test_flags = opts.test_flags;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
         if (opts.reserved[i]) {
             *why = "reserved vx_opts fields must be zero";
             return VX_EINVAL;
@@ -201,10 +213,33 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     }
     P.pair_slots = opts.t2_placement == kPlaceSlots;
 
+    // Cross-bucket match: partition f's pairs reach into partition f + 1
+    // only (D at most one partition wide), through the records of f + 1
+    // within D of its lower edge, Poisson with mean avg2 * D / 2^(64-p).
+    if (opts.match_scope > 1) {
+        *why = "match_scope must be 0 (bucket) or 1 (cross-bucket)";
+        return VX_EINVAL;
+    }
+    P.scope = (int)opts.match_scope;
+    P.hcap = 0;
+    if (P.scope == 1 && P.p > 0) {
+        const double W = std::ldexp(1.0, 64 - P.p);
+        if ((double)P.D > W) {
+            *why = "match_scope 1 needs match_distance <= 2^(64-p), one partition";
+            return VX_EINVAL;
+        }
+        const uint64_t hc = slot_capacity(avg2 * (double)P.D / W, slack);
+        if (hc > 256) {
+            *why = "match_scope 1: match distance gives a halo of more than 256 records";
+            return VX_EINVAL;
+        }
+        P.hcap = (uint32_t)hc;
+    }
+
     if (opts.t2_capacity) {
         P.t2cap = opts.t2_capacity;
     } else {
-        const double E = expected_pairs(P.N, P.D);
+        const double E = P.scope ? expected_pairs_global(P.N, P.D) : expected_pairs(P.N, P.D);
         P.t2cap = round_up((uint64_t)std::ceil(E + 24.0 * std::sqrt(E) + 4096.0), 256);
     }
     // Grids (tile sizes are the kernels' compile-time tiles).
@@ -255,6 +290,10 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     P.o_desc = at; at = round_up(at + desc_bytes, 256);
     P.o_tiles = at; at = round_up(at + 512, 256);
     P.o_regionB = at; at = round_up(at + P.regionB_bytes, 256);
+    const uint64_t nh = P.hcap ? np : 0;
+    P.o_halo_cnt = at; at = round_up(at + 4 * nh, 256);
+    P.o_halo_keys = at; at = round_up(at + 8 * nh * P.hcap, 256);
+    P.o_halo_nonces = at; at = round_up(at + 4 * nh * P.hcap, 256);
     P.scratch_bytes = at;
     *pl = P;
     return VX_OK;

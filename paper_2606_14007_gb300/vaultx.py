@@ -50,7 +50,8 @@ class vx_opts(ctypes.Structure):
         ("fuse_pair_hash", ctypes.c_uint32),
         ("pipeline_chunks", ctypes.c_uint32),
         ("t2_placement", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 5),
+        ("match_scope", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 4),
     ]
 
 

@@ -85,7 +85,9 @@ def test_required_bytes_rejects_bad_arguments(vx):
                dict(coarse_bits=11, scatter_mode=1), dict(scatter_mode=3),
                dict(slack_sigma=400, partition_log2=12), dict(t2_placement=3),
                dict(t2_placement=2, pipeline_chunks=2), dict(t2_placement=2, fuse_pair_hash=1),
-               dict(hash_block=128), dict(nonces_per_thread=4)]:
+               dict(hash_block=128), dict(nonces_per_thread=4), dict(match_scope=2),
+               dict(match_scope=1, match_distance=1 << 60),        # wider than a partition
+               dict(match_scope=1, match_distance=1 << 43)]:       # halo of ~1024 records
         with pytest.raises(vx.VxError):
             vx.vx_plot_required_bytes(31, vx.make_opts(**kw))
     vx.vx_plot_required_bytes(31, vx.make_opts(hash_block=256, nonces_per_thread=8))
@@ -144,3 +146,17 @@ def test_partition_plan_shape(vx):
     t1a, _, _ = vx.vx_plot_required_bytes(31, o)
     t1b, _, _ = vx.vx_plot_required_bytes(31)
     assert t1a >= 12 * 2 ** 31 and t1b >= 12 * 2 ** 31
+
+
+def test_cross_bucket_scope_plans_a_halo(vx):
+    # The cross-bucket match keeps, per partition, the next partition's
+    # records within D of its edge: mean 2^11 D / 2^(64-p) = 1 at the
+    # default D, so the halo arrays are small beside the partition slots.
+    _, _, sb = vx.vx_plot_required_bytes(31)
+    _, t2g, sg = vx.vx_plot_required_bytes(31, vx.make_opts(match_scope=1))
+    assert sb < sg < sb * 1.03
+    assert t2g >= 16 * 2 ** 31  # E|T2| = N for the cross-bucket match
+    h = vx.vx_plot_create(31, bytes(32), vx.make_opts(match_scope=1))
+    assert vx.vx_plot_kernel_mask(h) == ["key_setup", "hash_staged", "scatter2", "scan_counts",
+                                         "sortmatch", "pairhash"]
+    vx.vx_plot_destroy(h)

@@ -46,6 +46,12 @@ def oracle_plot(K, key, D=None):
     return t1, t2
 
 
+def oracle_plot_global(K, key, D=None):
+    t1 = orc.table1(K, key)
+    t2 = orc.match_global(key, t1, orc.default_distance(K) if D is None else D)
+    return t1, t2
+
+
 def test_hash_row_matches_oracle(vx):
     key = plot_key(3)
     for nonce0, count in [(0, 5000), (2 ** 32 - 3000, 3000), (123456789, 777), (2 ** 31 - 5, 10)]:
@@ -122,6 +128,43 @@ def test_plot_matches_oracle(vx, K, seed, kw, split):
     assert n2 == r2.shape[0]
     assert np.array_equal(t2, r2)
     assert np.array_equal(off.astype(np.uint64), orc.bucket_offsets(r1))
+
+
+# Cross-bucket match (every pair of the whole Table-1 order under D): the
+# halo of the next partition joins each partition's pair scan.
+GLOBAL_CASES = [
+    (1, 0, {}), (5, 3, {}), (11, 5, {}), (12, 6, {}), (14, 8, {}), (16, 9, {}), (20, 11, {}),
+    (22, 0, {}), (22, 0, DIRECT), (17, 18, STAGED), (19, 32, dict(partition_log2=7)),
+    (16, 12, dict(STAGED, partition_log2=6, coarse_bits=4)),   # two levels, 1024 partitions
+    (20, 24, dict(partition_log2=8, pipeline_chunks=8)),
+    (16, 22, FUSED), (14, 8, SLOTS), (20, 19, dict(partition_log2=6, t2_placement=2)),
+    (16, 20, dict(match_distance=1 << 44)),                    # fewer pairs than records
+    (14, 31, dict(match_distance=1 << 52)),                    # ~4 halo records per partition
+    (18, 33, dict(partition_log2=6, match_distance=1 << 49)),  # ~8 per partition, 4096 of them
+]
+
+
+@pytest.mark.parametrize("split", [False, True], ids=["fused", "split"])
+@pytest.mark.parametrize("K,seed,kw", GLOBAL_CASES)
+def test_cross_bucket_match_matches_oracle(vx, K, seed, kw, split):
+    key = plot_key(seed)
+    t1, t2, n2, _ = run_plot(vx, K, key, vx.make_opts(match_scope=1, **kw), split)
+    r1, r2 = oracle_plot_global(K, key, kw.get("match_distance"))
+    assert np.array_equal(t1, r1)
+    assert n2 == r2.shape[0]
+    assert np.array_equal(t2, r2)
+
+
+def test_cross_bucket_halo_overflow_is_reported(vx):
+    # 4096 partitions of ~64 records, D one partition wide: halos of ~64
+    # records against 64 + 1 sd + 16 places; some overflow, and the plot must
+    # say so (VX_EOVERFLOW naming the halo), never drop pairs silently.
+    p = vx.Plot(18, plot_key(34), vx.make_opts(match_scope=1, partition_log2=6, slack_sigma=1,
+                                               match_distance=1 << 52))
+    p.run()
+    assert vx.vx_sync(p.handle, check=False) == vx.VX_EOVERFLOW
+    assert "halo" in vx.last_error(p.handle)
+    p.close()
 
 
 @pytest.mark.parametrize("split", [False, True], ids=["fused", "split"])
