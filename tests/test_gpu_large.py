@@ -135,3 +135,70 @@ def test_plot_k27_properties(vx):
 
 def test_plot_k31_properties(vx):
     check_plot(vx, 31, 31)
+
+
+def test_plot_k32_properties(vx):
+    # K=32 in one GB300 (about 185 GB: Table 1 51.5 GB, Table 2 68.7 GB,
+    # partition slots 62 GB), no chunking.  Without a 2^32-entry position
+    # map: Table 1 strictly increasing with nonce sums of a permutation of
+    # 0..N-1 (sum and sum of squares mod 2^64), the pair count equal to an
+    # independent count and to the closed form, and sampled Table-2 pairs
+    # re-derived by the oracle (same bucket, distance, hash).
+    K, seed = 32, 32
+    key = plot_key(seed)
+    N = 1 << K
+    D = 1 << (64 - K)
+    p = vx.Plot(K, key)
+    p.run()
+    n2 = p.sync()
+    t1 = p.t1
+    dev = t1.device
+    s1 = torch.zeros((), dtype=torch.int64, device=dev)
+    s2 = torch.zeros((), dtype=torch.int64, device=dev)
+    independent = 0
+    prev = None
+    for s in range(0, N, CHUNK):
+        e = min(N, s + CHUNK)
+        nonce, hi, lo = fields(t1[s:e])
+        s1 += nonce.sum()
+        s2 += (nonce * nonce).sum()  # wraps mod 2^64, like the reference below
+        if prev is not None:
+            nonce = torch.cat([prev[0], nonce]); hi = torch.cat([prev[1], hi]); lo = torch.cat([prev[2], lo])
+        inc = (hi[1:] > hi[:-1]) | ((hi[1:] == hi[:-1]) & ((lo[1:] > lo[:-1]) |
+                                                           ((lo[1:] == lo[:-1]) & (nonce[1:] > nonce[:-1]))))
+        assert bool(inc.all()), "Table 1 not sorted near record %d" % s
+        prev = (nonce[-1:], hi[-1:], lo[-1:])
+        ahead = min(N, e + 4096)
+        _, hi2, lo2 = fields(t1[s:ahead])
+        bucket = hi2 >> 8
+        k40 = ((hi2 & 0xFF) << 32) | lo2
+        n_own = e - s
+        idx = torch.arange(n_own, device=dev)
+        alive = torch.ones(n_own, dtype=torch.bool, device=dev)
+        k = 1
+        while bool(alive.any()):
+            j = idx + k
+            ok = j < bucket.shape[0]
+            jj = torch.where(ok, j, torch.zeros_like(j))
+            m = alive & ok & (bucket[jj] == bucket[:n_own]) & ((k40[jj] - k40[:n_own]) < D)
+            independent += int(m.sum())
+            alive = m
+            k += 1
+            assert k < 4096, "look-ahead too short"
+    wrap = lambda x: (x + (1 << 63)) % (1 << 64) - (1 << 63)  # noqa: E731
+    assert int(s1) == wrap(N * (N - 1) // 2)
+    assert int(s2) == wrap((N - 1) * N * (2 * N - 1) // 6)
+    assert n2 == independent, (n2, independent)
+    lam = N / 2 ** 24
+    E = 2 ** 24 * (lam - 0.5)
+    assert abs(n2 - E) < 8 * math.sqrt(8 * N), (n2, E)
+    rng = np.random.default_rng(seed)
+    for r in t1[torch.from_numpy(rng.integers(0, N, 2000)).to(dev)].cpu().numpy():
+        assert r[4:].tobytes() == orc.keyed_hash(key, r[:4].tobytes(), 8)
+    for r in p.t2[torch.from_numpy(rng.integers(0, n2, 3000)).to(dev)].cpu().numpy():
+        assert r[8:].tobytes() == orc.keyed_hash(key, r[:8].tobytes(), 8)
+        ka = int.from_bytes(orc.keyed_hash(key, r[0:4].tobytes(), 8), "big")
+        kb = int.from_bytes(orc.keyed_hash(key, r[4:8].tobytes(), 8), "big")
+        assert ka >> 40 == kb >> 40 and 0 <= kb - ka < D
+    p.close()
+    torch.cuda.empty_cache()
