@@ -238,6 +238,23 @@ def match_global_bruteforce(recs_unsorted: np.ndarray, D: int) -> np.ndarray:
     return out
 
 
+def table2_key(t2: np.ndarray) -> np.ndarray:
+    """key2 of Table-2 records: big-endian u64 of the hash2 bytes (8..15)."""
+    t2 = np.ascontiguousarray(t2, dtype=np.uint8)
+    return t2[:, 8:16].copy().view(">u8").reshape(-1).astype(np.uint64)
+
+
+def sort_table2(t2: np.ndarray) -> np.ndarray:
+    """Table 2 ordered by (key2, a, b) ascending: the same 16-byte records,
+    sorted by their hash for lookups (NEXT-3); numpy's stable lexsort as the
+    sorting step, ties on key2 broken by the pair's nonces."""
+    t2 = np.ascontiguousarray(t2, dtype=np.uint8)
+    a = t2[:, 0:4].copy().view("<u4").reshape(-1)
+    b = t2[:, 4:8].copy().view("<u4").reshape(-1)
+    order = np.lexsort((b, a, table2_key(t2)))
+    return t2[order]
+
+
 def plot(K: int, key: bytes, D: int | None = None):
     """(Table 1, Table 2) of one plot."""
     t1 = table1(K, key)

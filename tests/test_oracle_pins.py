@@ -320,3 +320,36 @@ def test_match_global_all_pairs():
     nz = orc.nonces(t1).tolist()
     want = [(nz[i], nz[j]) for i in range(n) for j in range(i + 1, n)]
     assert list(zip(orc.nonces(t2[:, 0:4]).tolist(), orc.nonces(t2[:, 4:8]).tolist())) == want
+
+
+# ---------------------------------------------------------------------------
+# Table 2 sorted by hash2 (NEXT-3): the same records ordered by (key2, a, b).
+
+def test_sort_table2_hand_example():
+    # five records, two with equal hash2 (tie broken by a, then b)
+    def rec(a, b, h):
+        return (np.array([a, b], dtype="<u4").view(np.uint8).tolist() +
+                list(int(h).to_bytes(8, "big")))
+    rows = np.array([rec(7, 9, 0x0200), rec(1, 2, 0xFFFF000000000000), rec(3, 4, 0x0200),
+                     rec(3, 1, 0x0200), rec(9, 9, 0x0001)], dtype=np.uint8)
+    got = orc.sort_table2(rows)
+    want = rows[[4, 3, 2, 0, 1]]
+    assert np.array_equal(got, want)
+
+
+def test_sort_table2_is_an_ordered_permutation():
+    key = plot_key(40)
+    t1 = orc.table1(15, key)
+    t2 = orc.match_global(key, t1, orc.default_distance(15))
+    s = orc.sort_table2(t2)
+    # same multiset of records
+    assert np.array_equal(np.sort(t2.view("V16").reshape(-1)), np.sort(s.view("V16").reshape(-1)))
+    # ascending (key2, a, b) between neighbours
+    k = orc.table2_key(s).astype(object)
+    a = s[:, 0:4].copy().view("<u4").reshape(-1).astype(object)
+    b = s[:, 4:8].copy().view("<u4").reshape(-1).astype(object)
+    keys = list(zip(k, a, b))
+    assert all(x < y for x, y in zip(keys, keys[1:]))
+    # key2 is the big-endian reading of the hash bytes the record carries
+    r = s[len(s) // 2]
+    assert int(orc.table2_key(s[len(s) // 2: len(s) // 2 + 1])[0]) == int.from_bytes(r[8:].tobytes(), "big")
