@@ -238,11 +238,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=6)
     ap.add_argument("--e2e-copy-streams", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "large", "serve", "write"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "large", "serve", "write", "sort2"],
                     help="plain: the K=31 headline; batch: 64 mixed-K plots batched vs plain; "
                          "large: 4 x K=29 + 8 x K=27 batched vs plain; serve: Poisson requests "
                          "through the continuous-batching server vs one at a time; write: plots "
-                         "written to flat Table-2 files, serial vs overlapped with the next plot")
+                         "written to flat Table-2 files, serial vs overlapped with the next plot; "
+                         "sort2: Table 2 of a K plot sorted by hash2")
     ap.add_argument("--partition-log2", type=int, default=0)
     ap.add_argument("--scatter-mode", type=int, default=0)
     ap.add_argument("--fuse-pair-hash", type=int, default=0)
@@ -703,6 +704,61 @@ def run_write(vx, args):
             "data": "synthetic"}
 
 
+def run_sort2(vx, args):
+    """NEXT-3: Table 2 of a K plot sorted by hash2 (vx_sort_table2), timed
+    with CUDA events; the result is checked on the device: ascending
+    (key2, a, b) and the same multiset of records (sums of the words)."""
+    import torch
+    from paper_2606_14007_gb300.inputs import plot_key
+    K = args.K
+    stream = torch.cuda.current_stream()
+    p = vx.Plot(K, plot_key(K), plot_opts(vx, args))
+    p.run(stream)
+    n2 = p.sync()
+    wb = vx.vx_sort_table2_work_bytes(p.handle)
+    work = torch.empty(wb, dtype=torch.uint8, device="cuda")
+
+    def words_sum():
+        acc = torch.zeros(4, dtype=torch.int64, device="cuda")
+        for s in range(0, n2, 1 << 27):
+            acc += p.t2[s:min(n2, s + (1 << 27))].view(torch.int32).to(torch.int64).sum(0)
+        return acc.tolist()
+
+    before = words_sum()
+    for _ in range(args.warmup):
+        vx.vx_sort_table2(p.handle, work.data_ptr(), wb, stream)
+    ms = _timed(lambda: [vx.vx_sort_table2(p.handle, work.data_ptr(), wb, stream)
+                         for _ in range(args.steps)], stream) / args.steps
+    ok = vx.vx_sync(p.handle, check=False) == vx.VX_OK and words_sum() == before
+    t2 = p.t2
+    step = 1 << 27
+    prev = None
+    for s in range(0, n2, step):
+        b = t2[s:min(n2, s + step)].long()
+        a_ = b[:, 0] | (b[:, 1] << 8) | (b[:, 2] << 16) | (b[:, 3] << 24)
+        b_ = b[:, 4] | (b[:, 5] << 8) | (b[:, 6] << 16) | (b[:, 7] << 24)
+        hi = (b[:, 8] << 24) | (b[:, 9] << 16) | (b[:, 10] << 8) | b[:, 11]
+        lo = (b[:, 12] << 24) | (b[:, 13] << 16) | (b[:, 14] << 8) | b[:, 15]
+        if prev is not None:
+            a_, b_, hi, lo = (torch.cat([x, y]) for x, y in zip(prev, (a_, b_, hi, lo)))
+        inc = (hi[1:] > hi[:-1]) | ((hi[1:] == hi[:-1]) & (
+            (lo[1:] > lo[:-1]) | ((lo[1:] == lo[:-1]) & (
+                (a_[1:] > a_[:-1]) | ((a_[1:] == a_[:-1]) & (b_[1:] > b_[:-1]))))))
+        ok = ok and bool(inc.all())
+        prev = (a_[-1:], b_[-1:], hi[-1:], lo[-1:])
+    pk = peaks()
+    algo = 96 * n2  # two scatter levels and the sort, each reads and writes 16 B per record
+    out = {"mode": "sort2", "metric": "Table 2 sorted by hash2, records/s", "unit": "records/s",
+           "K": K, "table2_records": n2, "value": n2 / (ms / 1e3), "ms_per_sort": ms,
+           "work_bytes": wb, "algorithmic_bytes": algo,
+           "hbm": {"achieved_gbs": algo / (ms / 1e3) / 1e9, "peak_gbs": pk["hbm_gbs"],
+                   "frac": algo / (ms / 1e3) / 1e9 / pk["hbm_gbs"]},
+           "sorted_and_same_records": bool(ok), "steps": args.steps, "warmup": args.warmup,
+           "data": "synthetic"}
+    p.close()
+    return out
+
+
 def run_mode(args):
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -720,6 +776,8 @@ def run_mode(args):
                                 "aggregate nonces/s, 4 x K=29 + 8 x K=27 sharing HBM", "large")
     elif args.mode == "write":
         out = run_write(vx, args)
+    elif args.mode == "sort2":
+        out = run_sort2(vx, args)
     else:
         out = run_serve(vx, args)
     if int(os.environ.get("RANK", "0")) == 0:

@@ -218,6 +218,19 @@ int vx_table1_offsets(vx_plot *plot, void *d_out, void *stream);
 int vx_table_copy(vx_plot *plot, int which, uint64_t offset, void *host_dst, uint64_t bytes,
                   void *stream);
 
+/* Table 2 sorted by its hash, for lookups by hash value (the VaultX prover
+ * searches a plot by hash, Sec. I-B; the paper's Table 2 stays in pair
+ * order).  Reorders the plot's Table 2 in place into ascending (key2, a, b),
+ * key2 = big-endian u64 of the record's hash2 bytes; records are unchanged.
+ * Needs the plot complete and synced (vx_sync returned VX_OK; VX_ENOTREADY
+ * otherwise) and a caller-owned device work buffer of at least
+ * vx_sort_table2_work_bytes (256-byte aligned; about 36.5 B per Table-2
+ * record: two scatter levels of 16-byte records; the library never frees
+ * it).  Asynchronous on stream; vx_sync then reports VX_EOVERFLOW if a slot
+ * overflowed (Table 2 is then left partly rewritten). */
+int vx_sort_table2_work_bytes(const vx_plot *plot, uint64_t *bytes);
+int vx_sort_table2(vx_plot *plot, void *d_work, uint64_t work_bytes, void *stream);
+
 /* Writes Table 2 as a flat binary file (Sec. III-A / III-B: D2H through a
  * 256 MB pinned staging buffer on the library's own copy stream, sequential
  * 4 MB chunks; no header).  The device copy of one 128 MB half overlaps the

@@ -292,7 +292,7 @@ int map_status(uint32_t st)
     if (st & vx::kStTimeout) return VX_ETIMEDOUT;
     if (st & vx::kStBadTicket) return VX_ECUDA;
     if (st & (vx::kStSlot1Overflow | vx::kStSlot2Overflow | vx::kStCountMismatch |
-              vx::kStPartitionTooBig | vx::kStPairSlot | vx::kStHaloOverflow))
+              vx::kStPartitionTooBig | vx::kStPairSlot | vx::kStHaloOverflow | vx::kStSort2))
         return VX_EOVERFLOW;
     if (st & vx::kStT2Capacity) return VX_ENOMEM;
     return VX_OK;
@@ -308,6 +308,7 @@ std::string status_text(uint32_t st)
     if (st & vx::kStT2Capacity) s += "Table 2 exceeds its capacity; ";
     if (st & vx::kStPairSlot) s += "a partition's pairs exceed its pair slot (use t2_placement 1); ";
     if (st & vx::kStHaloOverflow) s += "a partition's cross-bucket halo exceeds its capacity; ";
+    if (st & vx::kStSort2) s += "sorting Table 2: a slot overflowed or records were lost; ";
     if (st & vx::kStTimeout) s += "device wait timed out; ";
     if (st & vx::kStBadTicket) s += "work ticket out of range (state not reset); ";
     return s;
@@ -694,6 +695,73 @@ int vx_sync(vx_plot *p)
     const int rc = map_status(st);
     if (rc != VX_OK) set_err(p, status_text(st));
     return rc;
+}
+
+// --------------------------------------------------- sorted Table 2
+namespace {
+int sort2_plan(const vx_plot *p, vx::Sort2Plan *sp)
+{
+    if (p->stage < 2 || !p->t2_known || p->status != 0) return VX_ENOTREADY;
+    if (vx::make_sort2_plan(p->t2_count, sp, sizeof(vx::Sort2Desc)) != VX_OK) return VX_EINVAL;
+    return VX_OK;
+}
+}  // namespace
+
+int vx_sort_table2_work_bytes(const vx_plot *p, uint64_t *bytes)
+{
+    if (!p || !bytes) return VX_EINVAL;
+    vx::Sort2Plan sp;
+    const int rc = sort2_plan(p, &sp);
+    if (rc != VX_OK) return rc;
+    *bytes = sp.bytes;
+    return VX_OK;
+}
+
+int vx_sort_table2(vx_plot *p, void *d_work, uint64_t work_bytes, void *stream)
+{
+    if (!p || !d_work || ((uintptr_t)d_work % 256) != 0) return VX_EINVAL;
+    vx::Sort2Plan sp;
+    int rc = sort2_plan(p, &sp);
+    if (rc != VX_OK) return rc;
+    if (work_bytes < sp.bytes) {
+        set_err(p, "work buffer smaller than vx_sort_table2_work_bytes");
+        return VX_EINVAL;
+    }
+    if (p->t2_count == 0) return VX_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t *w = (uint8_t *)d_work;
+    const vx::Plan &pl = p->plan;
+    vx::Sort2Desc d;
+    memset(&d, 0, sizeof(d));
+    d.count = reinterpret_cast<const uint64_t *>(p->d_scratch + pl.o_t2off + 8 * (1ull << pl.p));
+    d.p = sp.p;
+    d.p1 = sp.p1;
+    d.p2 = sp.p2;
+    d.dbits = sp.dbits;
+    d.cap1 = sp.cap1;
+    d.cap2 = sp.cap2;
+    d.chunks1 = sp.chunks1;
+    d.spin_limit = pl.spin_limit;
+    d.t2 = reinterpret_cast<uint4 *>(p->d_t2);
+    d.a_keys = reinterpret_cast<uint64_t *>(w + sp.o_akeys);
+    d.a_vals = reinterpret_cast<uint64_t *>(w + sp.o_avals);
+    d.b_keys = reinterpret_cast<uint64_t *>(w + sp.o_bkeys);
+    d.b_vals = reinterpret_cast<uint64_t *>(w + sp.o_bvals);
+    d.cnt1 = reinterpret_cast<uint32_t *>(w + sp.o_cnt1);
+    d.cnt2 = reinterpret_cast<uint32_t *>(w + sp.o_cnt2);
+    d.off = reinterpret_cast<uint64_t *>(w + sp.o_off);
+    d.lbs = reinterpret_cast<uint64_t *>(w + sp.o_lbs);
+    d.ticket = reinterpret_cast<uint32_t *>(w + sp.o_ticket);
+    d.status = reinterpret_cast<uint32_t *>(p->d_scratch + pl.o_status);
+    vx::Sort2Desc *dd = reinterpret_cast<vx::Sort2Desc *>(w + sp.o_desc);
+    VX_TRY(p, cudaMemcpyAsync(dd, &d, sizeof(d), cudaMemcpyHostToDevice, s));
+    const vx::Sort2Launch g{sp.tiles1, sp.tiles2, sp.tiles_scan, sp.parts, sp.cap2, sp.dbits};
+    cudaError_t e = vx::launch_sort2(dd, g, s);
+    if (e != cudaSuccess) return cuda_fail(p, "sort Table 2", e);
+    p->last = s;
+    p->have_last = true;
+    p->res_pending = false;
+    return record_result(p, s);  // vx_sync now waits for the sort and reads its status
 }
 
 int vx_table_info(const vx_plot *p, int which, const void **dptr, uint64_t *nrec,

@@ -33,6 +33,7 @@ constexpr uint32_t kStTimeout = 1u << 5;
 constexpr uint32_t kStBadTicket = 1u << 6;
 constexpr uint32_t kStPairSlot = 1u << 7;     // a partition's pairs exceed its pair slot
 constexpr uint32_t kStHaloOverflow = 1u << 8; // a partition's halo exceeds its capacity
+constexpr uint32_t kStSort2 = 1u << 9;        // sorted Table 2: slot overflow or lost records
 
 // ------------------------------------------------------ plot descriptor
 // One plot's plan and buffers.  The host fills everything but pre1/pre2,
@@ -79,6 +80,27 @@ struct Desc {
     uint32_t pre1[16];   // Table-1 hash state after round-1 columns 1..3
     uint32_t pre2[16];   // pair-hash state after round-1 columns 1..3
 };
+
+// Table 2 sorted by hash2 (vx_sort_table2): one plot's second sorting pass
+// over 16-byte records, with its own slots in a caller-provided work buffer.
+struct Sort2Desc {
+    const uint64_t *count; // device word with the Table-2 record count
+    int32_t p;             // partition bits (2^p partitions of ~2^11 records)
+    int32_t p1, p2;        // first / second scatter level bits (p = p1 + p2)
+    int32_t dbits;         // counting-sort digit bits inside a partition
+    uint32_t cap1, cap2;   // slot capacities (records) of the two levels
+    uint32_t chunks1;      // second-level CTAs per first-level slot
+    uint32_t spin_limit;   // polls before a bounded wait gives up
+    uint4 *t2;             // Table 2: read by the first level, rewritten sorted
+    uint64_t *a_keys, *a_vals; // first-level slots [2^p1][cap1]: key2, a << 32 | b
+    uint64_t *b_keys, *b_vals; // partitions [2^p][cap2]
+    uint32_t *cnt1, *cnt2; // fill counters
+    uint64_t *off;         // [2^p + 1] partition offsets in the sorted table
+    uint64_t *lbs;         // look-back words of the offset scan
+    uint32_t *ticket;      // chunk ticket of the offset scan
+    uint32_t *status;      // the plot's status word
+};
+
 
 // Nonces [lo, hi) of chunk `chunk` of a plot (chunks split 2^K evenly).
 __device__ __forceinline__ void nonce_chunk(const Desc &d, int chunk, uint64_t &lo, uint64_t &hi)
@@ -508,6 +530,13 @@ cudaError_t launch_scan_pairs(const Desc *descs, int nplots, cudaStream_t s);
 cudaError_t launch_match(const Desc *descs, int nplots, const uint32_t *tile_start,
                          uint32_t total_tiles, cudaStream_t s, uint32_t max_cap);
 cudaError_t launch_bucket_offsets(const Desc *desc, uint64_t *out, cudaStream_t s);
+// Table 2 sorted by hash2: grids of the five kernels of one sort.
+struct Sort2Launch {
+    uint32_t tiles1, tiles2, tiles_scan, parts, cap2;
+    int dbits;
+};
+cudaError_t launch_sort2(const Sort2Desc *d_desc, const Sort2Launch &g, cudaStream_t s);
+size_t sort2_smem_bytes(uint32_t cap, int dbits);
 cudaError_t launch_hash_records(const uint32_t key[8], uint64_t nonce0, uint64_t count,
                                 uint32_t *out, cudaStream_t s);
 cudaError_t launch_pair_hash(const uint32_t key[8], const uint32_t *pairs, uint64_t count,

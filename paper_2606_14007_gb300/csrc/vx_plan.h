@@ -299,4 +299,63 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     return VX_OK;
 }
 
+// Table 2 sorted by hash2 (vx_sort_table2): partitions of ~2^11 of the n
+// Table-2 records by the top p bits of key2 (uniform hash bits, so slot
+// fills are Poisson), two scatter levels of <= 10 bits, and a work buffer
+// holding both levels' slots (16 B per record) and the counters.
+struct Sort2Plan {
+    int p, p1, p2, dbits;
+    uint32_t cap1, cap2, chunks1;
+    uint32_t tiles1, tiles2, tiles_scan, parts;
+    uint64_t o_desc, o_ticket, o_cnt1, o_cnt2, o_off, o_lbs, o_akeys, o_avals, o_bkeys, o_bvals;
+    uint64_t bytes;
+};
+
+inline int make_sort2_plan(uint64_t n, Sort2Plan *out, size_t desc_bytes)
+{
+    Sort2Plan S;
+    memset(&S, 0, sizeof(S));
+    int lg = 0;
+    while (lg < 63 && (2ull << lg) <= n) ++lg;  // floor(log2(n)), 0 for n <= 1
+    S.p = lg - kDefaultPartLog2;
+    if (S.p < 0) S.p = 0;
+    if (S.p > kMaxPartBits) S.p = kMaxPartBits;
+    S.p1 = S.p <= 10 ? S.p : S.p / 2;
+    S.p2 = S.p - S.p1;
+    const double avg2 = (double)n / (double)(1ull << S.p);
+    uint64_t cap2 = S.p == 0 ? round_up(n, 4) : slot_capacity(avg2, kDefaultSlackSigma);
+    if (cap2 < 4) cap2 = 4;
+    if (cap2 > 16384) return VX_EINVAL;
+    S.cap2 = (uint32_t)cap2;
+    int db = lg - S.p;
+    if (db < 1) db = 1;
+    if (db > 13) db = 13;
+    S.dbits = db;
+    if (S.p2 > 0) {
+        const uint64_t cap1 = slot_capacity((double)n / (double)(1ull << S.p1), kDefaultSlackSigma);
+        if (cap1 > 0xFFFFFF00ull) return VX_EINVAL;
+        S.cap1 = (uint32_t)cap1;
+        S.chunks1 = (uint32_t)((cap1 + 4095) / 4096);
+        S.tiles2 = (uint32_t)((1u << S.p1) * S.chunks1);
+    }
+    S.tiles1 = (uint32_t)((n + 2047) / 2048);
+    S.parts = 1u << S.p;
+    S.tiles_scan = (uint32_t)((S.parts + kPlanScanChunk - 1) / kPlanScanChunk);
+    const uint64_t np = S.parts, n1 = S.p2 > 0 ? (1ull << S.p1) : 0ull;
+    uint64_t at = 0;
+    S.o_desc = at; at = round_up(at + desc_bytes, 256);
+    S.o_ticket = at; at = round_up(at + 4, 256);
+    S.o_cnt1 = at; at = round_up(at + 4 * n1, 256);
+    S.o_cnt2 = at; at = round_up(at + 4 * np, 256);
+    S.o_off = at; at = round_up(at + 8 * (np + 1), 256);
+    S.o_lbs = at; at = round_up(at + 8 * (uint64_t)S.tiles_scan, 256);
+    S.o_akeys = at; at = round_up(at + 8 * n1 * S.cap1, 256);
+    S.o_avals = at; at = round_up(at + 8 * n1 * S.cap1, 256);
+    S.o_bkeys = at; at = round_up(at + 8 * np * S.cap2, 256);
+    S.o_bvals = at; at = round_up(at + 8 * np * S.cap2, 256);
+    S.bytes = at;
+    *out = S;
+    return VX_OK;
+}
+
 }  // namespace vx

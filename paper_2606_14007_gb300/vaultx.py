@@ -100,6 +100,8 @@ def lib():
             "vx_table1_offsets": (c_int, [vp, vp, vp]),
             "vx_table_copy": (c_int, [vp, c_int, u64, vp, u64, vp]),
             "vx_plot_write": (c_int, [vp, ctypes.c_char_p, P(ctypes.c_double), P(ctypes.c_double)]),
+            "vx_sort_table2_work_bytes": (c_int, [vp, P(u64)]),
+            "vx_sort_table2": (c_int, [vp, vp, u64, vp]),
             "vx_plot_batch": (c_int, [P(vp), c_int, vp]),
             "vx_plot_destroy": (None, [vp]),
             "vx_plot_run_noalloc": (c_int, [c_int, u8p, P(vx_opts), vp, vp, u64, vp, P(u64)]),
@@ -225,6 +227,19 @@ def vx_table1_offsets(plot, d_out: int, stream=None):
 def vx_table_copy(plot, which: int, host_dst: int, nbytes: int, stream=None, offset: int = 0):
     return _check(lib().vx_table_copy(plot, which, offset, host_dst, nbytes, _stream(stream)),
                   "vx_table_copy", plot)
+
+
+def vx_sort_table2_work_bytes(plot) -> int:
+    n = ctypes.c_uint64()
+    _check(lib().vx_sort_table2_work_bytes(plot, ctypes.byref(n)), "vx_sort_table2_work_bytes", plot)
+    return n.value
+
+
+def vx_sort_table2(plot, d_work: int, work_bytes: int, stream=None):
+    """Table 2 reordered in place by (key2, a, b), key2 = big-endian hash2;
+    asynchronous, vx_sync reports its status."""
+    return _check(lib().vx_sort_table2(plot, d_work, work_bytes, _stream(stream)), "vx_sort_table2",
+                  plot)
 
 
 def vx_plot_write(plot, path: str) -> tuple[float, float]:
