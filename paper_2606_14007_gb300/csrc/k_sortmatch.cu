@@ -36,6 +36,9 @@ constexpr int kSMThreads = 256;
 // Tickets between a CTA and the partition whose slot it prefetches into L2:
 // about half of the CTAs resident at once (152 SMs x 5).  Measured at K=31:
 // 38.7 ms for 190..380, 39.0 ms for 760, 41.0 ms (no gain) from 1520 up.
+// Only the filled part is fetched (the whole slot cost 27% extra DRAM
+// reads), its fill count loaded at CTA start and used after step 1 so the
+// load's latency hides under the histogram.
 constexpr uint32_t kSlotPrefetchAhead = 384;
 
 // Shared layout: sorted key64 [cap] | sorted nonce [cap] | rank within the
@@ -86,19 +89,11 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 5)
     }
     const uint32_t cap = d.cap2;
     const int dbits = d.dbits;
-    if (threadIdx.x == 0) {
-        // Warm L2 with the slot of the partition kSlotPrefetchAhead tickets
-        // (CTAs) ahead, so that its CTA's first reads (steps 1, 3) hit L2.
-        const uint64_t fa = (uint64_t)f + kSlotPrefetchAhead;
-        if (fa < (1ull << d.p)) {
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_keys + fa * cap),
-                         "r"(cap * 8u)
-                         : "memory");
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_nonces + fa * cap),
-                         "r"(cap * 4u)
-                         : "memory");
-        }
-    }
+    // Warm L2 with the filled part of the slot of the partition
+    // kSlotPrefetchAhead tickets (CTAs) ahead, so that its CTA's first reads
+    // (steps 1, 3) hit L2; its fill count is read now and used after step 1.
+    const uint64_t fa = (uint64_t)f + kSlotPrefetchAhead;
+    const uint32_t nfa = (threadIdx.x == 0 && fa < (1ull << d.p)) ? min(d.cnt2[fa], cap) : 0u;
     const uint32_t ndig = 1u << dbits;
     const uint32_t hcap = HALO ? d.hcap : 0u;
     const SMLayout L(cap + hcap, dbits, MODE == kSortHash);  // + the next partition's halo
@@ -127,6 +122,15 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 5)
     for (uint32_t i = threadIdx.x; i < n; i += NT) {
         const uint32_t dg = (uint32_t)(key_at(i) >> shift) & dmask;
         RK[i] = (uint16_t)atomicAdd(&DC[dg], 1u);
+    }
+    if (nfa) {
+        const uint32_t nk = (nfa + 1u) & ~1u, nn = (nfa + 3u) & ~3u;  // 16-byte multiples
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_keys + fa * cap),
+                     "r"(nk * 8u)
+                     : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_nonces + fa * cap),
+                     "r"(nn * 4u)
+                     : "memory");
     }
     __syncthreads();
     // 2. digit counters -> digit start positions
