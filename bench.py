@@ -235,7 +235,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--K", type=int, default=31)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=6)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-copy-streams", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="plain", choices=["plain", "batch", "large", "serve", "write", "sort2"],
@@ -401,6 +401,20 @@ def main():
             copy_done[slot].record(copy_streams[0])
             return m
 
+        # the box's device-to-host rate into pinned memory, which bounds e2e:
+        # Table 2 (1 GiB pieces of the plot's buffer) into the ring, untimed
+        torch.cuda.synchronize()
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        probe = min(8 * chunk, plot._t2.numel())
+        with torch.cuda.stream(copy_streams[0]):
+            d0.record()
+            for k, off in enumerate(range(0, probe, chunk)):
+                nb = min(chunk, probe - off)
+                ring[(k % nring) * chunk:(k % nring) * chunk + nb].copy_(plot._t2[off:off + nb],
+                                                                       non_blocking=True)
+            d1.record()
+        torch.cuda.synchronize()
+        d2h_gbs = probe / (d0.elapsed_time(d1) / 1e3) / 1e9
         handles, counts = [], []
         barrier()
         torch.cuda.synchronize()
@@ -432,7 +446,7 @@ def main():
         e2e = {"value": N * args.e2e_steps * world / dt, "unit": UNIT,
                "h2d_bytes_per_step": desc_bytes,
                "d2h_bytes_per_step": int(16 * sum(counts) / len(counts)) + 12,
-               "steps": args.e2e_steps,
+               "steps": args.e2e_steps, "d2h_gbs_measured": d2h_gbs,
                "note": "per step: vx_plot_create from a host key, vx_plot_bind, vx_plot_run, "
                        "vx_sync, Table 2 copied to pinned host memory with vx_table_copy "
                        "(1 GiB pieces on %d copy stream(s)); the copy of plot i overlaps plot "
