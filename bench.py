@@ -16,6 +16,7 @@ step) and reports the same metric.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -254,6 +255,10 @@ def main():
                     help="0 pairs inside a logical bucket, 1 cross-bucket")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: requests per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--serve-streams", type=int, default=0, help="serve: concurrent waves (0 = library default)")
+    ap.add_argument("--serve-max-wave", type=int, default=0, help="serve: plots per wave (0 = library default)")
+    ap.add_argument("--serve-max-inflight", type=int, default=0,
+                    help="serve: plots on the device at once (0 = library default)")
     ap.add_argument("--write-K", type=int, default=28, help="write: K of every plot")
     ap.add_argument("--write-plots", type=int, default=6, help="write: plots per leg")
     ap.add_argument("--write-dir", default=None, help="write: directory for the plot files")
@@ -567,7 +572,14 @@ def run_serve(vx, args):
         return float(np.percentile(np.array(xs), q)) if xs else None
 
     # -- server
-    srv = vx.vx_serve_create()
+    so = None
+    if args.serve_streams or args.serve_max_wave or args.serve_max_inflight:
+        so = vx.vx_serve_opts()
+        so.size = ctypes.sizeof(vx.vx_serve_opts)
+        so.streams = args.serve_streams
+        so.max_wave = args.serve_max_wave
+        so.max_inflight = args.serve_max_inflight
+    srv = vx.vx_serve_create(so)
     lat, done_nonces, failed = [], 0, 0
     pending = {}
     i = 0
@@ -614,6 +626,8 @@ def run_serve(vx, args):
     return {"mode": "serve", "metric": "plot-request latency and aggregate nonces/s",
             "unit": "nonces/s", "rate_per_s": args.rate, "duration_s": args.duration,
             "requests": len(arrivals), "K_range": [22, 29],
+            "server_opts": {"streams": args.serve_streams or "default", "max_wave": args.serve_max_wave or "default",
+                            "max_inflight": args.serve_max_inflight or "default"},
             "served": {"value": done_nonces / served_s, "p50_s": pct(lat, 50), "p99_s": pct(lat, 99),
                        "completed": len(lat), "failed": failed, "wall_s": served_s,
                        "how": "vx_serve_submit/poll: admission by HBM footprint, waves on 2 streams"},
