@@ -333,9 +333,12 @@ typedef struct vx_server vx_server;
 
 typedef struct vx_serve_opts {
     uint32_t size;           /* sizeof(vx_serve_opts)                                  */
-    uint32_t max_inflight;   /* plots on the device at once (running or waiting to be
-                                fetched); 0 = 4 (more plots in flight crowd each
-                                other out of L2: 64 served 10% fewer nonces/s)         */
+    uint32_t max_inflight;   /* plots admitted and not yet fetched by vx_serve_poll
+                                (queued on the device, running, or done and waiting);
+                                0 = 4 (more plots in flight crowd each other out of
+                                L2: 64 served 10% fewer nonces/s).  A fetched plot
+                                no longer counts; its memory stays charged to the
+                                budget until vx_plot_destroy                           */
     uint64_t memory_budget;  /* bytes of device memory the server may hold; 0 = 80% of
                                 free memory at creation                                 */
     uint32_t streams;        /* concurrent waves in flight; 0 = 2                      */

@@ -80,6 +80,7 @@ struct Release {  // release hook context: one per handed-in plot
     std::shared_ptr<Shared> sh;
     uint64_t bytes;
     void *t1, *t2, *scratch;
+    bool inflight = true;  // counted in Shared::inflight until handed to the caller
 };
 
 void CUDART_CB on_wave_done(void *arg)
@@ -98,7 +99,7 @@ void release_plot(void *ctx, vx_plot *p)
         cudaFreeAsync(r->t2, r->sh->free_stream);
         cudaFreeAsync(r->scratch, r->sh->free_stream);
         r->sh->used -= r->bytes;
-        r->sh->inflight -= 1;
+        if (r->inflight) r->sh->inflight -= 1;
     }
     // The buffers belong to the server's pool, not to the plot.
     p->d_t1 = p->d_t2 = p->d_scratch = nullptr;
@@ -346,6 +347,14 @@ int vx_serve_poll(vx_server *S, uint64_t ticket, int *state, vx_plot **out)
     if (r->state == VX_DONE && out && !r->handed) {
         *out = r->plot;
         r->handed = true;
+        // Fetched: no longer in flight (its memory stays charged to the
+        // budget until the caller destroys it).
+        Release *rel = static_cast<Release *>(r->plot->release_ctx);
+        std::lock_guard<std::mutex> lk2(S->sh->mu);
+        if (rel && rel->inflight) {
+            rel->inflight = false;
+            S->sh->inflight -= 1;
+        }
     }
     if (r->state == VX_FAILED && r->plot && !r->handed) {
         vx_plot_destroy(r->plot);   // returns its memory to the budget
