@@ -303,20 +303,25 @@ __global__ void __launch_bounds__(256) k_s2_scan(const Sort2Desc *__restrict__ d
 // ------------------------------------------------------- partition sort
 // One CTA per partition: counting sort on the dbits key bits below the
 // partition prefix, insertion sort of each digit run by (key2, a, b), and
-// the records {a, b, hash2} written at the partition's offset.
+// the records {a, b, hash2} written at the partition's offset.  Shared
+// memory holds each record's key and its index in the slot (12 B with the
+// digit rank), five CTAs per SM; the packed pair is read from the slot (L2)
+// when the record is written out, or when two keys tie.
+constexpr uint32_t kS2PrefetchAhead = 384;  // partitions ahead: ~half the resident CTAs
+
 struct S2SortLayout {
-    size_t vals, rank, dcnt, ws, bytes;
+    size_t idx, rank, dcnt, ws, bytes;
     __host__ __device__ S2SortLayout(uint32_t cap, int dbits)
     {
-        vals = (size_t)cap * 8;
-        rank = vals + (size_t)cap * 8;
+        idx = (size_t)cap * 8;
+        rank = idx + (size_t)((cap + 1) & ~1u) * 2;
         dcnt = rank + (size_t)((cap + 1) & ~1u) * 2;
         ws = dcnt + ((size_t)1 << dbits) * 4;
         bytes = ws + 40 * 4;
     }
 };
 
-__global__ void __launch_bounds__(kS2SortThreads) k_s2_sort(const Sort2Desc *__restrict__ dp)
+__global__ void __launch_bounds__(kS2SortThreads, 5) k_s2_sort(const Sort2Desc *__restrict__ dp)
 {
     constexpr int NT = kS2SortThreads;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -328,7 +333,7 @@ __global__ void __launch_bounds__(kS2SortThreads) k_s2_sort(const Sort2Desc *__r
     const uint32_t ndig = 1u << dbits;
     const S2SortLayout L(cap, dbits);
     uint64_t *SK = reinterpret_cast<uint64_t *>(smem_raw);
-    uint64_t *SV = reinterpret_cast<uint64_t *>(smem_raw + L.vals);
+    uint16_t *SI = reinterpret_cast<uint16_t *>(smem_raw + L.idx);
     uint16_t *RK = reinterpret_cast<uint16_t *>(smem_raw + L.rank);
     uint32_t *DC = reinterpret_cast<uint32_t *>(smem_raw + L.dcnt);
     uint32_t *WS = reinterpret_cast<uint32_t *>(smem_raw + L.ws);
@@ -338,38 +343,53 @@ __global__ void __launch_bounds__(kS2SortThreads) k_s2_sort(const Sort2Desc *__r
     const uint64_t *__restrict__ iv = d.b_vals + (uint64_t)f * cap;
     const int shift = 64 - d.p - dbits;
     const uint32_t dmask = ndig - 1u;
+    // the filled part of the slot kS2PrefetchAhead partitions ahead goes to
+    // L2 after step 1 (its fill count is read now)
+    const uint64_t fa = (uint64_t)f + kS2PrefetchAhead;
+    const uint32_t nfa = (threadIdx.x == 0 && fa < (1ull << d.p)) ? min(d.cnt2[fa], cap) : 0u;
     for (uint32_t i = threadIdx.x; i < ndig; i += NT) DC[i] = 0u;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < n; i += NT)
         RK[i] = (uint16_t)atomicAdd(&DC[(uint32_t)(__ldg(ik + i) >> shift) & dmask], 1u);
+    if (nfa) {
+        const uint32_t nb = ((nfa + 1u) & ~1u) * 8u;  // 16-byte multiple (cap is even)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_keys + fa * cap), "r"(nb)
+                     : "memory");
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_vals + fa * cap), "r"(nb)
+                     : "memory");
+    }
     __syncthreads();
     block_scan_inplace_u32<NT>(DC, ndig, WS);
     for (uint32_t i = threadIdx.x; i < n; i += NT) {
         const uint64_t k = __ldg(ik + i);
         const uint32_t pos = DC[(uint32_t)(k >> shift) & dmask] + RK[i];
         SK[pos] = k;
-        SV[pos] = __ldg(iv + i);
+        SI[pos] = (uint16_t)i;
     }
     __syncthreads();
     for (uint32_t dg = threadIdx.x; dg < ndig; dg += NT) {
         const uint32_t s0 = DC[dg];
         const uint32_t s1 = dg + 1 < ndig ? DC[dg + 1] : n;
         for (uint32_t a = s0 + 1; a < s1; ++a) {
-            const uint64_t kx = SK[a], vx = SV[a];
+            const uint64_t kx = SK[a];
+            const uint16_t ix = SI[a];
             uint32_t b = a;
-            while (b > s0 && (SK[b - 1] > kx || (SK[b - 1] == kx && SV[b - 1] > vx))) {
-                SK[b] = SK[b - 1];
-                SV[b] = SV[b - 1];
+            while (b > s0) {
+                const uint64_t ky = SK[b - 1];
+                // equal keys (rare): order by the packed pair (a << 32 | b)
+                if (ky < kx || (ky == kx && __ldg(iv + SI[b - 1]) < __ldg(iv + ix))) break;
+                SK[b] = ky;
+                SI[b] = SI[b - 1];
                 --b;
             }
             SK[b] = kx;
-            SV[b] = vx;
+            SI[b] = ix;
         }
     }
     __syncthreads();
     uint4 *__restrict__ out = d.t2 + o;
     for (uint32_t r = threadIdx.x; r < n; r += NT) {
-        const uint64_t k = SK[r], v = SV[r];
+        const uint64_t k = SK[r], v = __ldg(iv + SI[r]);
         out[r] = make_uint4((uint32_t)(v >> 32), (uint32_t)v, bswap32((uint32_t)(k >> 32)),
                             bswap32((uint32_t)k));
     }
