@@ -86,21 +86,25 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_scatter1(const Sort2Desc *__r
         rank[j] = valid ? atomicAdd(&sm.hist[bin], 1u) : 0u;
     }
     __syncthreads();
+    constexpr int PB = ((1 << kMaxCoarseBits) + NT - 1) / NT;  // most bins a thread owns
+    const int per = (nbins + NT - 1) / NT;
+    const int b0 = threadIdx.x * per;
+    uint32_t claim[PB];
     {
-        const int per = (nbins + NT - 1) / NT;
-        const int b0 = threadIdx.x * per;
         uint32_t loc = 0;
         for (int k = 0; k < per; ++k)
             if (b0 + k < nbins) loc += sm.hist[b0 + k];
         uint32_t total;
         uint32_t run = block_exclusive_scan_u32<NT>(loc, sm.ws, &total);
-        for (int k = 0; k < per; ++k) {
+#pragma unroll
+        for (int k = 0; k < PB; ++k) {
             const int b = b0 + k;
-            if (b < nbins) {
+            claim[k] = 0u;
+            if (k < per && b < nbins) {
                 const uint32_t h = sm.hist[b];
                 sm.loff[b] = run;
                 run += h;
-                sm.gbase[b] = h ? atomicAdd(&cnt[b], h) : 0u;
+                if (h) claim[k] = atomicAdd(&cnt[b], h);  // result first needed after the restage
             }
         }
     }
@@ -115,6 +119,9 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_scatter1(const Sort2Desc *__r
             sm.vals[pos] = val[j];
         }
     }
+#pragma unroll
+    for (int k = 0; k < PB; ++k)
+        if (k < per && b0 + k < nbins) sm.gbase[b0 + k] = claim[k];
     __syncthreads();
     const uint32_t count = (uint32_t)(n - base < kS2Tile1 ? n - base : kS2Tile1);
     bool overflow = false;
