@@ -183,11 +183,16 @@ int vx_table1(vx_plot *plot, void *stream);
  * count is then in vx_table_info(VX_TABLE2).nrec.  Asynchronous. */
 int vx_match(vx_plot *plot, void *stream);
 
-/* Table 1 and Table 2 in one pass (Sec. III-A pipeline): key setup, hash +
- * bucketing scatter, then the fused partition sort + match kernel, which
- * sorts each partition in shared memory, writes it to Table 1, and hashes
- * its pairs straight into Table 2 at the offset a decoupled look-back over
- * the earlier partitions gives.  Same tables as vx_table1 + vx_match.
+/* Table 1 and Table 2 in one pass (Sec. III-A pipeline): key setup, keyed
+ * BLAKE3 of every nonce fused with the first bucketing scatter level, the
+ * second level, then the fused partition sort + match kernel.  That kernel
+ * sorts each partition in shared memory, writes it to Table 1, and writes
+ * its pairs {a, b} into Table 2 at the offset a decoupled look-back over the
+ * earlier partitions gives.  A streaming pass then hashes the pairs in
+ * place (vx_opts: fuse_pair_hash hashes inside the sort kernel instead,
+ * t2_placement=2 stages the pairs in the partition slots).  Same tables as
+ * vx_table1 + vx_match.  Ends with a 12-byte copy of the status and the
+ * Table-2 count to pinned host memory and an event that vx_sync waits on.
  * Allocates if nothing is bound.  Asynchronous. */
 int vx_plot_run(vx_plot *plot, void *stream);
 

@@ -6,13 +6,14 @@
 // K=31 bottleneck and proposes a parallel radix sort.  Kept here: the
 // fusion (a partition never leaves shared memory between sort and match).
 // Changed: one CTA per physical partition (a run of whole logical buckets,
-// ~2048 records), a counting-sort pass on the key bits below the partition
-// prefix followed by per-digit insertion sorts (about one record per digit),
-// pairs listed in shared memory so all lanes hash back to back, and the
-// partition's Table-2 base found by a decoupled look-back over the
-// partitions before it (partition order comes from a ticket counter, so
-// every partition a CTA waits on is already running; every wait is bounded
-// and a timeout poisons the chain instead of hanging).
+// ~2048 records; five CTAs per SM), a counting-sort pass on the key bits
+// below the partition prefix followed by per-digit insertion sorts (about
+// one record per digit), and the partition's Table-2 base found by a
+// decoupled look-back over the partitions before it (partition order comes
+// from a ticket counter, so every partition a CTA waits on is already
+// running; every wait is bounded and a timeout poisons the chain instead of
+// hanging).  With the cross-bucket match (HALO instances) the next
+// partition's halo is sorted in behind the partition's records.
 //
 // MODE kSortCount: the sort alone (Table 1 + per-partition pair counts),
 // used by the split vx_table1 / vx_match path.
