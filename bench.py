@@ -136,10 +136,17 @@ def aggregate(nonces_per_rank: int, steps: int, ms_total_local: float, world: in
 
 
 def source_digest(files) -> str:
+    """Digest of the kernels' code: C/C++ comments and blank lines are dropped,
+    so a comment edit does not void counters taken on the same code."""
+    import re
     h = hashlib.sha256()
     for f in files:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        lines = [ln.rstrip() for ln in text.splitlines() if ln.strip()]
+        h.update("\n".join(lines).encode())
     return h.hexdigest()[:16]
 
 
@@ -155,19 +162,24 @@ KERNEL_SOURCES = {
 }
 
 
-def ncu_traffic(kernel: str, K: int):
-    """DRAM bytes per launch of `kernel` at this workload from the committed
-    ncu summary, or None if absent or taken on a different kernel source."""
+def ncu_entry(kernel: str, K: int):
+    """The committed ncu figures of `kernel` at this workload, or None if absent
+    or taken on a different kernel source."""
     path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(path) as f:
-            t = json.load(f)
-        e = t[kernel]
+            e = json.load(f)[kernel]
         if e.get("source_digest") != source_digest(KERNEL_SOURCES[kernel]) or int(e["K"]) != K:
             return None
-        return float(e["bytes_per_launch"])
+        return e
     except Exception:
         return None
+
+
+def ncu_traffic(kernel: str, K: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary."""
+    e = ncu_entry(kernel, K)
+    return float(e["bytes_per_launch"]) if e else None
 
 
 def cpu_baseline(K_sample: int = 24):
@@ -368,6 +380,11 @@ def main():
                               % (pk_peak["sm_max_mhz"], pk_peak["source"]),
                 "work_per_launch": algo_ops[dom],
                 "traffic": ncu_traffic(dom, K)}
+        ent = ncu_entry(dom, K)
+        if ent and "alu_pipe_pct" in ent:
+            # the integer (ALU) pipe's own occupancy, from the committed ncu
+            # capture of the same kernel code
+            roof["alu_pipe_busy_ncu"] = ent["alu_pipe_pct"] / 100.0
     else:
         ach = pk[dom]["gbs"]
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
