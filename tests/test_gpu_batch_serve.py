@@ -101,3 +101,25 @@ def test_serve_rejects_oversized(vx):
     with pytest.raises(vx.VxError):
         vx.vx_serve_submit(srv, 20, plot_key(1))
     vx.vx_serve_destroy(srv)
+
+
+def test_batch_mixed_scope_and_placement(vx):
+    # One batch launch mixing cross-bucket and bucket-scope plots (the
+    # halo-capable kernel instances run both kinds) and both Table-2
+    # placements (a mixed launch places every plot by look-back): each plot
+    # equals its own oracle.
+    mix = [(14, 120, dict(match_scope=1)), (16, 121, {}), (18, 122, dict(match_scope=1, t2_placement=2)),
+           (12, 123, dict(t2_placement=2)), (20, 124, dict(match_scope=1)), (1, 125, dict(match_scope=1))]
+    plots = [vx.Plot(K, plot_key(s), vx.make_opts(**kw)) for K, s, kw in mix]
+    for rep in range(2):
+        vx.vx_plot_batch([p.handle for p in plots])
+        for (K, s, kw), p in zip(mix, plots):
+            p.sync()
+            key = plot_key(s)
+            t1 = orc.table1(K, key)
+            D = orc.default_distance(K)
+            r2 = orc.match_global(key, t1, D) if kw.get("match_scope") else orc.match(key, t1, D)
+            assert np.array_equal(p.t1.cpu().numpy(), t1), (rep, K)
+            assert np.array_equal(p.t2.cpu().numpy(), r2), (rep, K)
+    for p in plots:
+        p.close()
