@@ -267,6 +267,8 @@ def main():
                     help="0 pairs inside a logical bucket, 1 cross-bucket")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: requests per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--autotune", action="store_true",
+                    help="batch / large: every K plotted with the autotuner's plan (cached on disk)")
     ap.add_argument("--serve-streams", type=int, default=0, help="serve: concurrent waves (0 = library default)")
     ap.add_argument("--serve-max-wave", type=int, default=0, help="serve: plots per wave (0 = library default)")
     ap.add_argument("--serve-max-inflight", type=int, default=0,
@@ -523,13 +525,18 @@ def _timed(fn, stream):
     return a.elapsed_time(b)
 
 
-def run_batch_compare(vx, mix, steps, warmup, name, label):
+def run_batch_compare(vx, mix, steps, warmup, name, label, tune=False):
     """The same plots plotted one vx_plot_run after the other (plain) and as
     one vx_plot_batch (grouped launches in a recorded CUDA graph); every
-    plot's tables must be identical both ways."""
+    plot's tables must be identical both ways.  With tune, every K gets the
+    autotuner's plan (both legs use the same plans)."""
     import torch
     stream = torch.cuda.current_stream()
-    plots = [vx.Plot(K, key) for K, key in mix]
+    tuned = {}
+    if tune:
+        for K in sorted({K for K, _ in mix}):
+            tuned[K] = vx.autotune(K)
+    plots = [vx.Plot(K, key, tuned.get(K)) for K, key in mix]
     handles = [p.handle for p in plots]
     nonces = sum(1 << K for K, _ in mix)
 
@@ -574,6 +581,8 @@ def run_batch_compare(vx, mix, steps, warmup, name, label):
             "batched": {"value": nonces / (ms_batch / 1e3), "ms_per_step": ms_batch,
                         "how": "vx_plot_batch: grouped launches recorded into a CUDA graph"},
             "batched_over_plain": ms_plain / ms_batch, "equal_output": bool(equal),
+            "autotuned": {str(K): {"partition_log2": o.partition_log2, "scatter_mode": o.scatter_mode}
+                          for K, o in tuned.items()} or None,
             "steps": steps, "warmup": warmup, "data": "synthetic"}
 
 
@@ -814,11 +823,12 @@ def run_mode(args):
     if args.mode == "batch":
         mix = batch_mix(64, 20, 26, 2026, 1000)
         out = run_batch_compare(vx, mix, args.steps, args.warmup,
-                                "aggregate nonces/s, 64 plots, K uniform in 20..26", "batch")
+                                "aggregate nonces/s, 64 plots, K uniform in 20..26", "batch", args.autotune)
     elif args.mode == "large":
         mix = [(29, plot_key(3000 + i)) for i in range(4)] + [(27, plot_key(4000 + i)) for i in range(8)]
         out = run_batch_compare(vx, mix, args.steps, args.warmup,
-                                "aggregate nonces/s, 4 x K=29 + 8 x K=27 sharing HBM", "large")
+                                "aggregate nonces/s, 4 x K=29 + 8 x K=27 sharing HBM", "large",
+                                args.autotune)
     elif args.mode == "write":
         out = run_write(vx, args)
     elif args.mode == "sort2":

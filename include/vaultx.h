@@ -213,6 +213,19 @@ int vx_sync(vx_plot *plot);
 int vx_table_info(const vx_plot *plot, int which, const void **dptr, uint64_t *nrec,
                   uint32_t *rec_bytes);
 
+/* Autotuner: times every distinct plan for K that the candidate options give
+ * (partition size 2^9 .. 2^13 records, i.e. the physical partition count and
+ * the sort tile, and the staged or direct bucketing strategy; the hash
+ * kernels' threads x nonces shape is compiled in and not a candidate) on
+ * this device.  Each candidate runs one warm-up and three timed plots with a
+ * fixed synthetic key in library-owned memory on stream (CUDA events).
+ * *best gets base (defaults if null) with the fastest candidate's
+ * partition_log2 and scatter_mode, *best_ms its mean plot time.
+ * Synchronous; a candidate that cannot be planned or allocated is skipped
+ * (VX_ENOMEM if none ran).  The Python binding keeps an on-disk cache of the
+ * result keyed by device and K. */
+int vx_autotune(int K, const vx_opts *base, vx_opts *best, double *best_ms, void *stream);
+
 /* Writes the 2^24 + 1 logical-bucket offsets of Table 1 (u64, offsets[b] =
  * records in buckets < b) to d_out (device, 8-byte aligned).  Asynchronous. */
 int vx_table1_offsets(vx_plot *plot, void *d_out, void *stream);

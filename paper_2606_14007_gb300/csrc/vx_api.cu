@@ -764,6 +764,77 @@ int vx_sort_table2(vx_plot *p, void *d_work, uint64_t work_bytes, void *stream)
     return record_result(p, s);  // vx_sync now waits for the sort and reads its status
 }
 
+int vx_autotune(int K, const vx_opts *base, vx_opts *best, double *best_ms, void *stream)
+{
+    if (!best || K < 1 || K > 32) return VX_EINVAL;
+    vx_opts b0;
+    vx_opts_default(&b0);
+    if (base) {
+        if (base->size != 0 && base->size < sizeof(vx_opts)) return VX_EINVAL;
+        memcpy(&b0, base, sizeof(b0));
+        b0.size = sizeof(vx_opts);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    uint8_t key[32];
+    for (int i = 0; i < 32; ++i) key[i] = (uint8_t)(0xA5 ^ (i * 7));
+    struct Seen { int p, p1, p2, mode; uint32_t cap2; int dbits; };
+    std::vector<Seen> seen;
+    double best_t = 0;
+    bool found = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return VX_ECUDA;
+    }
+    for (int part = 9; part <= 13; ++part) {
+        for (uint32_t mode : {(uint32_t)vx::kScatterStaged, (uint32_t)vx::kScatterDirect}) {
+            vx_opts o = b0;
+            o.partition_log2 = part;
+            o.scatter_mode = mode;
+            vx::Plan pl;
+            const char *why = nullptr;
+            if (make_plan(K, &o, &pl, &why) != VX_OK) continue;
+            const Seen me{pl.p, pl.p1, pl.p2, pl.mode, pl.cap2, pl.dbits};
+            bool dup = false;
+            for (const Seen &x : seen)
+                dup = dup || (x.p == me.p && x.p1 == me.p1 && x.p2 == me.p2 && x.mode == me.mode &&
+                              x.cap2 == me.cap2 && x.dbits == me.dbits);
+            if (dup) continue;  // the planner clamped it to a plan already timed
+            seen.push_back(me);
+            vx_plot *p = nullptr;
+            if (vx_plot_create(K, key, &o, &p) != VX_OK) continue;
+            bool ok = vx_plot_alloc(p) == VX_OK && vx_plot_run(p, stream) == VX_OK &&
+                      vx_sync(p) == VX_OK;
+            float ms = 0;
+            if (ok) {
+                ok = cudaEventRecord(e0, s) == cudaSuccess;
+                for (int r = 0; ok && r < 3; ++r) ok = vx_plot_run(p, stream) == VX_OK;
+                ok = ok && cudaEventRecord(e1, s) == cudaSuccess && vx_sync(p) == VX_OK &&
+                     cudaEventSynchronize(e1) == cudaSuccess &&
+                     cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+            }
+            vx_plot_destroy(p);
+            if (!ok) {
+                cudaGetLastError();  // a failed candidate (e.g. out of memory) is skipped
+                continue;
+            }
+            const double t = ms / 3.0;
+            if (!found || t < best_t) {
+                found = true;
+                best_t = t;
+                *best = o;
+                // report the partition size the planner actually used
+                if (pl.p > 0) best->partition_log2 = K - pl.p;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!found) return VX_ENOMEM;
+    if (best_ms) *best_ms = best_t;
+    return VX_OK;
+}
+
 int vx_table_info(const vx_plot *p, int which, const void **dptr, uint64_t *nrec,
                   uint32_t *rec_bytes)
 {

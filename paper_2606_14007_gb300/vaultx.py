@@ -101,6 +101,7 @@ def lib():
             "vx_table_copy": (c_int, [vp, c_int, u64, vp, u64, vp]),
             "vx_plot_write": (c_int, [vp, ctypes.c_char_p, P(ctypes.c_double), P(ctypes.c_double)]),
             "vx_sort_table2_work_bytes": (c_int, [vp, P(u64)]),
+            "vx_autotune": (c_int, [c_int, P(vx_opts), P(vx_opts), P(ctypes.c_double), vp]),
             "vx_sort_table2": (c_int, [vp, vp, u64, vp]),
             "vx_plot_batch": (c_int, [P(vp), c_int, vp]),
             "vx_plot_destroy": (None, [vp]),
@@ -227,6 +228,58 @@ def vx_table1_offsets(plot, d_out: int, stream=None):
 def vx_table_copy(plot, which: int, host_dst: int, nbytes: int, stream=None, offset: int = 0):
     return _check(lib().vx_table_copy(plot, which, offset, host_dst, nbytes, _stream(stream)),
                   "vx_table_copy", plot)
+
+
+def vx_autotune(K: int, opts: vx_opts | None = None, stream=None) -> tuple[vx_opts, float]:
+    """The fastest plan for K on this device (library timing, no cache)."""
+    best, ms = vx_opts(), ctypes.c_double()
+    _check(lib().vx_autotune(K, ctypes.byref(opts) if opts else None, ctypes.byref(best),
+                             ctypes.byref(ms), _stream(stream)), "vx_autotune")
+    return best, ms.value
+
+
+_TUNED = ("partition_log2", "scatter_mode")
+
+
+def autotune(K: int, opts: vx_opts | None = None, cache_path: str | None = None,
+             stream=None) -> vx_opts:
+    """vx_autotune with an on-disk cache keyed by (device, K, base options):
+    the first call times the candidates, later calls (any process) reuse the
+    choice.  Cache file: cache_path, else $VX_TUNE_CACHE, else
+    ~/.cache/vaultx/tune.json."""
+    import json
+    import os
+    import torch
+    path = cache_path or os.environ.get("VX_TUNE_CACHE") or os.path.join(
+        os.path.expanduser("~"), ".cache", "vaultx", "tune.json")
+    base = opts if opts is not None else vx_opts_default()
+    prop = torch.cuda.get_device_properties(torch.cuda.current_device())
+    fields = {n: getattr(base, n) for n, _ in vx_opts._fields_
+              if n not in ("size", "reserved", "partition_log2", "scatter_mode")}
+    key = json.dumps([prop.name, prop.multi_processor_count, K, fields], sort_keys=True)
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    out = vx_opts()
+    ctypes.memmove(ctypes.byref(out), ctypes.byref(base), ctypes.sizeof(vx_opts))
+    if key in cache:
+        for n in _TUNED:
+            setattr(out, n, int(cache[key][n]))
+        return out
+    best, ms = vx_autotune(K, base, stream)
+    entry = {n: int(getattr(best, n)) for n in _TUNED}
+    entry["ms"] = ms
+    cache[key] = entry
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = path + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, path)
+    for n in _TUNED:
+        setattr(out, n, entry[n])
+    return out
 
 
 def vx_sort_table2_work_bytes(plot) -> int:
