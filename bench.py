@@ -182,24 +182,30 @@ def ncu_traffic(kernel: str, K: int):
     return float(e["bytes_per_launch"]) if e else None
 
 
-def cpu_baseline(K_sample: int = 24):
-    """The CPU oracle, as it stands, on one plot of 2^K_sample nonces: hash on
-    all host cores, sort and match on one core."""
+def cpu_baseline(K_sample: int = 24, K_single: int = 20):
+    """The CPU oracle, as it stands: one plot of 2^K_sample nonces with the
+    hash on all host cores and sort and match on one core, and one plot of
+    2^K_single nonces entirely on one core."""
     from oracle import oracle as orc
     from paper_2606_14007_gb300.inputs import plot_key
     orc.build()
-    key = plot_key(1000 + K_sample)
+
+    def one(K, threads):
+        key = plot_key(1000 + K)
+        t0 = time.perf_counter()
+        recs = orc.hash_range(key, 0, 1 << K, threads=threads)
+        t1 = orc.sort_table1(recs)
+        t2 = orc.match(key, t1, orc.default_distance(K))
+        return time.perf_counter() - t0, t2.shape[0]
+
     threads = os.cpu_count() or 1
-    t0 = time.perf_counter()
-    recs = orc.hash_range(key, 0, 1 << K_sample, threads=threads)
-    t1 = orc.sort_table1(recs)
-    n2 = orc.match_count(key, t1, orc.default_distance(K_sample))
-    t2 = orc.match(key, t1, orc.default_distance(K_sample))
-    dt = time.perf_counter() - t0
-    assert t2.shape[0] == n2
+    dt, _ = one(K_sample, threads)
+    dt1, _ = one(K_single, 1)
     return {"value": (1 << K_sample) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "one K=%d plot (2^%d nonces): keyed BLAKE3 on %d threads, qsort and match "
-                      "(incl. pair hashing) on 1 thread; %.1f s" % (K_sample, K_sample, threads, dt)}
+                      "(incl. pair hashing) on 1 thread; %.1f s" % (K_sample, K_sample, threads, dt),
+            "single_thread": {"value": (1 << K_single) / dt1, "unit": UNIT, "cores": 1,
+                              "sample": "one K=%d plot entirely on 1 thread; %.1f s" % (K_single, dt1)}}
 
 
 def run_reference(args):
