@@ -5,10 +5,11 @@ independently of the kernels, plus sampled recomputation by the oracle:
 Table 1: strictly increasing in (key64, nonce); every nonce exactly once;
 sampled records' hash bytes equal the oracle's keyed hash.
 Table 2: every entry (a, b) has pos(a) < pos(b) in Table 1, the same logical
-bucket and key64_b - key64_a < D; entries strictly increasing in
-(pos(a), pos(b)); their number equals an independent count of qualifying
+bucket (bucket scope) and key64_b - key64_a < D; entries strictly increasing
+in (pos(a), pos(b)); their number equals an independent count of qualifying
 pairs; sampled hash2 equal the oracle's; the count is within the closed-form
-expectation 2^24 (lambda - 1/2).
+expectation 2^24 (lambda - 1/2), or C(N,2) 2D / 2^64 for the cross-bucket
+match.
 """
 import math
 
@@ -40,11 +41,12 @@ def fields(t1_rows):
     return nonce, hi, lo
 
 
-def check_plot(vx, K, seed):
+def check_plot(vx, K, seed, scope=0):
+    # scope 1: the cross-bucket match (no same-bucket condition; E|T2| ~ N)
     key = plot_key(seed)
     N = 1 << K
     D = 1 << (64 - K)
-    p = vx.Plot(K, key)
+    p = vx.Plot(K, key, vx.make_opts(match_scope=scope) if scope else None)
     p.run()
     n2 = p.sync()
     t1 = p.t1
@@ -78,7 +80,9 @@ def check_plot(vx, K, seed):
             j = idx + k
             ok = j < bucket.shape[0]
             jj = torch.where(ok, j, torch.zeros_like(j))
-            m = alive & ok & (bucket[jj] == bucket[:n_own]) & ((k40[jj] - k40[:n_own]) < D)
+            same = (bucket[jj] == bucket[:n_own]) if not scope else torch.ones_like(alive)
+            gap = (k40[jj] - k40[:n_own]) + ((bucket[jj] - bucket[:n_own]) << 40)
+            m = alive & ok & same & (gap < D)
             independent += int(m.sum())
             alive = m
             k += 1
@@ -86,7 +90,7 @@ def check_plot(vx, K, seed):
     assert bool((counts == 1).all()), "a nonce is missing or repeated in Table 1"
     assert n2 == independent, (n2, independent)
     lam = N / 2 ** 24
-    E = 2 ** 24 * (lam - 0.5)
+    E = 2 ** 24 * (lam - 0.5) if not scope else N * (N - 1) / 2 * (2 * D / 2 ** 64)
     assert abs(n2 - E) < 8 * math.sqrt(8 * N), (n2, E)
     # Table 2 entries
     t2 = p.t2
@@ -101,10 +105,12 @@ def check_plot(vx, K, seed):
         assert bool((j > i).all())
         _, hi_i, lo_i = fields(t1[i])
         _, hi_j, lo_j = fields(t1[j])
-        assert bool(((hi_i >> 8) == (hi_j >> 8)).all()), "pair crosses a bucket"
+        if not scope:
+            assert bool(((hi_i >> 8) == (hi_j >> 8)).all()), "pair crosses a bucket"
         k40i = ((hi_i & 0xFF) << 32) | lo_i
         k40j = ((hi_j & 0xFF) << 32) | lo_j
-        assert bool(((k40j - k40i) < D).all()), "pair beyond the match distance"
+        gap = (k40j - k40i) + (((hi_j >> 8) - (hi_i >> 8)) << 40)
+        assert bool((gap < D).all()), "pair beyond the match distance"
         if last is not None:
             i = torch.cat([last[0], i]); j = torch.cat([last[1], j])
         order = (i[1:] > i[:-1]) | ((i[1:] == i[:-1]) & (j[1:] > j[:-1]))
@@ -135,6 +141,10 @@ def test_plot_k27_properties(vx):
 
 def test_plot_k31_properties(vx):
     check_plot(vx, 31, 31)
+
+
+def test_plot_k27_cross_bucket_properties(vx):
+    check_plot(vx, 27, 127, scope=1)
 
 
 def test_plot_k32_properties(vx):
