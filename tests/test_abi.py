@@ -160,3 +160,34 @@ def test_cross_bucket_scope_plans_a_halo(vx):
     assert vx.vx_plot_kernel_mask(h) == ["key_setup", "hash_staged", "scatter2", "scan_counts",
                                          "sortmatch", "pairhash"]
     vx.vx_plot_destroy(h)
+
+
+def test_planner_sweep_plans_or_rejects_cleanly(vx):
+    # Every K and a grid of option combinations: the planner either returns
+    # footprints that hold the tables (12 B per nonce; 16 B per expected
+    # pair, within the 24-sigma margin) or refuses with VX_EINVAL -- never
+    # another code, never a crash.
+    import itertools
+    planned = rejected = 0
+    for K in range(1, 33):
+        N = 1 << K
+        for s, mode, scope, place, pc in itertools.product(
+                (0, 6, 9, 11, 13), (0, 1, 2), (0, 1), (0, 1, 2), (0, 2, 8)):
+            o = vx.make_opts(partition_log2=s, scatter_mode=mode, match_scope=scope,
+                             t2_placement=place, pipeline_chunks=pc)
+            try:
+                t1, t2, sc = vx.vx_plot_required_bytes(K, o)
+            except vx.VxError as e:
+                assert e.code == vx.VX_EINVAL, (K, s, mode, scope, place, pc, e.code)
+                rejected += 1
+                continue
+            planned += 1
+            assert t1 >= 12 * N and t1 % 256 == 0 and t2 % 256 == 0 and sc % 256 == 0
+            if scope:
+                E = N * (N - 1) / 2 * (2 * 2.0 ** (64 - K) / 2 ** 64)
+            else:
+                lam = N / 2 ** 24
+                u = min(1.0, 2.0 ** (64 - K) / 2 ** 40)
+                E = 2 ** 24 * lam * lam / 2 * (2 * u - u * u)
+            assert t2 >= 16 * E, (K, s, scope, t2, E)
+    assert planned > 5000 and rejected > 0
