@@ -15,17 +15,20 @@ namespace vx {
 // per (CTA, bin) claims a run of the final partition slot; records are
 // restaged in bin order in place (through registers) and written out so
 // that consecutive threads store consecutive addresses of each run.
+// FB: the most second-level bits the instance handles (10; 11 for the
+// 2^21 partitions of K = 32).
+template <int FB>
 struct Scatter2Smem {
     uint64_t keys[kScatterTile];
     uint32_t nonces[kScatterTile];
-    uint32_t hist[1 << kMaxFineBits];
-    uint32_t loff[1 << kMaxFineBits];
-    uint32_t gbase[1 << kMaxFineBits];
+    uint32_t hist[1 << FB];
+    uint32_t loff[1 << FB];
+    uint32_t gbase[1 << FB];
     uint32_t ws[kScatterThreads / 32 + 1];
     uint64_t bar;
 };
 
-template <bool HALO>
+template <bool HALO, int FB>
 __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__restrict__ descs,
                                                              int nplots,
                                                              const uint32_t *__restrict__ tile_start,
@@ -34,7 +37,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__rest
     constexpr int NT = kScatterThreads;
     constexpr int PER = kScatterTile / NT;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    Scatter2Smem &sm = *reinterpret_cast<Scatter2Smem *>(smem_raw);
+    Scatter2Smem<FB> &sm = *reinterpret_cast<Scatter2Smem<FB> *>(smem_raw);
 
     const int plot = find_plot(tile_start, nplots, blockIdx.x);
     const Desc &d = descs[plot];
@@ -80,7 +83,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__rest
         rank[j] = valid ? atomicAdd(&sm.hist[bin], 1u) : 0u;
     }
     __syncthreads();
-    constexpr int PB = ((1 << kMaxFineBits) + NT - 1) / NT;  // most bins a thread owns
+    constexpr int PB = ((1 << FB) + NT - 1) / NT;  // most bins a thread owns
     const int per = (nbins + NT - 1) / NT;
     const int b0 = threadIdx.x * per;
     uint32_t claim[PB];
@@ -139,11 +142,14 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__rest
 }
 
 cudaError_t launch_scatter2(const Desc *descs, int nplots, const uint32_t *tile_start,
-                            uint32_t total_tiles, int chunk, cudaStream_t s, bool halo)
+                            uint32_t total_tiles, int chunk, cudaStream_t s, bool halo,
+                            int fine_bits)
 {
     if (total_tiles == 0) return cudaSuccess;
-    const size_t smem = sizeof(Scatter2Smem);
-    auto fn = halo ? k_scatter2<true> : k_scatter2<false>;
+    const bool wide = fine_bits > kMaxFineBits;
+    const size_t smem = wide ? sizeof(Scatter2Smem<kMaxFineBitsWide>) : sizeof(Scatter2Smem<kMaxFineBits>);
+    auto fn = wide ? (halo ? k_scatter2<true, kMaxFineBitsWide> : k_scatter2<false, kMaxFineBitsWide>)
+                   : (halo ? k_scatter2<true, kMaxFineBits> : k_scatter2<false, kMaxFineBits>);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<total_tiles, kScatterThreads, smem, s>>>(descs, nplots, tile_start, chunk);

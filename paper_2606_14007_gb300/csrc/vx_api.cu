@@ -184,6 +184,7 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
     L->G = L->C = 1;
     L->max_cap2 = 0;
     L->max_dbits = 1;
+    L->max_p2 = 0;
     int min_bits = 64;
     for (int i = 0; i < n; ++i) {
         if (!plots[i] || !plots[i]->d_t1) return VX_EINVAL;
@@ -195,6 +196,7 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
         L->C = std::max(L->C, pl.pchunks);
         L->max_cap2 = std::max(L->max_cap2, pl.cap2 + pl.hcap);
         L->max_dbits = std::max(L->max_dbits, pl.dbits);
+        L->max_p2 = std::max(L->max_p2, pl.p2);
         if (pl.mode == kScatterStaged) min_bits = std::min(min_bits, pl.p2 > 0 ? pl.p1 : pl.p);
     }
     uint64_t acc[vx::kTileArrays] = {};
@@ -361,9 +363,11 @@ cudaError_t launch_front(const LaunchSet &L, const vx::Lanes &ln, const vx::Trac
             if (ov) {
                 cudaEventRecord(ln.sync[g], A);
                 cudaStreamWaitEvent(B, ln.sync[g], 0);
-                VX_LAUNCH(KID_S2, B, vx::launch_scatter2(L.descs, L.n, L.t_s2[g], L.n_s2[g], g, B, L.halo));
+                VX_LAUNCH(KID_S2, B, vx::launch_scatter2(L.descs, L.n, L.t_s2[g], L.n_s2[g], g, B, L.halo,
+                                                         L.max_p2));
             } else {
-                VX_LAUNCH(KID_S2, A, vx::launch_scatter2(L.descs, L.n, L.t_s2[g], L.n_s2[g], g, A, L.halo));
+                VX_LAUNCH(KID_S2, A, vx::launch_scatter2(L.descs, L.n, L.t_s2[g], L.n_s2[g], g, A, L.halo,
+                                                         L.max_p2));
             }
         }
     }

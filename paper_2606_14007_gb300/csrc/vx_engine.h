@@ -41,6 +41,7 @@ struct LaunchSet {
     bool halo;         // some plot matches across buckets: kernels with the halo code
     uint32_t max_cap2;
     int max_dbits;
+    int max_p2;        // widest second scatter level of the launch
 };
 
 // Records the (kernel, start, end) events of one run; null = not traced.

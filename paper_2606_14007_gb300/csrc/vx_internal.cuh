@@ -15,6 +15,7 @@ constexpr int kBucketBits = 24;          // 2^24 logical buckets (Sec. I-A, III-
 constexpr int kMaxK = 32;                // u32 nonces
 constexpr int kMaxCoarseBits = 10;       // first scatter level, <= 1024 bins
 constexpr int kMaxFineBits = 10;         // second scatter level, <= 1024 bins
+constexpr int kMaxFineBitsWide = 11;     // ... up to 2048 (2^21 partitions, K = 32)
 constexpr int kScatterTile = 4096;       // records per CTA in the second scatter level
 constexpr int kScatterThreads = 512;
 constexpr int kSortThreads = 256;
@@ -515,7 +516,8 @@ constexpr uint64_t kT2HashTile = 256 * 8;  // Table-2 records per pair-hash CTA
 size_t sortmatch_smem_bytes(uint32_t cap, int dbits);
 uint32_t sortmatch_max_cap();  // largest slot the sort keeps in registers
 cudaError_t launch_scatter2(const Desc *descs, int nplots, const uint32_t *tile_start,
-                            uint32_t total_tiles, int chunk, cudaStream_t s, bool halo);
+                            uint32_t total_tiles, int chunk, cudaStream_t s, bool halo,
+                            int fine_bits);  // the launch's widest second level
 cudaError_t launch_scan_counts(const Desc *descs, int nplots, const uint32_t *tile_start,
                                uint32_t total_tiles, cudaStream_t s);
 // Same chunked look-back scan over the per-partition pair counts (slot

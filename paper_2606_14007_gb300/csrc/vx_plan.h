@@ -19,7 +19,7 @@ namespace vx {
 
 constexpr int kDefaultPartLog2 = 11;       // mean records per physical partition: 2048
 constexpr uint32_t kDefaultSlackSigma = 12;
-constexpr int kMaxPartBits = 20;           // two scatter levels of <= 10 bits each
+constexpr int kMaxPartBits = 21;           // scatter levels of <= 10 and <= 11 bits
 constexpr int kAggMaxBits = 6;             // warp-aggregate ranks up to 64 bins
 constexpr size_t kStageBytes = 4096;       // pinned staging: Desc + tile prefixes
 constexpr size_t kStageTilesOffset = 3584;
@@ -159,8 +159,8 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
         P.p1 = P.p <= 10 ? P.p : P.p / 2;
     }
     P.p2 = P.p - P.p1;
-    if (P.mode == kScatterStaged && (P.p1 > 10 || P.p2 > 10)) {
-        *why = "coarse_bits leaves a scatter level wider than 10 bits";
+    if (P.mode == kScatterStaged && (P.p1 > 10 || P.p2 > 11)) {
+        *why = "coarse_bits leaves a scatter level wider than 10 (first) or 11 (second) bits";
         return VX_EINVAL;
     }
     // Pipeline chunks, only where a second kernel exists to overlap (the
@@ -319,7 +319,7 @@ inline int make_sort2_plan(uint64_t n, Sort2Plan *out, size_t desc_bytes)
     while (lg < 63 && (2ull << lg) <= n) ++lg;  // floor(log2(n)), 0 for n <= 1
     S.p = lg - kDefaultPartLog2;
     if (S.p < 0) S.p = 0;
-    if (S.p > kMaxPartBits) S.p = kMaxPartBits;
+    if (S.p > 20) S.p = 20;  // its second level keeps to <= 10 bits
     S.p1 = S.p <= 10 ? S.p : S.p / 2;
     S.p2 = S.p - S.p1;
     const double avg2 = (double)n / (double)(1ull << S.p);

@@ -41,12 +41,12 @@ def fields(t1_rows):
     return nonce, hi, lo
 
 
-def check_plot(vx, K, seed, scope=0):
+def check_plot(vx, K, seed, scope=0, **kw):
     # scope 1: the cross-bucket match (no same-bucket condition; E|T2| ~ N)
     key = plot_key(seed)
     N = 1 << K
     D = 1 << (64 - K)
-    p = vx.Plot(K, key, vx.make_opts(match_scope=scope) if scope else None)
+    p = vx.Plot(K, key, vx.make_opts(match_scope=scope, **kw) if (scope or kw) else None)
     p.run()
     n2 = p.sync()
     t1 = p.t1
@@ -145,6 +145,12 @@ def test_plot_k31_properties(vx):
 
 def test_plot_k27_cross_bucket_properties(vx):
     check_plot(vx, 27, 127, scope=1)
+
+
+def test_plot_k27_with_2pow21_partitions(vx):
+    # partitions of ~64 records: 2^21 of them, an 11-bit second scatter level
+    # (the layout K=32 uses with its default ~2048-record partitions)
+    check_plot(vx, 27, 227, partition_log2=6)
 
 
 def test_plot_k32_properties(vx):
