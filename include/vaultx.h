@@ -133,17 +133,19 @@ typedef struct vx_opts {
 
 typedef struct vx_plot vx_plot;
 
-/* Fills *opts with the defaults.  Returns VX_EINVAL on NULL. */
+/* Fills *opts with the defaults.  Returns VX_EINVAL on NULL.  Library
+ * housekeeping: the paper has no counterpart. */
 int vx_opts_default(vx_opts *opts);
 
-/* Short static description of a status code. */
+/* Short static description of a status code.  The paper has no counterpart. */
 const char *vx_strerror(int status);
 
 /* Detail of the last failure on this plot (static empty string if none or
- * plot is NULL).  Valid until the next call on the plot. */
+ * plot is NULL).  Valid until the next call on the plot.  The paper has no
+ * counterpart. */
 const char *vx_last_error(const vx_plot *plot);
 
-/* Library version, (major << 16) | minor. */
+/* Library version, (major << 16) | minor.  The paper has no counterpart. */
 int vx_version(void);
 
 /* Device memory one plot needs (Sec. I-A: Table 1 stays resident in VRAM).
@@ -164,10 +166,15 @@ int vx_plot_create(int K, const uint8_t key[32], const vx_opts *opts, vx_plot **
 /* Gives the plot caller-owned device buffers of at least the sizes
  * vx_plot_required_bytes reports, each 256-byte aligned.  t2_capacity is the
  * number of 16-byte Table-2 records d_t2 can hold (0 = t2_bytes / 16 of the
- * default plan).  Replaces any earlier binding; frees library-owned memory. */
+ * default plan).  Replaces any earlier binding; frees library-owned memory.
+ * Both tables live in device memory for the whole plot (Sec. I-A); that the
+ * caller owns the buffers has no counterpart in the paper, whose plotter
+ * allocates them itself. */
 int vx_plot_bind(vx_plot *plot, void *d_t1, void *d_t2, void *d_scratch, uint64_t t2_capacity);
 
-/* Allocates library-owned device buffers (cudaMalloc) if none are bound. */
+/* Allocates library-owned device buffers (cudaMalloc) if none are bound:
+ * the paper's own arrangement, Table 1 and Table 2 in device memory
+ * (Sec. I-A, III-A). */
 int vx_plot_alloc(vx_plot *plot);
 
 /* Table 1 (Sec. III-A hash stage; sort half of the fused Sort+Match kernel):
@@ -204,12 +211,15 @@ int vx_plot_run(vx_plot *plot, void *stream);
  * stream is not waited for, and the values are this run's even when a later
  * plot on the stream reuses the same Table-1 and scratch buffers.  After
  * vx_table1, vx_match or vx_plot_batch it synchronises the whole stream and
- * reads the scratch buffer. */
+ * reads the scratch buffer.  The paper's host likewise waits for the device
+ * before Table 2 leaves it (Sec. III-A); the status codes (capacity
+ * overflow, bounded-wait timeout) have no counterpart there. */
 int vx_sync(vx_plot *plot);
 
 /* Zero-copy view of a table: device pointer, record count, record size.
  * Table-2 counts are known after vx_sync following vx_match (VX_ENOTREADY
- * before). */
+ * before).  The tables are the ones Sec. III-A keeps in device memory; the
+ * view itself has no counterpart in the paper. */
 int vx_table_info(const vx_plot *plot, int which, const void **dptr, uint64_t *nrec,
                   uint32_t *rec_bytes);
 
@@ -223,16 +233,21 @@ int vx_table_info(const vx_plot *plot, int which, const void **dptr, uint64_t *n
  * partition_log2 and scatter_mode, *best_ms its mean plot time.
  * Synchronous; a candidate that cannot be planned or allocated is skipped
  * (VX_ENOMEM if none ran).  The Python binding keeps an on-disk cache of the
- * result keyed by device and K. */
+ * result keyed by device and K.  The paper has no counterpart (its kernels
+ * use a fixed block size, Sec. III-B). */
 int vx_autotune(int K, const vx_opts *base, vx_opts *best, double *best_ms, void *stream);
 
 /* Writes the 2^24 + 1 logical-bucket offsets of Table 1 (u64, offsets[b] =
- * records in buckets < b) to d_out (device, 8-byte aligned).  Asynchronous. */
+ * records in buckets < b) to d_out (device, 8-byte aligned): the 2^24
+ * buckets Table 1 is organised into (Sec. I-A, III-B), which this library
+ * stores concatenated rather than at fixed per-bucket capacity.
+ * Asynchronous. */
 int vx_table1_offsets(vx_plot *plot, void *d_out, void *stream);
 
 /* Copies bytes [offset, offset + bytes) of a table to host memory (pinned
  * memory makes it asynchronous on stream).  The range must lie within
- * nrec * rec_bytes. */
+ * nrec * rec_bytes.  The device-to-host transfer of Sec. III-A, for any
+ * byte range of either table. */
 int vx_table_copy(vx_plot *plot, int which, uint64_t offset, void *host_dst, uint64_t bytes,
                   void *stream);
 
@@ -262,10 +277,12 @@ int vx_plot_write(vx_plot *plot, const char *path, double *seconds_d2h, double *
  * grouped launch over all plots' work (mixed K and keys), recorded once into
  * a CUDA graph per batch shape and replayed.  Each plot must be bound or
  * allocatable.  Per-plot status via vx_sync on each plot (the batch records
- * the stream on every plot).  Asynchronous. */
+ * the stream on every plot).  Asynchronous.  The paper plots one K at a time
+ * and has no counterpart. */
 int vx_plot_batch(vx_plot *const *plots, int n, void *stream);
 
-/* Frees library-owned memory and the handle.  NULL is a no-op. */
+/* Frees library-owned memory and the handle.  NULL is a no-op.  The paper
+ * has no counterpart. */
 void vx_plot_destroy(vx_plot *plot);
 
 /* ------------------------------------------------- no-allocation path */
@@ -311,30 +328,37 @@ int vx_plot_run_noalloc(int K, const uint8_t key[32], const vx_opts *opts, void 
 int vx_plot_profile(vx_plot *plot, int runs);
 
 /* Sums the traced runs: ms[k] = total milliseconds of kernel k, k <
- * *nkernels (cap must be >= 9); *nruns = runs recorded.  Waits for them. */
+ * *nkernels (cap must be >= 9); *nruns = runs recorded.  Waits for them.
+ * The per-stage times of Sec. IV-C, summed per kernel. */
 int vx_plot_profile_read(vx_plot *plot, double *ms, int cap, int *nkernels, int *nruns);
 
 /* Which kernel slots (bit k = kernel k of vx_kernel_name) one run of this
  * plot launches: split != 0 for vx_table1 + vx_match, else vx_plot_run.
- * Host only. */
+ * Host only.  The paper has no counterpart. */
 int vx_plot_kernel_mask(const vx_plot *plot, int split, uint32_t *mask);
 
 /* Name of traced kernel k ("key_setup", "hash_staged", "hash_direct",
  * "scatter2", "scan_counts", "sort", "scan_pairs", "match", "sortmatch"),
- * or "" if out of range.  Kernels a run does not use time as zero. */
+ * or "" if out of range.  Kernels a run does not use time as zero.  The
+ * paper has no counterpart. */
 const char *vx_kernel_name(int k);
 
 /* ------------------------------------------------ stand-alone stages */
 
 /* Keyed BLAKE3 of nonces nonce0 .. nonce0+count-1 into 12-byte Table-1
  * records in nonce order (no bucketing), at d_out (device, 4-byte aligned,
- * 12*count bytes).  The hash row of the path on its own.  Asynchronous. */
+ * 12*count bytes).  The hash row of the path on its own: one keyed hash of
+ * each little-endian nonce with the plot key (Sec. III-B), without the
+ * bucket insertion.  Asynchronous. */
 int vx_hash_nonces(const uint8_t key[32], uint64_t nonce0, uint64_t count, void *d_out,
                    void *stream);
 
 /* Pair hash of Table 2 on its own: for each of `count` pairs (a, b) at
  * d_pairs (device, 2 LE u32 each, 8-byte aligned) writes the 16-byte
- * Table-2 record {a, b, hash2[0..7]} to d_out (16-byte aligned).
+ * Table-2 record {a, b, hash2[0..7]} to d_out (16-byte aligned),
+ * hash2 = keyed hash of LE32(a) || LE32(b) with the plot key.  The paper
+ * produces Table-2 records from matched pairs (Sec. II-B, III-A) but does
+ * not state their content; this is the reading the whole library uses.
  * Asynchronous. */
 int vx_pair_hash(const uint8_t key[32], const void *d_pairs, uint64_t count, void *d_out,
                  void *stream);
@@ -364,7 +388,9 @@ typedef struct vx_serve_opts {
     vx_opts plot_opts;       /* options for every plot (size 0 = defaults)            */
 } vx_serve_opts;
 
-/* Creates a continuous-batching plot server on the current device. */
+/* Creates a continuous-batching plot server on the current device.  The
+ * vx_serve_* calls have no counterpart in the paper, which plots one K at a
+ * time. */
 int vx_serve_create(const vx_serve_opts *opts, vx_server **out);
 
 /* Queues a plot request; *ticket identifies it.  VX_EINVAL for a bad K or a
