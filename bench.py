@@ -257,12 +257,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--e2e-copy-streams", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "large", "serve", "write", "sort2"],
+    ap.add_argument("--mode", default="plain",
+                    choices=["plain", "batch", "large", "serve", "write", "sort2", "tiled"],
                     help="plain: the K=31 headline; batch: 64 mixed-K plots batched vs plain; "
                          "large: 4 x K=29 + 8 x K=27 batched vs plain; serve: Poisson requests "
                          "through the continuous-batching server vs one at a time; write: plots "
                          "written to flat Table-2 files, serial vs overlapped with the next plot; "
-                         "sort2: Table 2 of a K plot sorted by hash2")
+                         "sort2: Table 2 of a K plot sorted by hash2; tiled: a K plot built "
+                         "window by window into pinned host memory vs the whole plot and its copy")
     ap.add_argument("--partition-log2", type=int, default=0)
     ap.add_argument("--scatter-mode", type=int, default=0)
     ap.add_argument("--fuse-pair-hash", type=int, default=0)
@@ -282,6 +284,11 @@ def main():
     ap.add_argument("--write-K", type=int, default=28, help="write: K of every plot")
     ap.add_argument("--write-plots", type=int, default=6, help="write: plots per leg")
     ap.add_argument("--write-dir", default=None, help="write: directory for the plot files")
+    ap.add_argument("--window-bits", type=int, default=2, help="tiled: 2^c windows")
+    ap.add_argument("--tiled-no-table1", action="store_true",
+                    help="tiled: copy out Table 2 only (the plot file's table)")
+    ap.add_argument("--tiled-no-whole", action="store_true",
+                    help="tiled: skip the whole-plot comparison leg (e.g. when it does not fit)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -819,6 +826,86 @@ def run_sort2(vx, args):
     return out
 
 
+def run_tiled(vx, args):
+    """NEXT-4: a whole K plot built one window of whole logical buckets at a
+    time in two window buffers (vx_plot_tiled), its tables copied to pinned
+    host memory while the next window computes; wall-clock per plot (the
+    call is synchronous).  Beside it, the whole plot in one device buffer set
+    followed by the same copies (vx_plot_run, vx_sync, two device-to-host
+    copies).  The tiled tables are checked on the host: Table-1 nonces are a
+    permutation of 0..2^K-1 (sum and sum of squares), both counts equal the
+    whole plot's."""
+    import torch
+    from paper_2606_14007_gb300.inputs import plot_key
+    K, c = args.K, args.window_bits
+    N = 1 << K
+    key = plot_key(K)
+    opts = plot_opts(vx, args)
+    t1_out = not args.tiled_no_table1
+    dev_bytes, h1b, h2b = vx.vx_plot_tiled_bytes(K, c, opts)
+    whole_bytes = sum(vx.vx_plot_required_bytes(K, opts))
+    h1 = torch.empty(h1b if t1_out else 0, dtype=torch.uint8, pin_memory=True)
+    h2 = torch.empty(h2b, dtype=torch.uint8, pin_memory=True)
+    stream = torch.cuda.current_stream()
+
+    def tiled():
+        rc, n1, n2 = vx.vx_plot_tiled(K, key, c, h1.data_ptr() if t1_out else 0, h1b if t1_out else 0,
+                                      h2.data_ptr(), h2b, opts, stream)
+        return n1, n2
+
+    def wall(fn, steps):
+        ts = []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return sorted(ts)[len(ts) // 2] * 1e3, out
+
+    for _ in range(args.warmup):
+        tiled()
+    ms_tiled, (n1, n2) = wall(tiled, args.steps)
+    ok = n1 == N
+    if t1_out:
+        nonce = h1[: 12 * N].view(N, 12)[:, :4].contiguous().view(torch.int32).to(torch.int64)
+        nonce &= 0xFFFFFFFF
+        sq = ((N - 1) * N * (2 * N - 1) // 6) % (1 << 64)   # int64 sums wrap mod 2^64
+        sq = sq - (1 << 64) if sq >= (1 << 63) else sq
+        ok = ok and int(nonce.sum()) == N * (N - 1) // 2 and int((nonce * nonce).sum()) == sq
+        del nonce
+    out = {"mode": "tiled", "metric": "plot to host memory, nonces/s", "unit": "nonces/s",
+           "K": K, "window_bits": c, "windows": 1 << c, "value": N / (ms_tiled / 1e3),
+           "ms_per_plot": ms_tiled, "device_bytes": dev_bytes, "whole_plot_device_bytes": whole_bytes,
+           "table1_copied": t1_out, "table1_records": n1, "table2_records": n2,
+           "host_bytes_per_plot": (12 * n1 if t1_out else 0) + 16 * n2,
+           "tables_check": bool(ok), "steps": args.steps, "warmup": args.warmup,
+           "timing": "wall clock around the synchronous call, median of steps",
+           "data": "synthetic"}
+    if not args.tiled_no_whole:
+        p = vx.Plot(K, key, opts)
+        s2 = torch.cuda.Stream()
+
+        def whole():
+            p.run(stream)
+            m2 = p.sync()
+            torch.cuda.current_stream().wait_stream(stream)
+            with torch.cuda.stream(s2):
+                if t1_out:
+                    h1[: 12 * N].copy_(p._t1[: 12 * N], non_blocking=True)
+                h2[: 16 * m2].copy_(p._t2[: 16 * m2], non_blocking=True)
+            s2.synchronize()
+            return m2
+
+        for _ in range(args.warmup):
+            whole()
+        ms_whole, m2 = wall(whole, args.steps)
+        out.update({"whole_plot_ms_with_copy": ms_whole, "whole_table2_records": m2,
+                    "tables_check": bool(ok and m2 == n2)})
+        p.close()
+    return out
+
+
 def run_mode(args):
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -839,6 +926,8 @@ def run_mode(args):
         out = run_write(vx, args)
     elif args.mode == "sort2":
         out = run_sort2(vx, args)
+    elif args.mode == "tiled":
+        out = run_tiled(vx, args)
     else:
         out = run_serve(vx, args)
     if int(os.environ.get("RANK", "0")) == 0:

@@ -128,7 +128,20 @@ typedef struct vx_opts {
                                    2^11 * D / 2^(64-p) records) are collected while
                                    the partitions are filled; needs D <= 2^(64-p)
                                    and a halo of at most 256 records             */
-    uint32_t reserved[4];       /* must be zero                                      */
+    uint32_t window_bits;       /* c: 0 = (default) the whole plot.  c >= 1 makes
+                                   this plot window `window` of 2^c: only the
+                                   records whose key64 has top c bits == window
+                                   (2^(24-c) consecutive logical buckets), their
+                                   sorted Table 1 and their Table-2 pairs; the
+                                   2^c windows concatenated in window order are
+                                   the whole plot's tables.  Every nonce is still
+                                   hashed (the hash decides the window); buffers
+                                   shrink by ~2^c.  Chunked device-memory tiling
+                                   (Sec. V future work).  Needs match_scope 0 and
+                                   c <= the partition bits (K - partition_log2,
+                                   at most 21); c <= 16                            */
+    uint32_t window;            /* the window index, < 2^window_bits                 */
+    uint32_t reserved[2];       /* must be zero                                      */
 } vx_opts;
 
 typedef struct vx_plot vx_plot;
@@ -272,6 +285,40 @@ int vx_sort_table2(vx_plot *plot, void *d_work, uint64_t work_bytes, void *strea
  * data is handed to the file system (no fsync); seconds_d2h = time spent
  * waiting for device copies, seconds_total = the whole call.  Synchronous. */
 int vx_plot_write(vx_plot *plot, const char *path, double *seconds_d2h, double *seconds_total);
+
+/* ------------------------------------------- chunked device-memory tiling */
+
+/* Memory vx_plot_tiled needs for 2^K nonces in 2^window_bits windows
+ * (vx_opts.window_bits; opts' own window fields must be zero):
+ *   device_bytes:  two windows' buffers (one window computes while the other's
+ *                  tables are copied out; one window if window_bits is 0)
+ *   host_t1_bytes: 12 * 2^K, Table 1 exactly
+ *   host_t2_bytes: the windows' Table-2 capacities, 16 B per record (a bound)
+ * Any output pointer may be NULL.  Host only.  VX_EINVAL for a combination
+ * the planner rejects (see vx_opts.window_bits). */
+int vx_plot_tiled_bytes(int K, const vx_opts *opts, int window_bits, uint64_t *device_bytes,
+                        uint64_t *host_t1_bytes, uint64_t *host_t2_bytes);
+
+/* A whole plot in device memory of about 2^(1 - window_bits) of its
+ * footprint (chunked VRAM tiling, Sec. V future work): the 2^window_bits
+ * windows of vx_opts.window_bits are built one after the other in two
+ * library-owned window buffers on `stream`, and each finished window's
+ * tables are copied, on a copy stream of the library's own and overlapped
+ * with the next window's kernels, to their places in host memory: Table 1
+ * (12-byte records, 2^K of them; host_t1 may be NULL to skip it, else it
+ * holds at least 12 * 2^K bytes) and Table 2 (16-byte records) at host_t2,
+ * host_t2_bytes long.  The host tables equal the whole plot's (vx_plot_run
+ * without windows) byte for byte.  Pinned host memory (cudaHostAlloc) makes
+ * the copies asynchronous; pageable memory works but serialises them.
+ * Each window re-hashes all 2^K nonces.  *t1_count / *t2_count (may be
+ * NULL) get the record counts.  Returns VX_OK; VX_ENOMEM if Table 2 did not
+ * fit host_t2_bytes (*t2_count is then the size needed; Table 1 is
+ * complete) or a window buffer could not be allocated; a window's
+ * VX_EOVERFLOW / VX_ETIMEDOUT stops the plot.  Synchronous.  The paper
+ * names the direction; the window scheme is this library's. */
+int vx_plot_tiled(int K, const uint8_t key[32], const vx_opts *opts, int window_bits,
+                  void *host_t1, uint64_t host_t1_bytes, void *host_t2, uint64_t host_t2_bytes,
+                  uint64_t *t1_count, uint64_t *t2_count, void *stream);
 
 /* Runs vx_table1 + vx_match for n plots as one batch: every stage is one
  * grouped launch over all plots' work (mixed K and keys), recorded once into

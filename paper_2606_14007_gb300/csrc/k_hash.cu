@@ -110,7 +110,26 @@ __device__ __forceinline__ void scan_and_claim(uint32_t *hist, uint32_t *loff, u
     }
 }
 
-template <int NT, int NPT, bool AGG, bool HALO>
+// Windowed plots (WIN instances) keep the keys whose top wbits equal win and
+// bin them by the bits after those; a plot without a window (wbits 0) keeps
+// every key, so one WIN launch may also carry whole plots.
+// Window bits plus bin bits are at most the 21 partition bits, so both tests
+// read only the key's high word.
+template <bool WIN>
+__device__ __forceinline__ bool in_window(const Desc &d, uint64_t key)
+{
+    const uint32_t hi = (uint32_t)(key >> 32);
+    return !WIN || ((hi >> 1) >> (31 - d.wbits)) == d.win;  // wbits 0: always
+}
+
+template <bool WIN>
+__device__ __forceinline__ uint32_t key_bin(const Desc &d, uint64_t key, int bits)
+{
+    const uint32_t hi = (uint32_t)(key >> 32);
+    return bits ? (WIN ? hi << d.wbits : hi) >> (32 - bits) : 0u;
+}
+
+template <int NT, int NPT, bool AGG, bool HALO, bool WIN>
 __global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ descs, int nplots,
                                                      const uint32_t *__restrict__ tile_start,
                                                      int chunk)
@@ -144,35 +163,63 @@ __global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ de
 
     uint64_t key[NPT];
     uint32_t rank[NPT];
+    uint32_t count;  // records the tile keeps
+    if constexpr (!WIN) {
 #pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-        const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
-        const bool valid = nonce < N;
-        uint32_t h0, h1;
-        b3_finish<false>(pre, (uint32_t)nonce, 0u, h0, h1);
-        key[j] = key64_of(h0, h1);
-        const uint32_t bin = bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u;
-        rank[j] = bin_rank<AGG>(sm.hist, bin, valid);
-    }
-    __syncthreads();
-    scan_and_claim<NT>(sm.hist, sm.loff, sm.gbase, sm.ws, nbins, cnt, 0u);
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-        const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
-        if (nonce < N) {
+        for (int j = 0; j < NPT; ++j) {
+            const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
+            const bool valid = nonce < N;
+            uint32_t h0, h1;
+            b3_finish<false>(pre, (uint32_t)nonce, 0u, h0, h1);
+            key[j] = key64_of(h0, h1);
             const uint32_t bin = bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u;
-            const uint32_t pos = sm.loff[bin] + rank[j];
-            sm.keys[pos] = key[j];
-            sm.nonces[pos] = (uint32_t)nonce;
+            rank[j] = bin_rank<AGG>(sm.hist, bin, valid);
         }
+        __syncthreads();
+        scan_and_claim<NT>(sm.hist, sm.loff, sm.gbase, sm.ws, nbins, cnt, 0u);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
+            if (nonce < N) {
+                const uint32_t bin = bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u;
+                const uint32_t pos = sm.loff[bin] + rank[j];
+                sm.keys[pos] = key[j];
+                sm.nonces[pos] = (uint32_t)nonce;
+            }
+        }
+        __syncthreads();
+        count = (uint32_t)((N - base) < (uint64_t)T ? (N - base) : (uint64_t)T);
+    } else {
+        uint32_t keep = 0;  // bit j: record j's nonce exists and its key is in the window
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
+            uint32_t h0, h1;
+            b3_finish<false>(pre, (uint32_t)nonce, 0u, h0, h1);
+            key[j] = key64_of(h0, h1);
+            const bool valid = nonce < N && in_window<WIN>(d, key[j]);
+            keep |= (valid ? 1u : 0u) << j;
+            rank[j] = bin_rank<AGG>(sm.hist, key_bin<WIN>(d, key[j], bits), valid);
+        }
+        __syncthreads();
+        scan_and_claim<NT>(sm.hist, sm.loff, sm.gbase, sm.ws, nbins, cnt, 0u);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            if (keep >> j & 1u) {
+                const uint32_t pos = sm.loff[key_bin<WIN>(d, key[j], bits)] + rank[j];
+                sm.keys[pos] = key[j];
+                sm.nonces[pos] = (uint32_t)(base + (uint64_t)j * NT + threadIdx.x);
+            }
+        }
+        __syncthreads();
+        count = sm.loff[nbins - 1] + sm.hist[nbins - 1];  // the histogram's total
     }
-    __syncthreads();
-    const uint32_t count = (uint32_t)((N - base) < (uint64_t)T ? (N - base) : (uint64_t)T);
     bool overflow = false, hover = false;
     for (uint32_t i = threadIdx.x; i < count; i += NT) {
         const uint64_t k = sm.keys[i];
-        const uint32_t bin = bits ? (uint32_t)(k >> (64 - bits)) : 0u;
+        const uint32_t bin = WIN ? key_bin<WIN>(d, k, bits) : (bits ? (uint32_t)(k >> (64 - bits)) : 0u);
         const uint32_t g = sm.gbase[bin] + (i - sm.loff[bin]);
         if (g < cap) {
             const uint64_t at = (uint64_t)bin * cap + g;
@@ -187,12 +234,12 @@ __global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ de
     if (hover) atomicOr(d.status, kStHaloOverflow);
 }
 
-template <int NT, int NPT, bool AGG, bool HALO>
+template <int NT, int NPT, bool AGG, bool HALO, bool WIN>
 static cudaError_t launch_hs(const Desc *descs, int nplots, const uint32_t *tile_start,
                              uint32_t total_tiles, int chunk, cudaStream_t s)
 {
     const size_t smem = sizeof(HashSmem<NT, NPT>);
-    auto fn = k_hash_scatter<NT, NPT, AGG, HALO>;
+    auto fn = k_hash_scatter<NT, NPT, AGG, HALO, WIN>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<total_tiles, NT, smem, s>>>(descs, nplots, tile_start, chunk);
@@ -201,17 +248,26 @@ static cudaError_t launch_hs(const Desc *descs, int nplots, const uint32_t *tile
 
 // AGG (warp-aggregated ranks) pays off when a warp's 32 records fall into
 // few bins; the host picks it from the smallest bin count in the launch.
-// HALO instances carry the cross-bucket halo code; plain launches do not.
+// HALO instances carry the cross-bucket halo code and WIN instances the
+// window filter; plain launches carry neither.
+template <bool HALO, bool WIN>
+static cudaError_t launch_hs_agg(const Desc *descs, int nplots, const uint32_t *tile_start,
+                                 uint32_t total_tiles, bool agg, int chunk, cudaStream_t s)
+{
+    constexpr int T = kHashThreads, P = kHashNoncesPerThread;
+    return agg ? launch_hs<T, P, true, HALO, WIN>(descs, nplots, tile_start, total_tiles, chunk, s)
+               : launch_hs<T, P, false, HALO, WIN>(descs, nplots, tile_start, total_tiles, chunk, s);
+}
+
 cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *tile_start,
                                 uint32_t total_tiles, HashCfg cfg, int chunk, cudaStream_t s)
 {
     if (total_tiles == 0) return cudaSuccess;
-    constexpr int T = kHashThreads, P = kHashNoncesPerThread;
-    if (cfg.halo)
-        return cfg.agg ? launch_hs<T, P, true, true>(descs, nplots, tile_start, total_tiles, chunk, s)
-                       : launch_hs<T, P, false, true>(descs, nplots, tile_start, total_tiles, chunk, s);
-    return cfg.agg ? launch_hs<T, P, true, false>(descs, nplots, tile_start, total_tiles, chunk, s)
-                   : launch_hs<T, P, false, false>(descs, nplots, tile_start, total_tiles, chunk, s);
+    if (cfg.win)
+        return cfg.halo ? launch_hs_agg<true, true>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s)
+                        : launch_hs_agg<false, true>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s);
+    return cfg.halo ? launch_hs_agg<true, false>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s)
+                    : launch_hs_agg<false, false>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s);
 }
 
 // ------------------------------------------------- hash + direct scatter
@@ -221,7 +277,7 @@ cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *t
 // a global atomic and stores key64 and nonce there.  No shared memory and
 // no second scatter pass; the claims and scattered stores run on the LSU
 // and L2 while the ALU pipe -- the kernel's bound -- keeps hashing.
-template <int NT, int NPT, bool HALO>
+template <int NT, int NPT, bool HALO, bool WIN>
 __global__ void __launch_bounds__(NT) k_hash_direct(const Desc *__restrict__ descs, int nplots,
                                                     const uint32_t *__restrict__ tile_start,
                                                     int chunk)
@@ -247,15 +303,17 @@ __global__ void __launch_bounds__(NT) k_hash_direct(const Desc *__restrict__ des
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
         const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
-        const uint32_t bin = bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u;
-        slot[j] = nonce < N ? atomicAdd(&d.cnt2[bin], 1u) : 0xffffffffu;
+        const uint32_t bin = WIN ? key_bin<WIN>(d, key[j], bits) : (bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u);
+        // A record outside the window claims no slot: its slot reads as "none".
+        slot[j] = (nonce < N && in_window<WIN>(d, key[j])) ? atomicAdd(&d.cnt2[bin], 1u) : 0xffffffffu;
     }
     bool overflow = false, hover = false;
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
         const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
         if (nonce >= N) continue;
-        const uint32_t bin = bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u;
+        if (WIN && slot[j] == 0xffffffffu) continue;
+        const uint32_t bin = WIN ? key_bin<WIN>(d, key[j], bits) : (bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u);
         if (slot[j] < cap) {
             const uint64_t at = (uint64_t)bin * cap + slot[j];
             d.b_keys[at] = key[j];
@@ -269,17 +327,24 @@ __global__ void __launch_bounds__(NT) k_hash_direct(const Desc *__restrict__ des
     if (hover) atomicOr(d.status, kStHaloOverflow);
 }
 
+template <bool HALO, bool WIN>
+static cudaError_t launch_hd(const Desc *descs, int nplots, const uint32_t *tile_start,
+                             uint32_t total_tiles, int chunk, cudaStream_t s)
+{
+    k_hash_direct<kHashThreads, kHashNoncesPerThread, HALO, WIN><<<total_tiles, kHashThreads, 0, s>>>(
+        descs, nplots, tile_start, chunk);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_hash_direct(const Desc *descs, int nplots, const uint32_t *tile_start,
-                               uint32_t total_tiles, int chunk, cudaStream_t s, bool halo)
+                               uint32_t total_tiles, int chunk, cudaStream_t s, HashCfg cfg)
 {
     if (total_tiles == 0) return cudaSuccess;
-    if (halo)
-        k_hash_direct<kHashThreads, kHashNoncesPerThread, true><<<total_tiles, kHashThreads, 0, s>>>(
-            descs, nplots, tile_start, chunk);
-    else
-        k_hash_direct<kHashThreads, kHashNoncesPerThread, false><<<total_tiles, kHashThreads, 0, s>>>(
-            descs, nplots, tile_start, chunk);
-    return cudaGetLastError();
+    if (cfg.win)
+        return cfg.halo ? launch_hd<true, true>(descs, nplots, tile_start, total_tiles, chunk, s)
+                        : launch_hd<false, true>(descs, nplots, tile_start, total_tiles, chunk, s);
+    return cfg.halo ? launch_hd<true, false>(descs, nplots, tile_start, total_tiles, chunk, s)
+                    : launch_hd<false, false>(descs, nplots, tile_start, total_tiles, chunk, s);
 }
 
 // ------------------------------------------------ Table-2 pair hashing

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__rest
     const uint32_t count = min((uint32_t)kScatterTile, filled - start);
     const int p2 = d.p2;
     const int nbins = 1 << p2;
-    const int shift = 64 - d.p;                        // fine index = key >> shift
+    const int shift = 64 - d.pk;                       // fine index = key >> shift
     const uint32_t bin_mask = (uint32_t)nbins - 1u;
     // Copy a multiple of 4 records: the slot (cap1 % 4 == 0) always holds them.
     const uint32_t ncopy = (count + 3u) & ~3u;
@@ -238,7 +238,9 @@ __global__ void __launch_bounds__(kScanCtaThreads) k_scan_counts(const Desc *__r
         const uint64_t all = s_base + total;
         out[n] = all;
         if (SRC == 0) {
-            if (all != d.N) atomicOr(d.status, kStCountMismatch);
+            // Every nonce exactly once; a window's share is random (the
+            // windows of one plot add up to 2^K, checked by their caller).
+            if (d.wbits == 0 && all != d.N) atomicOr(d.status, kStCountMismatch);
         } else {
             if (all > d.t2cap) atomicOr(d.status, kStT2Capacity);
         }
@@ -321,18 +323,31 @@ cudaError_t launch_scan_pairs(const Desc *descs, int nplots, cudaStream_t s)
 
 // ----------------------------------------------- logical bucket offsets
 // offsets[b] = first Table-1 record of logical bucket b, found by a binary
-// search inside the physical partition that holds bucket b.
+// search inside the physical partition that holds bucket b.  A window's
+// Table 1 holds buckets [w0, w0 + 2^(24 - wbits)) only: buckets below get
+// offset 0, buckets above the window's record count.
 __global__ void k_bucket_offsets(const Desc *__restrict__ dp, uint64_t *__restrict__ out)
 {
     const Desc &d = *dp;
     const uint32_t nb = 1u << kBucketBits;
     const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b > nb) return;
+    const uint64_t np = 1ull << d.p;
     if (b == nb) {
-        out[nb] = d.N;
+        out[nb] = d.wbits ? d.t1off[np] : d.N;
         return;
     }
-    const uint32_t f = d.p ? (b >> (kBucketBits - d.p)) : 0u;
+    const int wb = kBucketBits - (int)d.wbits;  // bucket bits inside the window
+    const uint32_t w0 = d.win << wb;
+    if (b < w0) {
+        out[b] = 0;
+        return;
+    }
+    if (b - w0 >= (1u << wb)) {
+        out[b] = d.t1off[np];
+        return;
+    }
+    const uint32_t f = d.p ? ((b - w0) >> (wb - d.p)) : 0u;
     uint64_t lo = d.t1off[f], hi = d.t1off[f + 1];
     const uint32_t *t1w = reinterpret_cast<const uint32_t *>(d.t1);
     while (lo < hi) {   // first record whose bucket >= b

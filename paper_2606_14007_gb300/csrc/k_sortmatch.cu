@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 5)
     const uint32_t *inonces = d.b_nonces + (uint64_t)f * cap;
     auto key_at = [&](uint32_t i) -> uint64_t { return SLOTS ? ikeys[i] : __ldg(ikeys + i); };
     auto nonce_at = [&](uint32_t i) -> uint32_t { return SLOTS ? inonces[i] : __ldg(inonces + i); };
-    const int shift = 64 - d.p - dbits;
+    const int shift = 64 - d.pk - dbits;
     const uint32_t dmask = ndig - 1u;
 
     // 1. digit histogram (rank of each record within its digit)

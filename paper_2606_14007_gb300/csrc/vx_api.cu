@@ -40,7 +40,7 @@ static_assert(kHashThreads == 256 && kHashNoncesPerThread == 8, "hash shape the 
 static_assert(kMatchThreads >= 256, "k_match loads a halo (<= 256 records) one per thread");
 static_assert(sizeof(Desc) + 64 <= kStageTilesOffset, "descriptor overlaps staged tiles");
 static_assert(kStageTilesOffset + kTileArrays * 2 * sizeof(uint32_t) <= kStageResultOffset &&
-                  kStageResultOffset + 16 <= kStageBytes,
+                  kStageResultOffset + 24 <= kStageBytes,
               "staged tiles overlap the result block");
 int make_plan(int K, const vx_opts *o, Plan *pl, const char **why)
 {
@@ -113,6 +113,7 @@ void free_owned(vx_plot *p)
     p->desc_dirty = true;
     p->stage = 0;
     p->t2_known = false;
+    p->t1_known = false;
 }
 
 // Descriptor of a bound plot (host copy).
@@ -137,6 +138,9 @@ void fill_desc(const vx_plot *p, Desc *d)
     d->pchunks = pl.pchunks;
     d->scope = (uint32_t)pl.scope;
     d->hcap = pl.hcap;
+    d->pk = pl.pk;
+    d->wbits = pl.wbits;
+    d->win = pl.win;
     if (pl.p2 > 0) {
         d->a_keys = reinterpret_cast<uint64_t *>(p->d_t1);
         d->a_nonces = reinterpret_cast<uint32_t *>(p->d_t1 + pl.regionA_keys);
@@ -180,7 +184,7 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
     const int W = n + 1;
     enum { A_STG = 0, A_DIR = 8, A_S2 = 16, A_PC = 24, A_T2H = 32, A_SCAN = 40, A_PART = 41 };
     static_assert(A_PART + 1 == vx::kTileArrays, "tile arrays");
-    bool fuse = true, slots = true, halo = false;
+    bool fuse = true, slots = true, halo = false, win = false;
     L->G = L->C = 1;
     L->max_cap2 = 0;
     L->max_dbits = 1;
@@ -192,6 +196,7 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
         fuse = fuse && pl.fuse_pair_hash;
         slots = slots && pl.pair_slots;
         halo = halo || pl.scope != 0;
+        win = win || pl.wbits != 0;
         L->G = std::max(L->G, pl.hchunks);
         L->C = std::max(L->C, pl.pchunks);
         L->max_cap2 = std::max(L->max_cap2, pl.cap2 + pl.hcap);
@@ -232,6 +237,7 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
     L->fuse_pair_hash = fuse;
     L->pair_slots = slots;
     L->halo = halo;
+    L->win = win;
     for (int g = 0; g < vx::kMaxChunks; ++g) {
         L->t_staged[g] = d + (A_STG + g) * W;
         L->t_direct[g] = d + (A_DIR + g) * W;
@@ -355,10 +361,10 @@ cudaError_t launch_front(const LaunchSet &L, const vx::Lanes &ln, const vx::Trac
     for (int g = 0; g < L.G; ++g) {
         if (L.n_staged[g])
             VX_LAUNCH(KID_STAGED, A, vx::launch_hash_scatter(L.descs, L.n, L.t_staged[g], L.n_staged[g],
-                                                             vx::HashCfg{L.agg, L.halo}, g, A));
+                                                             vx::HashCfg{L.agg, L.halo, L.win}, g, A));
         if (L.n_direct[g])
             VX_LAUNCH(KID_DIRECT, A, vx::launch_hash_direct(L.descs, L.n, L.t_direct[g], L.n_direct[g], g, A,
-                                                            L.halo));
+                                                            vx::HashCfg{L.agg, L.halo, L.win}));
         if (L.n_s2[g]) {
             if (ov) {
                 cudaEventRecord(ln.sync[g], A);
@@ -593,6 +599,7 @@ int vx_table1(vx_plot *p, void *stream)
     if (e != cudaSuccess) return cuda_fail(p, "Table-1 launch", e);
     p->stage = 1;
     p->t2_known = false;
+    p->t1_known = false;
     p->last = s;
     p->have_last = true;
     p->res_pending = false;
@@ -620,6 +627,7 @@ int vx_match(vx_plot *p, void *stream)
     if (e != cudaSuccess) return cuda_fail(p, "match launch", e);
     p->stage = 2;
     p->t2_known = false;
+    p->t1_known = false;
     p->last = s;
     p->have_last = true;
     p->res_pending = false;
@@ -637,6 +645,8 @@ int record_result(vx_plot *p, cudaStream_t s)
     if (!p->ev_done) VX_TRY(p, cudaEventCreateWithFlags(&p->ev_done, cudaEventDisableTiming));
     VX_TRY(p, cudaMemcpyAsync(h, p->d_scratch + p->plan.o_status, 4, cudaMemcpyDeviceToHost, s));
     VX_TRY(p, cudaMemcpyAsync(h + 8, p->d_scratch + p->plan.o_t2off + 8 * (1ull << p->plan.p), 8,
+                              cudaMemcpyDeviceToHost, s));
+    VX_TRY(p, cudaMemcpyAsync(h + 16, p->d_scratch + p->plan.o_t1off + 8 * (1ull << p->plan.p), 8,
                               cudaMemcpyDeviceToHost, s));
     VX_TRY(p, cudaEventRecord(p->ev_done, s));
     p->res_pending = true;
@@ -661,6 +671,7 @@ int vx_plot_run(vx_plot *p, void *stream)
     if (e != cudaSuccess) return cuda_fail(p, "plot launch", e);
     p->stage = 2;
     p->t2_known = false;
+    p->t1_known = false;
     p->last = s;
     p->have_last = true;
     p->res_pending = false;
@@ -675,12 +686,15 @@ int vx_sync(vx_plot *p)
         VX_TRY(p, cudaEventSynchronize(p->ev_done));
         const uint8_t *h = reinterpret_cast<const uint8_t *>(p->h_stage) + vx::kStageResultOffset;
         uint32_t st = 0;
-        uint64_t total = 0;
+        uint64_t total = 0, t1 = 0;
         memcpy(&st, h, 4);
         memcpy(&total, h + 8, 8);
+        memcpy(&t1, h + 16, 8);
         p->status = st;
         p->t2_count = total;
         p->t2_known = true;
+        p->t1_count = t1;
+        p->t1_known = true;
         const int rc = map_status(st);
         if (rc != VX_OK) set_err(p, status_text(st));
         return rc;
@@ -689,6 +703,13 @@ int vx_sync(vx_plot *p)
     uint32_t st = 0;
     VX_TRY(p, cudaMemcpy(&st, p->d_scratch + p->plan.o_status, 4, cudaMemcpyDeviceToHost));
     p->status = st;
+    if (p->stage >= 1) {
+        uint64_t t1 = 0;
+        VX_TRY(p, cudaMemcpy(&t1, p->d_scratch + p->plan.o_t1off + 8 * (1ull << p->plan.p), 8,
+                             cudaMemcpyDeviceToHost));
+        p->t1_count = t1;
+        p->t1_known = true;
+    }
     if (p->stage >= 2) {
         uint64_t total = 0;
         VX_TRY(p, cudaMemcpy(&total, p->d_scratch + p->plan.o_t2off + 8 * (1ull << p->plan.p), 8,
@@ -845,8 +866,10 @@ int vx_table_info(const vx_plot *p, int which, const void **dptr, uint64_t *nrec
     if (!p || (which != VX_TABLE1 && which != VX_TABLE2)) return VX_EINVAL;
     if (which == VX_TABLE1) {
         if (p->stage < 1) return VX_ENOTREADY;
+        // A window's record count is known once vx_sync has read it.
+        if (p->plan.wbits && !p->t1_known) return VX_ENOTREADY;
         if (dptr) *dptr = p->d_t1;
-        if (nrec) *nrec = p->plan.N;
+        if (nrec) *nrec = p->plan.wbits ? p->t1_count : p->plan.N;
         if (rec_bytes) *rec_bytes = 12;
         return VX_OK;
     }
@@ -1134,6 +1157,7 @@ void mark_issued(vx_plot *const *plots, int n, cudaStream_t s)
         vx_plot *p = plots[i];
         p->stage = 2;
         p->t2_known = false;
+        p->t1_known = false;
         p->last = s;
         p->have_last = true;
         p->res_pending = false;

@@ -39,6 +39,7 @@ struct LaunchSet {
     bool fuse_pair_hash;
     bool pair_slots;   // every plot uses the slot placement (t_t2h[0] = slot pair-hash grid)
     bool halo;         // some plot matches across buckets: kernels with the halo code
+    bool win;          // some plot is a window: hash kernels with the window filter
     uint32_t max_cap2;
     int max_dbits;
     int max_p2;        // widest second scatter level of the launch
@@ -83,6 +84,8 @@ struct vx_plot {
     int stage = 0;                 // 0 created, 1 Table 1 issued, 2 match issued
     bool t2_known = false;
     uint64_t t2_count = 0;
+    bool t1_known = false;          // a window's Table-1 count, read by vx_sync
+    uint64_t t1_count = 0;
     uint32_t status = 0;
     std::string err;
     // Second streams and fork/join events of the pipelined run.

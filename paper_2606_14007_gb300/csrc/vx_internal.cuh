@@ -58,6 +58,10 @@ struct Desc {
     int32_t pchunks;     // partition chunks (sort / pair-hash pipeline)
     uint32_t scope;      // match: 0 = inside a logical bucket, 1 = cross-bucket
     uint32_t hcap;       // halo records per partition (scope 1 with p > 0), else 0
+    int32_t pk;          // partition bits in key space (p + wbits): every key shift
+    uint32_t wbits;      // window: the plot keeps the records whose top wbits
+    uint32_t win;        //   key bits equal win (wbits 0: every record)
+    uint32_t pad0;
     uint32_t *halo_cnt;  // [2^p] halo fill counters
     uint64_t *halo_keys; // [2^p * hcap] records of partition f within D of its
     uint32_t *halo_nonces; //            lower edge (unsorted): f - 1's halo
@@ -423,7 +427,7 @@ __device__ __forceinline__ void halo_add(const Desc &d, uint64_t part, uint64_t 
                                          bool &overflow)
 {
     if (d.hcap == 0 || part == 0) return;
-    if ((key & (~0ull >> d.p)) >= d.D) return;  // offset inside the partition (p >= 1)
+    if ((key & (~0ull >> d.pk)) >= d.D) return;  // offset inside the partition (p >= 1)
     const uint32_t h = atomicAdd(&d.halo_cnt[part], 1u);
     if (h < d.hcap) {
         d.halo_keys[part * d.hcap + h] = key;
@@ -490,6 +494,7 @@ namespace vx {
 struct HashCfg {
     bool agg;     // warp-aggregated histogram (few first-level bins)
     bool halo;    // some plot of the launch matches across buckets (halo code)
+    bool win;     // some plot of the launch is a window (window filter)
 };
 cudaError_t launch_key_setup(Desc *descs, int nplots, cudaStream_t s);
 // Hash kernels and the second scatter level take one nonce chunk (of
@@ -497,7 +502,7 @@ cudaError_t launch_key_setup(Desc *descs, int nplots, cudaStream_t s);
 cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *tile_start,
                                 uint32_t total_tiles, HashCfg cfg, int chunk, cudaStream_t s);
 cudaError_t launch_hash_direct(const Desc *descs, int nplots, const uint32_t *tile_start,
-                               uint32_t total_tiles, int chunk, cudaStream_t s, bool halo);
+                               uint32_t total_tiles, int chunk, cudaStream_t s, HashCfg cfg);
 // Sort + match variants: Table-2 records at final offsets found by a
 // look-back ({a, b, 0, 0}, hashed later by launch_t2_hash; or hashed in the
 // kernel), or pairs {a, b} written into each partition's own slot.

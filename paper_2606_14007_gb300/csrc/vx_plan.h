@@ -36,6 +36,8 @@ enum { kPlaceAuto = 0, kPlaceLookback = 1, kPlaceSlots = 2 };
 
 struct Plan {
     int K, s, p, p1, p2, dbits;
+    int pk;                                // partition bits in key space: p + wbits
+    uint32_t wbits, win;                   // window: top wbits of key64 == win (wbits 0: whole plot)
     int mode;                              // kScatterStaged or kScatterDirect
     uint32_t test_flags, spin_limit;
     bool fuse_pair_hash;
@@ -121,7 +123,7 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
         return VX_EINVAL;
     }
     P.test_flags = opts.test_flags;
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 2; ++i)
         if (opts.reserved[i]) {
             *why = "reserved vx_opts fields must be zero";
             return VX_EINVAL;
@@ -144,6 +146,24 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     P.p = K - P.s;
     if (P.p < 0) P.p = 0;
     if (P.p > kMaxPartBits) P.p = kMaxPartBits;
+    // A window keeps the 2^(p - c) partitions whose top c key bits are its
+    // index; every shift into the key uses pk = p, every array 2^(p - c).
+    P.pk = P.p;
+    P.wbits = opts.window_bits;
+    P.win = opts.window;
+    if (P.wbits > 16 || (int)P.wbits > P.p) {
+        *why = "window_bits must be at most 16 and at most the partition bits K - partition_log2";
+        return VX_EINVAL;
+    }
+    if (P.win >> P.wbits) {
+        *why = "window must be below 2^window_bits";
+        return VX_EINVAL;
+    }
+    if (P.wbits && opts.match_scope != 0) {
+        *why = "window_bits needs match_scope 0 (a window holds no halo of the next one)";
+        return VX_EINVAL;
+    }
+    P.p -= (int)P.wbits;
     if (opts.scatter_mode > kScatterDirect) {
         *why = "scatter_mode must be 0 (auto), 1 (staged) or 2 (direct)";
         return VX_EINVAL;
@@ -174,8 +194,10 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     while (P.hchunks > 1 && ((1ull << K) < (uint64_t)P.hchunks)) P.hchunks >>= 1;
     P.pchunks = P.fuse_pair_hash ? 1 : want;
     while (P.pchunks > 1 && (1ull << P.p) < (uint64_t)P.pchunks) P.pchunks >>= 1;
-    const double avg2 = (double)P.N / (double)(1ull << P.p);
-    uint64_t cap2 = P.p == 0 ? round_up(P.N, 4) : slot_capacity(avg2, slack);
+    // Records of the plot (of the window: Binomial(2^K, 2^-c), Poisson-like).
+    const double wrec = std::ldexp((double)P.N, -(int)P.wbits);
+    const double avg2 = std::ldexp((double)P.N, -P.pk);
+    uint64_t cap2 = (P.pk == 0) ? round_up(P.N, 4) : slot_capacity(avg2, slack);
     if (cap2 > round_up(P.N, 4)) cap2 = round_up(P.N, 4);
     if (cap2 > 16384) {
         *why = "partition slot larger than the sort's shared-memory capacity";
@@ -183,8 +205,9 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     }
     P.cap2 = (uint32_t)cap2;
     if (P.p2 > 0) {
-        const double avg1 = (double)P.N / (double)P.hchunks / (double)(1ull << P.p1);
-        uint64_t cap1 = P.p1 == 0 ? round_up(P.N, 4) : slot_capacity(avg1, slack);
+        const double avg1 = wrec / (double)P.hchunks / (double)(1ull << P.p1);
+        // One level-1 bin of a whole plot holds every record: exact.
+        uint64_t cap1 = (P.p1 == 0 && !P.wbits) ? round_up(P.N, 4) : slot_capacity(avg1, slack);
         if (cap1 > round_up(P.N / P.hchunks, 4)) cap1 = round_up(P.N / P.hchunks, 4);
         if (cap1 > 0xFFFFFF00ull) {
             *why = "first-level slot too large";
@@ -193,7 +216,7 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
         P.cap1 = (uint32_t)cap1;
         P.chunks1 = (uint32_t)((cap1 + 4095) / 4096);
     }
-    int db = K - P.p;
+    int db = K - P.pk;
     if (db < 1) db = 1;
     if (db > 13) db = 13;
     P.dbits = db;
@@ -222,7 +245,7 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     }
     P.scope = (int)opts.match_scope;
     P.hcap = 0;
-    if (P.scope == 1 && P.p > 0) {
+    if (P.scope == 1 && P.p > 0) {  // wbits == 0 here: p == pk
         const double W = std::ldexp(1.0, 64 - P.p);
         if ((double)P.D > W) {
             *why = "match_scope 1 needs match_distance <= 2^(64-p), one partition";
@@ -239,7 +262,8 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     if (opts.t2_capacity) {
         P.t2cap = opts.t2_capacity;
     } else {
-        const double E = P.scope ? expected_pairs_global(P.N, P.D) : expected_pairs(P.N, P.D);
+        const double E = (P.scope ? expected_pairs_global(P.N, P.D) : expected_pairs(P.N, P.D)) /
+                         std::ldexp(1.0, (int)P.wbits);
         P.t2cap = round_up((uint64_t)std::ceil(E + 24.0 * std::sqrt(E) + 4096.0), 256);
     }
     // Grids (tile sizes are the kernels' compile-time tiles).
@@ -269,7 +293,10 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     // consumed by the second scatter level before any Table-1 write).  The
     // final-partition slots get their own region in the scratch buffer: the
     // fused sort + match reads them while it writes both tables.
-    const uint64_t t1_tab = 12 * P.N;
+    // A window's record count is random: its Table 1 takes the most its
+    // partition slots can hold, so no write can pass the buffer's end.
+    const uint64_t t1_rec = P.wbits ? std::min<uint64_t>(P.N, ((uint64_t)1 << P.p) * P.cap2) : P.N;
+    const uint64_t t1_tab = 12 * t1_rec;
     const uint64_t t2_tab = 16 * P.t2cap;
     P.t1_bytes = round_up((t1_tab > P.regionA_bytes ? t1_tab : P.regionA_bytes) + 256, 256);
     P.t2_bytes = round_up(t2_tab + 256, 256);

@@ -264,6 +264,9 @@ int vx_serve_create(const vx_serve_opts *o, vx_server **out)
     if (!opts.streams) opts.streams = 2;
     if (!opts.max_wave) opts.max_wave = 32;
     if (opts.streams > 16 || opts.max_wave > 4096) return VX_EINVAL;
+    // Requests are whole plots: a window option would make every one the
+    // same window of its plot.
+    if (opts.plot_opts.window_bits || opts.plot_opts.window) return VX_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return VX_ECUDA;
     if (!opts.memory_budget) {

@@ -1,0 +1,139 @@
+// vx_tiled.cu -- a whole plot built one window at a time in device memory
+// (chunked VRAM tiling, the paper's third direction of future work, Sec. V).
+//
+// A window is a run of whole logical buckets: the records whose key64 has
+// its top c bits equal to the window index.  The bucket-scope match never
+// leaves a bucket, so each window's Table 1 and Table 2 are exactly the
+// whole plot's tables restricted to its buckets, and the windows in index
+// order concatenate to the whole plot's tables (Table 1 in (key64, nonce)
+// order, Table 2 in bucket order).  Each window hashes every nonce again and
+// keeps its own share: on GB300 hashing 2^31 nonces takes ~51 ms, less than
+// moving the 26 GB of unsorted records across the host link once, so
+// recomputing beats spilling the records and reading them back.
+//
+// Two window plots alternate: while one computes on the caller's stream, the
+// other's tables are copied to host memory on a copy stream of its own.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "vx_engine.h"
+
+namespace {
+
+int window_opts(const vx_opts *opts, int window_bits, vx_opts *o)
+{
+    if (window_bits < 0 || window_bits > 16) return VX_EINVAL;
+    if (opts) {
+        if (opts->size != 0 && opts->size < sizeof(vx_opts)) return VX_EINVAL;
+        memcpy(o, opts, sizeof(vx_opts));
+        if (o->window_bits || o->window) return VX_EINVAL;  // the argument sets them
+    } else {
+        vx_opts_default(o);
+    }
+    o->size = sizeof(vx_opts);
+    o->window_bits = (uint32_t)window_bits;
+    o->window = 0;
+    return VX_OK;
+}
+
+}  // namespace
+
+extern "C" int vx_plot_tiled_bytes(int K, const vx_opts *opts, int window_bits,
+                                   uint64_t *device_bytes, uint64_t *host_t1_bytes,
+                                   uint64_t *host_t2_bytes)
+{
+    vx_opts o;
+    if (window_opts(opts, window_bits, &o) != VX_OK) return VX_EINVAL;
+    vx::Plan pl;
+    const char *why = nullptr;
+    if (vx::make_plan(K, &o, &pl, &why) != VX_OK) return VX_EINVAL;
+    const uint64_t nw = 1ull << window_bits;
+    const uint64_t one = pl.t1_bytes + pl.t2_bytes + pl.scratch_bytes;
+    if (device_bytes) *device_bytes = one * (nw > 1 ? 2 : 1);
+    if (host_t1_bytes) *host_t1_bytes = 12ull << K;
+    if (host_t2_bytes) *host_t2_bytes = 16 * pl.t2cap * nw;
+    return VX_OK;
+}
+
+extern "C" int vx_plot_tiled(int K, const uint8_t key[32], const vx_opts *opts, int window_bits,
+                             void *host_t1, uint64_t host_t1_bytes, void *host_t2,
+                             uint64_t host_t2_bytes, uint64_t *t1_count, uint64_t *t2_count,
+                             void *stream)
+{
+    if (!key || !host_t2) return VX_EINVAL;
+    vx_opts o;
+    if (window_opts(opts, window_bits, &o) != VX_OK) return VX_EINVAL;
+    vx::Plan pl;
+    const char *why = nullptr;
+    if (vx::make_plan(K, &o, &pl, &why) != VX_OK) return VX_EINVAL;
+    const uint64_t N = 1ull << K;
+    if (host_t1 && host_t1_bytes < 12 * N) return VX_EINVAL;
+    const uint32_t nw = 1u << window_bits;
+    const int nbuf = nw > 1 ? 2 : 1;
+
+    vx_plot *P[2] = {nullptr, nullptr};
+    cudaStream_t cs = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    int rc = VX_OK;
+    for (int i = 0; i < nbuf && rc == VX_OK; ++i) {
+        rc = vx_plot_create(K, key, &o, &P[i]);
+        if (rc == VX_OK) rc = vx_plot_alloc(P[i]);
+    }
+    if (rc == VX_OK && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = VX_ECUDA;
+    for (int i = 0; i < nbuf && rc == VX_OK; ++i)
+        if (cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming) != cudaSuccess) rc = VX_ECUDA;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t off1 = 0, off2 = 0;
+    bool t2_full = false;
+    // Waits for window plot X (its own completion event only, so the window
+    // queued behind it keeps the GPU busy), then queues the copies of its
+    // tables to their places in host memory on the copy stream.
+    auto drain = [&](int slot) -> int {
+        vx_plot *X = P[slot];
+        const int r = vx_sync(X);
+        if (r != VX_OK) return r;
+        const uint64_t n1 = X->t1_count, n2 = X->t2_count;
+        if (off1 + n1 > N) return VX_EOVERFLOW;  // more records than nonces: never in a valid run
+        if (host_t1 && n1 &&
+            cudaMemcpyAsync((uint8_t *)host_t1 + 12 * off1, X->d_t1, 12 * n1, cudaMemcpyDeviceToHost,
+                            cs) != cudaSuccess)
+            return VX_ECUDA;
+        if (16 * (off2 + n2) > host_t2_bytes) t2_full = true;
+        if (!t2_full && n2 &&
+            cudaMemcpyAsync((uint8_t *)host_t2 + 16 * off2, X->d_t2, 16 * n2, cudaMemcpyDeviceToHost,
+                            cs) != cudaSuccess)
+            return VX_ECUDA;
+        off1 += n1;
+        off2 += n2;
+        return cudaEventRecord(copied[slot], cs) == cudaSuccess ? VX_OK : VX_ECUDA;
+    };
+    for (uint32_t w = 0; w < nw && rc == VX_OK; ++w) {
+        const int slot = (int)(w & 1u);
+        vx_plot *X = P[slot];
+        // The buffers of window w - 2 are free once its copies are done.
+        if (w >= 2 && cudaStreamWaitEvent(s, copied[slot], 0) != cudaSuccess) {
+            rc = VX_ECUDA;
+            break;
+        }
+        X->plan.win = w;
+        X->opts.window = w;
+        X->desc_dirty = true;
+        rc = vx_plot_run(X, s);
+        if (rc == VX_OK && w >= 1) rc = drain(slot ^ 1);
+    }
+    if (rc == VX_OK) rc = drain((int)((nw - 1) & 1u));
+    if (cs && cudaStreamSynchronize(cs) != cudaSuccess && rc == VX_OK) rc = VX_ECUDA;
+    if (rc == VX_OK && off1 != N) rc = VX_EOVERFLOW;  // every nonce in exactly one window
+    if (rc == VX_OK && t2_full) rc = VX_ENOMEM;     // *t2_count says how much is needed
+    if (t1_count) *t1_count = off1;
+    if (t2_count) *t2_count = off2;
+
+    for (int i = 0; i < 2; ++i) {
+        if (copied[i]) cudaEventDestroy(copied[i]);
+        vx_plot_destroy(P[i]);
+    }
+    if (cs) cudaStreamDestroy(cs);
+    return rc;
+}

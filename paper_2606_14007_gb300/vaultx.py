@@ -51,7 +51,9 @@ class vx_opts(ctypes.Structure):
         ("pipeline_chunks", ctypes.c_uint32),
         ("t2_placement", ctypes.c_uint32),
         ("match_scope", ctypes.c_uint32),
-        ("reserved", ctypes.c_uint32 * 4),
+        ("window_bits", ctypes.c_uint32),
+        ("window", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32 * 2),
     ]
 
 
@@ -104,6 +106,9 @@ def lib():
             "vx_autotune": (c_int, [c_int, P(vx_opts), P(vx_opts), P(ctypes.c_double), vp]),
             "vx_sort_table2": (c_int, [vp, vp, u64, vp]),
             "vx_plot_batch": (c_int, [P(vp), c_int, vp]),
+            "vx_plot_tiled_bytes": (c_int, [c_int, P(vx_opts), c_int, P(u64), P(u64), P(u64)]),
+            "vx_plot_tiled": (c_int, [c_int, u8p, P(vx_opts), c_int, vp, u64, vp, u64, P(u64), P(u64),
+                                      vp]),
             "vx_plot_destroy": (None, [vp]),
             "vx_plot_run_noalloc": (c_int, [c_int, u8p, P(vx_opts), vp, vp, u64, vp, P(u64)]),
             "vx_hash_nonces": (c_int, [u8p, u64, u64, vp, vp]),
@@ -313,6 +318,44 @@ def vx_plot_destroy(plot):
         lib().vx_plot_destroy(plot)
 
 
+def vx_plot_tiled_bytes(K: int, window_bits: int, opts: vx_opts | None = None) -> tuple[int, int, int]:
+    """(device bytes, host Table-1 bytes, host Table-2 bound) of a tiled plot."""
+    a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().vx_plot_tiled_bytes(K, ctypes.byref(opts) if opts else None, window_bits,
+                                     ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "vx_plot_tiled_bytes")
+    return a.value, b.value, c.value
+
+
+def vx_plot_tiled(K: int, key: bytes, window_bits: int, host_t1: int, host_t1_bytes: int,
+                  host_t2: int, host_t2_bytes: int, opts: vx_opts | None = None, stream=None,
+                  check: bool = True):
+    """Whole plot one window at a time, tables copied to host memory at
+    host_t1 (0 = skip Table 1) and host_t2; synchronous.  Returns (status,
+    Table-1 records, Table-2 records)."""
+    n1, n2 = ctypes.c_uint64(), ctypes.c_uint64()
+    rc = lib().vx_plot_tiled(K, _key(key), ctypes.byref(opts) if opts else None, window_bits,
+                             host_t1 or None, host_t1_bytes, host_t2, host_t2_bytes,
+                             ctypes.byref(n1), ctypes.byref(n2), _stream(stream))
+    if check:
+        _check(rc, "vx_plot_tiled")
+    return rc, n1.value, n2.value
+
+
+def plot_tiled(K: int, key: bytes, window_bits: int, opts: vx_opts | None = None, table1: bool = True,
+               pin: bool = True, stream=None):
+    """vx_plot_tiled into fresh host tensors: returns (t1, t2), uint8 views
+    shaped (records, 12) and (records, 16) (t1 None unless table1)."""
+    import torch
+    _, h1, h2 = vx_plot_tiled_bytes(K, window_bits, opts)
+    t1 = torch.empty(h1 if table1 else 0, dtype=torch.uint8, pin_memory=pin)
+    t2 = torch.empty(h2, dtype=torch.uint8, pin_memory=pin)
+    _, n1, n2 = vx_plot_tiled(K, key, window_bits, t1.data_ptr() if table1 else 0, h1 if table1 else 0,
+                              t2.data_ptr(), h2, opts, stream)
+    return (t1[: T1_REC * n1].view(n1, T1_REC) if table1 else None,
+            t2[: T2_REC * n2].view(n2, T2_REC))
+
+
 def vx_plot_run_noalloc(K: int, key: bytes, d_t1: int, d_t2: int, t2_capacity: int = 0,
                         opts: vx_opts | None = None, stream=None, check: bool = True):
     """Whole plot with the library's static scratch array (no allocation);
@@ -445,6 +488,8 @@ class Plot:
         vx_sync(self.handle)
         _, n, _, _ = vx_table_info(self.handle, VX_TABLE2, check=False)
         self.n2 = n
+        _, n1, _, _ = vx_table_info(self.handle, VX_TABLE1, check=False)
+        self.n1 = n1  # a window's share of the 2^K records
         return n
 
     @property

@@ -191,3 +191,49 @@ def test_planner_sweep_plans_or_rejects_cleanly(vx):
                 E = 2 ** 24 * lam * lam / 2 * (2 * u - u * u)
             assert t2 >= 16 * E, (K, s, scope, t2, E)
     assert planned > 5000 and rejected > 0
+
+
+def test_window_plans_shrink_and_reject_cleanly(vx):
+    # A window of c bits keeps ~2^-c of the records: its buffers shrink by
+    # about that factor (Table 1 is sized for the most its partition slots
+    # can hold, so a little less), and two of them (vx_plot_tiled) fit in
+    # about 2^(1-c) of the whole plot's footprint.
+    whole = sum(vx.vx_plot_required_bytes(31))
+    E = 2 ** 24 * (2 ** 7 - 0.5)  # expected Table-2 records at K=31
+    for c in (1, 2, 3, 4, 8):
+        parts = vx.vx_plot_required_bytes(31, vx.make_opts(window_bits=c, window=(1 << c) - 1))
+        t1, t2, sc = parts
+        assert t1 >= 12 * 2 ** 31 / 2 ** c and t2 >= 16 * E / 2 ** c
+        assert sum(parts) < 1.25 * whole / 2 ** c + (64 << 20), (c, sum(parts), whole)
+        dev, h1, h2 = vx.vx_plot_tiled_bytes(31, c)
+        assert dev == 2 * sum(parts)
+        assert h1 == 12 * 2 ** 31 and h2 >= 16 * E
+    # c = 0 is the whole plot, one buffer
+    assert vx.vx_plot_tiled_bytes(31, 0)[0] == whole
+    # K=32 in two windows of ~1/4 of its footprint each
+    assert vx.vx_plot_tiled_bytes(32, 2)[0] < 0.6 * sum(vx.vx_plot_required_bytes(32))
+    bad = [dict(window_bits=21, window=0),                # more bits than the 20 partition bits of K=31
+           dict(window_bits=17, window=0, partition_log2=6),  # above the 16-bit limit
+           dict(window_bits=2, window=4),                 # window index out of range
+           dict(window_bits=0, window=1),
+           dict(window_bits=2, window=1, match_scope=1)]  # no halo across windows
+    for kw in bad:
+        with pytest.raises(vx.VxError) as ei:
+            vx.vx_plot_required_bytes(31, vx.make_opts(**kw))
+        assert ei.value.code == vx.VX_EINVAL, kw
+    vx.vx_plot_required_bytes(31, vx.make_opts(window_bits=16, window=(1 << 16) - 1))
+    for c in (-1, 17):
+        with pytest.raises(vx.VxError):
+            vx.vx_plot_tiled_bytes(31, c)
+    with pytest.raises(vx.VxError):   # opts that already name a window
+        vx.vx_plot_tiled_bytes(31, 2, vx.make_opts(window_bits=2))
+
+
+def test_window_plan_at_the_partition_limit(vx):
+    # c equal to the partition bits: each window is one partition.
+    for K, s in [(12, 6), (20, 11), (27, 11)]:
+        p = K - s
+        t1, t2, sc = vx.vx_plot_required_bytes(K, vx.make_opts(window_bits=p, window=0, partition_log2=s))
+        assert t1 >= 12 * 2 ** s
+        with pytest.raises(vx.VxError):
+            vx.vx_plot_required_bytes(K, vx.make_opts(window_bits=p + 1, window=0, partition_log2=s))

@@ -45,11 +45,26 @@ def check_plot(vx, K, seed, scope=0, **kw):
     # scope 1: the cross-bucket match (no same-bucket condition; E|T2| ~ N)
     key = plot_key(seed)
     N = 1 << K
-    D = 1 << (64 - K)
     p = vx.Plot(K, key, vx.make_opts(match_scope=scope, **kw) if (scope or kw) else None)
     p.run()
     n2 = p.sync()
     t1 = p.t1
+    check_tables(K, key, seed, t1, p.t2, n2, scope)
+    # first and last records of Table 1 and Table 2, and the bucket offsets
+    off = p.offsets()
+    assert int(off[0]) == 0 and int(off[-1]) == N
+    b_first = int(fields(t1[:1])[1][0] >> 8)
+    assert int(off[b_first]) == 0 and int(off[b_first + 1]) > 0
+    p.close()
+    torch.cuda.empty_cache()
+
+
+def check_tables(K, key, seed, t1, t2, n2, scope=0):
+    """The properties of a whole plot's tables t1 (2^K x 12) and t2 (n2 x 16),
+    uint8 tensors on the device."""
+    N = 1 << K
+    D = 1 << (64 - K)
+    assert t1.shape[0] == N and t2.shape[0] == n2
     dev = t1.device
     counts = torch.zeros(N, dtype=torch.int32, device=dev)
     pos = torch.empty(N, dtype=torch.int32, device=dev)
@@ -93,7 +108,6 @@ def check_plot(vx, K, seed, scope=0, **kw):
     E = 2 ** 24 * (lam - 0.5) if not scope else N * (N - 1) / 2 * (2 * D / 2 ** 64)
     assert abs(n2 - E) < 8 * math.sqrt(8 * N), (n2, E)
     # Table 2 entries
-    t2 = p.t2
     last = None
     for s in range(0, n2, CHUNK):
         e = min(n2, s + CHUNK)
@@ -125,14 +139,7 @@ def check_plot(vx, K, seed, scope=0, **kw):
     rows = torch.from_numpy(rng.integers(0, n2, 3000)).to(dev)
     for r in t2[rows].cpu().numpy():
         assert r[8:].tobytes() == orc.keyed_hash(key, r[:8].tobytes(), 8)
-    # first and last records of Table 1 and Table 2, and the bucket offsets
-    off = p.offsets()
-    assert int(off[0]) == 0 and int(off[-1]) == N
-    b_first = int(fields(t1[:1])[1][0] >> 8)
-    assert int(off[b_first]) == 0 and int(off[b_first + 1]) > 0
-    p.close()
     del counts, pos
-    torch.cuda.empty_cache()
 
 
 def test_plot_k27_properties(vx):
@@ -217,4 +224,19 @@ def test_plot_k32_properties(vx):
         kb = int.from_bytes(orc.keyed_hash(key, r[4:8].tobytes(), 8), "big")
         assert ka >> 40 == kb >> 40 and 0 <= kb - ka < D
     p.close()
+    torch.cuda.empty_cache()
+
+
+def test_plot_k27_tiled_properties(vx):
+    # The K=27 plot built in four windows of whole logical buckets
+    # (vx_plot_tiled: two window buffers, ~2/4 of the plot's device
+    # footprint), its tables gathered in pinned host memory, then checked on
+    # the device by the whole-plot properties.
+    K, seed = 27, 327
+    key = plot_key(seed)
+    dev_bytes, _, _ = vx.vx_plot_tiled_bytes(K, 2)
+    whole = sum(vx.vx_plot_required_bytes(K))
+    assert dev_bytes < 0.65 * whole, (dev_bytes, whole)
+    t1, t2 = vx.plot_tiled(K, key, 2)
+    check_tables(K, key, seed, t1.cuda(), t2.cuda(), t2.shape[0])
     torch.cuda.empty_cache()
