@@ -289,6 +289,9 @@ def main():
                     help="tiled: copy out Table 2 only (the plot file's table)")
     ap.add_argument("--tiled-no-whole", action="store_true",
                     help="tiled: skip the whole-plot comparison leg (e.g. when it does not fit)")
+    ap.add_argument("--tiled-file", default=None,
+                    help="tiled: write Table 2 as a plot file in this directory (vx_plot_tiled_write) "
+                         "instead of into host memory; compared with the whole plot + vx_plot_write")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -846,11 +849,13 @@ def run_tiled(vx, args):
     whole_bytes = sum(vx.vx_plot_required_bytes(K, opts))
     h1 = torch.empty(h1b if t1_out else 0, dtype=torch.uint8, pin_memory=True)
     h2 = torch.empty(h2b, dtype=torch.uint8, pin_memory=True)
+    work = torch.empty(dev_bytes, dtype=torch.uint8, device="cuda")  # window buffers, allocated once
     stream = torch.cuda.current_stream()
 
     def tiled():
         rc, n1, n2 = vx.vx_plot_tiled(K, key, c, h1.data_ptr() if t1_out else 0, h1b if t1_out else 0,
-                                      h2.data_ptr(), h2b, opts, stream)
+                                      h2.data_ptr(), h2b, opts, stream, d_work=work.data_ptr(),
+                                      work_bytes=work.numel())
         return n1, n2
 
     def wall(fn, steps):
@@ -880,8 +885,11 @@ def run_tiled(vx, args):
            "table1_copied": t1_out, "table1_records": n1, "table2_records": n2,
            "host_bytes_per_plot": (12 * n1 if t1_out else 0) + 16 * n2,
            "tables_check": bool(ok), "steps": args.steps, "warmup": args.warmup,
-           "timing": "wall clock around the synchronous call, median of steps",
+           "timing": "wall clock around the synchronous call, median of steps; window buffers "
+                     "in one device buffer allocated before timing (as the whole plot's)",
            "data": "synthetic"}
+    del work
+    torch.cuda.empty_cache()
     if not args.tiled_no_whole:
         p = vx.Plot(K, key, opts)
         s2 = torch.cuda.Stream()
@@ -906,6 +914,67 @@ def run_tiled(vx, args):
     return out
 
 
+def run_tiled_file(vx, args):
+    """NEXT-4 + NEXT-1: a K plot built window by window with Table 2 streamed
+    into a flat plot file (vx_plot_tiled_write), against the whole plot
+    followed by vx_plot_write; wall clock per plot file, median of steps.
+    The two files must be byte-identical."""
+    import filecmp
+    import torch
+    from paper_2606_14007_gb300.inputs import plot_key
+    K, c = args.K, args.window_bits
+    key = plot_key(K)
+    opts = plot_opts(vx, args)
+    os.makedirs(args.tiled_file, exist_ok=True)
+    fa = os.path.join(args.tiled_file, "tiled_k%d.plot" % K)
+    fb = os.path.join(args.tiled_file, "whole_k%d.plot" % K)
+    dev_bytes, _, _ = vx.vx_plot_tiled_bytes(K, c, opts)
+    work = torch.empty(dev_bytes, dtype=torch.uint8, device="cuda")  # window buffers, allocated once
+    stream = torch.cuda.current_stream()
+
+    def tiled():
+        _, n1, n2, sec = vx.vx_plot_tiled_write(K, key, c, fa, 0, 0, opts, stream,
+                                                d_work=work.data_ptr(), work_bytes=work.numel())
+        return n2
+
+    p = vx.Plot(K, key, opts)
+
+    def whole():
+        p.run(stream)
+        m2 = p.sync()
+        vx.vx_plot_write(p.handle, fb)
+        return m2
+
+    # the two legs alternate step by step, so that both see the same state of
+    # the host's page cache and disk
+    for _ in range(args.warmup):
+        tiled()
+        whole()
+    tt, tw, counts = [], [], {}
+    for _ in range(args.steps):
+        for name, fn, acc in (("tiled", tiled, tt), ("whole", whole, tw)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            counts[name] = fn()
+            torch.cuda.synchronize()
+            acc.append(time.perf_counter() - t0)
+    n2, m2 = counts["tiled"], counts["whole"]
+    ms_t = sorted(tt)[len(tt) // 2] * 1e3
+    ms_w = sorted(tw)[len(tw) // 2] * 1e3
+    same = n2 == m2 and filecmp.cmp(fa, fb, shallow=False)
+    size = os.path.getsize(fa)
+    p.close()
+    for f in (fa, fb):
+        os.remove(f)
+    return {"mode": "tiled-file", "metric": "plot file written, nonces/s", "unit": "nonces/s",
+            "K": K, "window_bits": c, "value": (1 << K) / (ms_t / 1e3), "ms_per_plot_file": ms_t,
+            "whole_plot_ms_per_plot_file": ms_w, "file_bytes": size, "files_identical": bool(same),
+            "steps_ms_tiled": [round(t * 1e3, 1) for t in tt], "steps_ms_whole": [round(t * 1e3, 1) for t in tw],
+            "device_bytes": dev_bytes, "whole_plot_device_bytes": sum(vx.vx_plot_required_bytes(K, opts)),
+            "steps": args.steps, "warmup": args.warmup,
+            "timing": "wall clock around each synchronous call, median of steps", "data": "synthetic"}
+
+
 def run_mode(args):
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -927,7 +996,7 @@ def run_mode(args):
     elif args.mode == "sort2":
         out = run_sort2(vx, args)
     elif args.mode == "tiled":
-        out = run_tiled(vx, args)
+        out = run_tiled_file(vx, args) if args.tiled_file else run_tiled(vx, args)
     else:
         out = run_serve(vx, args)
     if int(os.environ.get("RANK", "0")) == 0:

@@ -302,7 +302,10 @@ int vx_plot_tiled_bytes(int K, const vx_opts *opts, int window_bits, uint64_t *d
 /* A whole plot in device memory of about 2^(1 - window_bits) of its
  * footprint (chunked VRAM tiling, Sec. V future work): the 2^window_bits
  * windows of vx_opts.window_bits are built one after the other in two
- * library-owned window buffers on `stream`, and each finished window's
+ * window buffer sets on `stream` -- cut from d_work, caller-owned device
+ * memory of at least vx_plot_tiled_bytes' device_bytes (256-byte aligned,
+ * never freed by the library), or allocated for the call and freed before
+ * it returns when d_work is NULL -- and each finished window's
  * tables are copied, on a copy stream of the library's own and overlapped
  * with the next window's kernels, to their places in host memory: Table 1
  * (12-byte records, 2^K of them; host_t1 may be NULL to skip it, else it
@@ -317,8 +320,24 @@ int vx_plot_tiled_bytes(int K, const vx_opts *opts, int window_bits, uint64_t *d
  * VX_EOVERFLOW / VX_ETIMEDOUT stops the plot.  Synchronous.  The paper
  * names the direction; the window scheme is this library's. */
 int vx_plot_tiled(int K, const uint8_t key[32], const vx_opts *opts, int window_bits,
-                  void *host_t1, uint64_t host_t1_bytes, void *host_t2, uint64_t host_t2_bytes,
-                  uint64_t *t1_count, uint64_t *t2_count, void *stream);
+                  void *d_work, uint64_t work_bytes, void *host_t1, uint64_t host_t1_bytes,
+                  void *host_t2, uint64_t host_t2_bytes, uint64_t *t1_count, uint64_t *t2_count,
+                  void *stream);
+
+/* vx_plot_tiled with Table 2 written as a flat plot file at `path` (created
+ * or truncated; the bytes of vx_plot_write of the whole plot) instead of
+ * into host memory: each finished window's Table 2 is appended through the
+ * library's 256 MB pinned staging buffer in sequential 4 MB chunks
+ * (Sec. III-A, III-B) while the next window computes, so no host buffer of
+ * the table's size is needed.  d_work and host_t1 as in vx_plot_tiled (both
+ * may be NULL).
+ * *seconds (may be NULL) gets the call's wall time.  On an error the file
+ * holds the windows written so far.  Synchronous.  VX_EINVAL also when the
+ * file cannot be opened; VX_ECUDA when a write fails. */
+int vx_plot_tiled_write(int K, const uint8_t key[32], const vx_opts *opts, int window_bits,
+                        void *d_work, uint64_t work_bytes, const char *path, void *host_t1,
+                        uint64_t host_t1_bytes, uint64_t *t1_count, uint64_t *t2_count,
+                        double *seconds, void *stream);
 
 /* Runs vx_table1 + vx_match for n plots as one batch: every stage is one
  * grouped launch over all plots' work (mixed K and keys), recorded once into

@@ -1255,27 +1255,25 @@ cudaStream_t g_copy_stream = nullptr;
 cudaEvent_t g_copy_ev[2] = {nullptr, nullptr};
 }  // namespace
 
-extern "C" int vx_plot_write(vx_plot *p, const char *path, double *sec_d2h, double *sec_total)
+namespace vx {
+
+// Appends plot p's Table 2 (synced) to the open file fd through the pinned
+// staging buffer: double-buffered half-buffer copies on the library's copy
+// stream, each written as sequential 4 MB chunks.  *d2h (may be null) gets
+// the seconds spent waiting for copies.  VX_OK or VX_ECUDA (detail on p).
+int write_table2_fd(vx_plot *p, int fd, double *d2h_out)
 {
-    if (!p || !path) return VX_EINVAL;
-    int rc = vx_sync(p);
-    if (rc != VX_OK) return rc;
     const void *src = nullptr;
     uint64_t nrec = 0;
     uint32_t rb = 0;
-    if ((rc = vx_table_info(p, VX_TABLE2, &src, &nrec, &rb)) != VX_OK) return rc;
+    int rc = vx_table_info(p, VX_TABLE2, &src, &nrec, &rb);
+    if (rc != VX_OK) return rc;
     std::lock_guard<std::mutex> lk(g_stage_mu);
     if (!g_stage) {
         VX_TRY(p, cudaMallocHost((void **)&g_stage, vx::kWriteStageBytes));
         VX_TRY(p, cudaStreamCreateWithFlags(&g_copy_stream, cudaStreamNonBlocking));
         VX_TRY(p, cudaEventCreateWithFlags(&g_copy_ev[0], cudaEventDisableTiming));
         VX_TRY(p, cudaEventCreateWithFlags(&g_copy_ev[1], cudaEventDisableTiming));
-    }
-    const auto t0 = std::chrono::steady_clock::now();
-    int fd = open(path, O_WRONLY | O_CREAT | O_TRUNC, 0644);
-    if (fd < 0) {
-        set_err(p, std::string("cannot open ") + path);
-        return VX_EINVAL;
     }
     const uint64_t total = nrec * rb;
     const uint64_t half = vx::kWriteStageBytes / 2;
@@ -1317,12 +1315,35 @@ extern "C" int vx_plot_write(vx_plot *p, const char *path, double *sec_d2h, doub
             slot ^= 1;
         }
     }
-    if (close(fd) != 0) ok = false;
     cudaStreamSynchronize(g_copy_stream);
     if (!ok) {
         set_err(p, "Table-2 write failed");
         return VX_ECUDA;
     }
+    if (d2h_out) *d2h_out = d2h;
+    return VX_OK;
+}
+
+}  // namespace vx
+
+extern "C" int vx_plot_write(vx_plot *p, const char *path, double *sec_d2h, double *sec_total)
+{
+    if (!p || !path) return VX_EINVAL;
+    int rc = vx_sync(p);
+    if (rc != VX_OK) return rc;
+    const auto t0 = std::chrono::steady_clock::now();
+    int fd = open(path, O_WRONLY | O_CREAT | O_TRUNC, 0644);
+    if (fd < 0) {
+        set_err(p, std::string("cannot open ") + path);
+        return VX_EINVAL;
+    }
+    double d2h = 0;
+    rc = vx::write_table2_fd(p, fd, &d2h);
+    if (close(fd) != 0 && rc == VX_OK) {
+        set_err(p, "Table-2 write failed");
+        rc = VX_ECUDA;
+    }
+    if (rc != VX_OK) return rc;
     if (sec_d2h) *sec_d2h = d2h;
     if (sec_total) *sec_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return VX_OK;

@@ -126,5 +126,9 @@ int make_plan(int K, const vx_opts *o, Plan *pl, const char **why);
 void fill_desc_ext(const vx_plot *p, Desc *d);
 int build_tiles_ext(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, LaunchSet *L);
 int map_status_ext(uint32_t st);
+// Appends plot p's Table 2 (synced) to the open file fd through the pinned
+// staging buffer (double-buffered, sequential 4 MB writes); synchronous.
+// *d2h (may be null): seconds waiting for device copies.
+int write_table2_fd(vx_plot *p, int fd, double *d2h);
 
 }  // namespace vx

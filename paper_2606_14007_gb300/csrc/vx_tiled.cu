@@ -12,9 +12,15 @@
 // recomputing beats spilling the records and reading them back.
 //
 // Two window plots alternate: while one computes on the caller's stream, the
-// other's tables are copied to host memory on a copy stream of its own.
+// other's tables go to the host -- into the caller's memory on a copy stream
+// of the library's own, or (Table 2) appended to a flat plot file through
+// the pinned staging buffer, as vx_plot_write does for a whole plot
+// (Sec. III-A, III-B: 4 MB sequential chunks, 256 MB pinned staging).
 #include <cuda_runtime.h>
+#include <fcntl.h>
+#include <unistd.h>
 
+#include <chrono>
 #include <cstring>
 
 #include "vx_engine.h"
@@ -37,31 +43,20 @@ int window_opts(const vx_opts *opts, int window_bits, vx_opts *o)
     return VX_OK;
 }
 
-}  // namespace
+// Where each window's Table 2 goes: host memory (t2, t2_bytes long; copied
+// asynchronously) or the open file fd (written before the next window's
+// buffers are reused).
+struct Sink {
+    uint8_t *t2 = nullptr;
+    uint64_t t2_bytes = 0;
+    int fd = -1;
+};
 
-extern "C" int vx_plot_tiled_bytes(int K, const vx_opts *opts, int window_bits,
-                                   uint64_t *device_bytes, uint64_t *host_t1_bytes,
-                                   uint64_t *host_t2_bytes)
+int tiled_run(int K, const uint8_t key[32], const vx_opts *opts, int window_bits, void *d_work,
+              uint64_t work_bytes, void *host_t1, uint64_t host_t1_bytes, const Sink &sink,
+              uint64_t *t1_count, uint64_t *t2_count, void *stream)
 {
-    vx_opts o;
-    if (window_opts(opts, window_bits, &o) != VX_OK) return VX_EINVAL;
-    vx::Plan pl;
-    const char *why = nullptr;
-    if (vx::make_plan(K, &o, &pl, &why) != VX_OK) return VX_EINVAL;
-    const uint64_t nw = 1ull << window_bits;
-    const uint64_t one = pl.t1_bytes + pl.t2_bytes + pl.scratch_bytes;
-    if (device_bytes) *device_bytes = one * (nw > 1 ? 2 : 1);
-    if (host_t1_bytes) *host_t1_bytes = 12ull << K;
-    if (host_t2_bytes) *host_t2_bytes = 16 * pl.t2cap * nw;
-    return VX_OK;
-}
-
-extern "C" int vx_plot_tiled(int K, const uint8_t key[32], const vx_opts *opts, int window_bits,
-                             void *host_t1, uint64_t host_t1_bytes, void *host_t2,
-                             uint64_t host_t2_bytes, uint64_t *t1_count, uint64_t *t2_count,
-                             void *stream)
-{
-    if (!key || !host_t2) return VX_EINVAL;
+    if (!key) return VX_EINVAL;
     vx_opts o;
     if (window_opts(opts, window_bits, &o) != VX_OK) return VX_EINVAL;
     vx::Plan pl;
@@ -71,6 +66,10 @@ extern "C" int vx_plot_tiled(int K, const uint8_t key[32], const vx_opts *opts, 
     if (host_t1 && host_t1_bytes < 12 * N) return VX_EINVAL;
     const uint32_t nw = 1u << window_bits;
     const int nbuf = nw > 1 ? 2 : 1;
+    // Window buffers: caller-owned work memory cut into nbuf sets of
+    // (Table 1, Table 2, scratch), or library-owned ones for this call.
+    const uint64_t one = pl.t1_bytes + pl.t2_bytes + pl.scratch_bytes;
+    if (d_work && (work_bytes < one * nbuf || ((uintptr_t)d_work & 255u))) return VX_EINVAL;
 
     vx_plot *P[2] = {nullptr, nullptr};
     cudaStream_t cs = nullptr;
@@ -78,7 +77,13 @@ extern "C" int vx_plot_tiled(int K, const uint8_t key[32], const vx_opts *opts, 
     int rc = VX_OK;
     for (int i = 0; i < nbuf && rc == VX_OK; ++i) {
         rc = vx_plot_create(K, key, &o, &P[i]);
-        if (rc == VX_OK) rc = vx_plot_alloc(P[i]);
+        if (rc != VX_OK) break;
+        if (d_work) {
+            uint8_t *b = (uint8_t *)d_work + one * i;  // plan sizes are multiples of 256
+            rc = vx_plot_bind(P[i], b, b + pl.t1_bytes, b + pl.t1_bytes + pl.t2_bytes, 0);
+        } else {
+            rc = vx_plot_alloc(P[i]);
+        }
     }
     if (rc == VX_OK && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = VX_ECUDA;
     for (int i = 0; i < nbuf && rc == VX_OK; ++i)
@@ -88,11 +93,12 @@ extern "C" int vx_plot_tiled(int K, const uint8_t key[32], const vx_opts *opts, 
     uint64_t off1 = 0, off2 = 0;
     bool t2_full = false;
     // Waits for window plot X (its own completion event only, so the window
-    // queued behind it keeps the GPU busy), then queues the copies of its
-    // tables to their places in host memory on the copy stream.
+    // queued behind it keeps the GPU busy), then sends its tables on: Table 1
+    // (and Table 2 into host memory) as copies on the copy stream, Table 2
+    // into the file through the staging buffer.
     auto drain = [&](int slot) -> int {
         vx_plot *X = P[slot];
-        const int r = vx_sync(X);
+        int r = vx_sync(X);
         if (r != VX_OK) return r;
         const uint64_t n1 = X->t1_count, n2 = X->t2_count;
         if (off1 + n1 > N) return VX_EOVERFLOW;  // more records than nonces: never in a valid run
@@ -100,11 +106,15 @@ extern "C" int vx_plot_tiled(int K, const uint8_t key[32], const vx_opts *opts, 
             cudaMemcpyAsync((uint8_t *)host_t1 + 12 * off1, X->d_t1, 12 * n1, cudaMemcpyDeviceToHost,
                             cs) != cudaSuccess)
             return VX_ECUDA;
-        if (16 * (off2 + n2) > host_t2_bytes) t2_full = true;
-        if (!t2_full && n2 &&
-            cudaMemcpyAsync((uint8_t *)host_t2 + 16 * off2, X->d_t2, 16 * n2, cudaMemcpyDeviceToHost,
-                            cs) != cudaSuccess)
-            return VX_ECUDA;
+        if (sink.fd >= 0) {
+            if ((r = vx::write_table2_fd(X, sink.fd, nullptr)) != VX_OK) return r;
+        } else {
+            if (16 * (off2 + n2) > sink.t2_bytes) t2_full = true;
+            if (!t2_full && n2 &&
+                cudaMemcpyAsync(sink.t2 + 16 * off2, X->d_t2, 16 * n2, cudaMemcpyDeviceToHost, cs) !=
+                    cudaSuccess)
+                return VX_ECUDA;
+        }
         off1 += n1;
         off2 += n2;
         return cudaEventRecord(copied[slot], cs) == cudaSuccess ? VX_OK : VX_ECUDA;
@@ -135,5 +145,58 @@ extern "C" int vx_plot_tiled(int K, const uint8_t key[32], const vx_opts *opts, 
         vx_plot_destroy(P[i]);
     }
     if (cs) cudaStreamDestroy(cs);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int vx_plot_tiled_bytes(int K, const vx_opts *opts, int window_bits,
+                                   uint64_t *device_bytes, uint64_t *host_t1_bytes,
+                                   uint64_t *host_t2_bytes)
+{
+    vx_opts o;
+    if (window_opts(opts, window_bits, &o) != VX_OK) return VX_EINVAL;
+    vx::Plan pl;
+    const char *why = nullptr;
+    if (vx::make_plan(K, &o, &pl, &why) != VX_OK) return VX_EINVAL;
+    const uint64_t nw = 1ull << window_bits;
+    const uint64_t one = pl.t1_bytes + pl.t2_bytes + pl.scratch_bytes;
+    if (device_bytes) *device_bytes = one * (nw > 1 ? 2 : 1);
+    if (host_t1_bytes) *host_t1_bytes = 12ull << K;
+    if (host_t2_bytes) *host_t2_bytes = 16 * pl.t2cap * nw;
+    return VX_OK;
+}
+
+extern "C" int vx_plot_tiled(int K, const uint8_t key[32], const vx_opts *opts, int window_bits,
+                             void *d_work, uint64_t work_bytes, void *host_t1,
+                             uint64_t host_t1_bytes, void *host_t2, uint64_t host_t2_bytes,
+                             uint64_t *t1_count, uint64_t *t2_count, void *stream)
+{
+    if (!host_t2) return VX_EINVAL;
+    Sink sink;
+    sink.t2 = (uint8_t *)host_t2;
+    sink.t2_bytes = host_t2_bytes;
+    return tiled_run(K, key, opts, window_bits, d_work, work_bytes, host_t1, host_t1_bytes, sink,
+                     t1_count, t2_count, stream);
+}
+
+extern "C" int vx_plot_tiled_write(int K, const uint8_t key[32], const vx_opts *opts,
+                                   int window_bits, void *d_work, uint64_t work_bytes,
+                                   const char *path, void *host_t1, uint64_t host_t1_bytes,
+                                   uint64_t *t1_count, uint64_t *t2_count, double *seconds,
+                                   void *stream)
+{
+    if (!path) return VX_EINVAL;
+    vx_opts o;  // reject bad arguments before the file is created
+    if (!key || window_opts(opts, window_bits, &o) != VX_OK) return VX_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    Sink sink;
+    sink.fd = open(path, O_WRONLY | O_CREAT | O_TRUNC, 0644);
+    if (sink.fd < 0) return VX_EINVAL;
+    int rc = tiled_run(K, key, opts, window_bits, d_work, work_bytes, host_t1, host_t1_bytes, sink,
+                       t1_count, t2_count, stream);
+    if (close(sink.fd) != 0 && rc == VX_OK) rc = VX_ECUDA;
+    if (seconds)
+        *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return rc;
 }

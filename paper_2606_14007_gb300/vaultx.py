@@ -107,8 +107,10 @@ def lib():
             "vx_sort_table2": (c_int, [vp, vp, u64, vp]),
             "vx_plot_batch": (c_int, [P(vp), c_int, vp]),
             "vx_plot_tiled_bytes": (c_int, [c_int, P(vx_opts), c_int, P(u64), P(u64), P(u64)]),
-            "vx_plot_tiled": (c_int, [c_int, u8p, P(vx_opts), c_int, vp, u64, vp, u64, P(u64), P(u64),
-                                      vp]),
+            "vx_plot_tiled": (c_int, [c_int, u8p, P(vx_opts), c_int, vp, u64, vp, u64, vp, u64, P(u64),
+                                      P(u64), vp]),
+            "vx_plot_tiled_write": (c_int, [c_int, u8p, P(vx_opts), c_int, vp, u64, ctypes.c_char_p, vp,
+                                            u64, P(u64), P(u64), P(ctypes.c_double), vp]),
             "vx_plot_destroy": (None, [vp]),
             "vx_plot_run_noalloc": (c_int, [c_int, u8p, P(vx_opts), vp, vp, u64, vp, P(u64)]),
             "vx_hash_nonces": (c_int, [u8p, u64, u64, vp, vp]),
@@ -329,29 +331,51 @@ def vx_plot_tiled_bytes(K: int, window_bits: int, opts: vx_opts | None = None) -
 
 def vx_plot_tiled(K: int, key: bytes, window_bits: int, host_t1: int, host_t1_bytes: int,
                   host_t2: int, host_t2_bytes: int, opts: vx_opts | None = None, stream=None,
-                  check: bool = True):
+                  check: bool = True, d_work: int = 0, work_bytes: int = 0):
     """Whole plot one window at a time, tables copied to host memory at
-    host_t1 (0 = skip Table 1) and host_t2; synchronous.  Returns (status,
+    host_t1 (0 = skip Table 1) and host_t2; window buffers cut from d_work
+    (device, 0 = allocated for the call); synchronous.  Returns (status,
     Table-1 records, Table-2 records)."""
     n1, n2 = ctypes.c_uint64(), ctypes.c_uint64()
     rc = lib().vx_plot_tiled(K, _key(key), ctypes.byref(opts) if opts else None, window_bits,
-                             host_t1 or None, host_t1_bytes, host_t2, host_t2_bytes,
-                             ctypes.byref(n1), ctypes.byref(n2), _stream(stream))
+                             d_work or None, work_bytes, host_t1 or None, host_t1_bytes, host_t2,
+                             host_t2_bytes, ctypes.byref(n1), ctypes.byref(n2), _stream(stream))
     if check:
         _check(rc, "vx_plot_tiled")
     return rc, n1.value, n2.value
 
 
+def vx_plot_tiled_write(K: int, key: bytes, window_bits: int, path: str, host_t1: int = 0,
+                        host_t1_bytes: int = 0, opts: vx_opts | None = None, stream=None,
+                        check: bool = True, d_work: int = 0, work_bytes: int = 0):
+    """Whole plot one window at a time, Table 2 written as a flat plot file
+    at `path` (Table 1 copied to host_t1 unless 0); window buffers cut from
+    d_work (0 = allocated for the call); synchronous.  Returns (status,
+    Table-1 records, Table-2 records, seconds)."""
+    n1, n2, sec = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double()
+    rc = lib().vx_plot_tiled_write(K, _key(key), ctypes.byref(opts) if opts else None, window_bits,
+                                   d_work or None, work_bytes, path.encode(), host_t1 or None,
+                                   host_t1_bytes, ctypes.byref(n1), ctypes.byref(n2), ctypes.byref(sec),
+                                   _stream(stream))
+    if check:
+        _check(rc, "vx_plot_tiled_write")
+    return rc, n1.value, n2.value, sec.value
+
+
 def plot_tiled(K: int, key: bytes, window_bits: int, opts: vx_opts | None = None, table1: bool = True,
-               pin: bool = True, stream=None):
+               pin: bool = True, stream=None, work=None):
     """vx_plot_tiled into fresh host tensors: returns (t1, t2), uint8 views
-    shaped (records, 12) and (records, 16) (t1 None unless table1)."""
+    shaped (records, 12) and (records, 16) (t1 None unless table1).  `work`:
+    an optional uint8 device tensor of at least vx_plot_tiled_bytes' device
+    bytes for the window buffers."""
     import torch
     _, h1, h2 = vx_plot_tiled_bytes(K, window_bits, opts)
     t1 = torch.empty(h1 if table1 else 0, dtype=torch.uint8, pin_memory=pin)
     t2 = torch.empty(h2, dtype=torch.uint8, pin_memory=pin)
     _, n1, n2 = vx_plot_tiled(K, key, window_bits, t1.data_ptr() if table1 else 0, h1 if table1 else 0,
-                              t2.data_ptr(), h2, opts, stream)
+                              t2.data_ptr(), h2, opts, stream,
+                              d_work=work.data_ptr() if work is not None else 0,
+                              work_bytes=work.numel() if work is not None else 0)
     return (t1[: T1_REC * n1].view(n1, T1_REC) if table1 else None,
             t2[: T2_REC * n2].view(n2, T2_REC))
 

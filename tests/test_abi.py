@@ -237,3 +237,12 @@ def test_window_plan_at_the_partition_limit(vx):
         assert t1 >= 12 * 2 ** s
         with pytest.raises(vx.VxError):
             vx.vx_plot_required_bytes(K, vx.make_opts(window_bits=p + 1, window=0, partition_log2=s))
+
+
+def test_tiled_write_rejects_bad_arguments_before_creating_the_file(vx, tmp_path):
+    # argument errors come back before any file or device work
+    path = tmp_path / "plot.bin"
+    for K, c, o in [(31, 17, None), (31, -1, None), (14, 2, vx.make_opts(window_bits=1))]:
+        rc, _, _, _ = vx.vx_plot_tiled_write(K, bytes(32), c, str(path), opts=o, stream=0, check=False)
+        assert rc == vx.VX_EINVAL
+        assert not path.exists()

@@ -197,3 +197,69 @@ def test_window_table1_count_needs_sync(vx):
     _, n1, rb, rc = vx.vx_table_info(p.handle, vx.VX_TABLE1, check=False)
     assert rc == vx.VX_OK and rb == 12 and 0 < n1 < (1 << 16)
     p.close()
+
+
+@pytest.mark.parametrize("K,seed,c", [(16, 85, 0), (18, 86, 2), (20, 87, 3), (14, 88, 5)])
+def test_tiled_plot_file_equals_oracle(vx, tmp_path, K, seed, c):
+    # Table 2 streamed window by window into a flat plot file; Table 1 into
+    # pinned host memory.
+    key = plot_key(seed)
+    path = str(tmp_path / "plot.bin")
+    h1 = torch.empty(12 << K, dtype=torch.uint8, pin_memory=True)
+    opts = vx.make_opts(partition_log2=6) if c > K - 11 else None
+    rc, n1, n2, sec = vx.vx_plot_tiled_write(K, key, c, path, h1.data_ptr(), h1.numel(), opts)
+    r1, r2 = oracle_tables(K, key)
+    data = np.fromfile(path, dtype=np.uint8)
+    assert n1 == 1 << K and n2 == r2.shape[0] and data.size == 16 * n2 and sec > 0
+    assert np.array_equal(data.reshape(-1, 16), r2)
+    assert np.array_equal(h1.view(-1, 12).numpy(), r1)
+
+
+def test_tiled_plot_file_equals_whole_plot_file(vx, tmp_path):
+    # the bytes vx_plot_write gives for the whole plot
+    K, key = 20, plot_key(89)
+    a, b = str(tmp_path / "whole.bin"), str(tmp_path / "tiled.bin")
+    p = vx.Plot(K, key)
+    p.run()
+    p.sync()
+    vx.vx_plot_write(p.handle, a)
+    p.close()
+    vx.vx_plot_tiled_write(K, key, 3, b)
+    assert open(a, "rb").read() == open(b, "rb").read()
+
+
+def test_tiled_plot_file_bad_path(vx, tmp_path):
+    rc, _, _, _ = vx.vx_plot_tiled_write(16, plot_key(90), 2, str(tmp_path / "no" / "such" / "dir.bin"),
+                                         check=False)
+    assert rc == vx.VX_EINVAL
+
+
+def test_tiled_plots_in_a_caller_work_buffer(vx, tmp_path):
+    # Window buffers cut from one caller-owned device buffer, reused by
+    # consecutive plots (host memory, then a plot file).
+    K, c = 20, 2
+    dev_bytes, _, _ = vx.vx_plot_tiled_bytes(K, c)
+    work = torch.empty(dev_bytes, dtype=torch.uint8, device="cuda")
+    for seed in (96, 97):
+        key = plot_key(seed)
+        t1, t2 = vx.plot_tiled(K, key, c, work=work)
+        r1, r2 = oracle_tables(K, key)
+        assert np.array_equal(t1.numpy(), r1) and np.array_equal(t2.numpy(), r2), seed
+    path = str(tmp_path / "plot.bin")
+    vx.vx_plot_tiled_write(K, plot_key(98), c, path, d_work=work.data_ptr(), work_bytes=work.numel())
+    _, r2 = oracle_tables(K, plot_key(98))
+    assert np.array_equal(np.fromfile(path, dtype=np.uint8).reshape(-1, 16), r2)
+
+
+def test_tiled_work_buffer_checks(vx):
+    K, c = 18, 2
+    dev_bytes, h1b, h2b = vx.vx_plot_tiled_bytes(K, c)
+    work = torch.empty(dev_bytes + 256, dtype=torch.uint8, device="cuda")
+    h1 = torch.empty(h1b, dtype=torch.uint8)
+    h2 = torch.empty(h2b, dtype=torch.uint8)
+    key = plot_key(99)
+    for ptr, nb in [(work.data_ptr(), dev_bytes - 256),        # too small
+                    (work.data_ptr() + 128, dev_bytes)]:      # not 256-byte aligned
+        rc, _, _ = vx.vx_plot_tiled(K, key, c, h1.data_ptr(), h1b, h2.data_ptr(), h2b, check=False,
+                                    d_work=ptr, work_bytes=nb)
+        assert rc == vx.VX_EINVAL
