@@ -246,3 +246,14 @@ def test_tiled_write_rejects_bad_arguments_before_creating_the_file(vx, tmp_path
         rc, _, _, _ = vx.vx_plot_tiled_write(K, bytes(32), c, str(path), opts=o, stream=0, check=False)
         assert rc == vx.VX_EINVAL
         assert not path.exists()
+
+
+def test_server_rejects_window_options(vx):
+    # A served request is a whole plot: window options in the server's plot
+    # options are refused before any device work.
+    o = vx.vx_serve_opts()
+    o.size = ctypes.sizeof(vx.vx_serve_opts)
+    o.plot_opts = vx.make_opts(window_bits=1)
+    with pytest.raises(vx.VxError) as ei:
+        vx.vx_serve_create(o)
+    assert ei.value.code == vx.VX_EINVAL
