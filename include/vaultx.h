@@ -291,7 +291,8 @@ int vx_plot_write(vx_plot *plot, const char *path, double *seconds_d2h, double *
 /* Memory vx_plot_tiled needs for 2^K nonces in 2^window_bits windows
  * (vx_opts.window_bits; opts' own window fields must be zero):
  *   device_bytes:  two windows' buffers (one window computes while the other's
- *                  tables are copied out; one window if window_bits is 0)
+ *                  tables are copied out; one window if window_bits is 0),
+ *                  plus one byte per nonce of window ids for 1..8 window bits
  *   host_t1_bytes: 12 * 2^K, Table 1 exactly
  *   host_t2_bytes: the windows' Table-2 capacities, 16 B per record (a bound)
  * Any output pointer may be NULL.  Host only.  VX_EINVAL for a combination
@@ -313,7 +314,11 @@ int vx_plot_tiled_bytes(int K, const vx_opts *opts, int window_bits, uint64_t *d
  * host_t2_bytes long.  The host tables equal the whole plot's (vx_plot_run
  * without windows) byte for byte.  Pinned host memory (cudaHostAlloc) makes
  * the copies asynchronous; pageable memory works but serialises them.
- * Each window re-hashes all 2^K nonces.  *t1_count / *t2_count (may be
+ * With 1..8 window bits a first pass hashes every nonce and stores its
+ * window (one byte), and each window hashes only the nonces listed for it:
+ * two hashes of every nonce in all.  With more window bits, or the hash
+ * split into nonce chunks (vx_opts.pipeline_chunks), each window hashes
+ * every nonce and keeps its share.  *t1_count / *t2_count (may be
  * NULL) get the record counts.  Returns VX_OK; VX_ENOMEM if Table 2 did not
  * fit host_t2_bytes (*t2_count is then the size needed; Table 1 is
  * complete) or a window buffer could not be allocated; a window's

@@ -30,6 +30,7 @@ __global__ void k_key_setup(Desc *descs)
         *d.status = 0u;
         *d.ticket = 0u;
         *d.ticket_s = 0u;
+        if (d.wcount) *d.wcount = 0u;
     }
     const uint64_t n1 = d.p2 > 0 ? ((uint64_t)d.hchunks << d.p1) : 0ull;
     const uint64_t n2 = 1ull << d.p;
@@ -110,9 +111,13 @@ __device__ __forceinline__ void scan_and_claim(uint32_t *hist, uint32_t *loff, u
     }
 }
 
-// Windowed plots (WIN instances) keep the keys whose top wbits equal win and
-// bin them by the bits after those; a plot without a window (wbits 0) keeps
-// every key, so one WIN launch may also carry whole plots.
+// Windowed plots keep the keys whose top wbits equal win and bin them by the
+// bits after those.  kWinFilter instances hash every nonce and test its key
+// (a plot without a window, wbits 0, keeps every key, so one such launch may
+// also carry whole plots); kWinList instances hash only the nonces listed
+// for the window (Desc::wlist, from a pass that stored every nonce's window).
+enum { kWinNone = 0, kWinFilter = 1, kWinList = 2 };
+
 // Window bits plus bin bits are at most the 21 partition bits, so both tests
 // read only the key's high word.
 template <bool WIN>
@@ -129,21 +134,24 @@ __device__ __forceinline__ uint32_t key_bin(const Desc &d, uint64_t key, int bit
     return bits ? (WIN ? hi << d.wbits : hi) >> (32 - bits) : 0u;
 }
 
-template <int NT, int NPT, bool AGG, bool HALO, bool WIN>
+template <int NT, int NPT, bool AGG, bool HALO, int WM>
 __global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ descs, int nplots,
                                                      const uint32_t *__restrict__ tile_start,
                                                      int chunk)
 {
     using S = HashSmem<NT, NPT>;
     constexpr int T = S::T;
+    constexpr bool WIN = WM != kWinNone;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S &sm = *reinterpret_cast<S *>(smem_raw);
 
     const int plot = find_plot(tile_start, nplots, blockIdx.x);
     const Desc &d = descs[plot];
-    uint64_t lo, N;  // this chunk's nonces: [lo, N)
+    uint64_t lo, N;  // this chunk's nonces: [lo, N), or (list) list entries [0, N)
     nonce_chunk(d, chunk, lo, N);
+    if (WM == kWinList) N = min(*d.wcount, d.listcap);
     const uint64_t base = lo + (uint64_t)(blockIdx.x - tile_start[plot]) * T;
+    if (WM == kWinList && base >= N) return;  // the grid covers the list's capacity
     const bool two_level = d.p2 > 0;
     const int bits = two_level ? d.p1 : d.p;
     const int nbins = 1 << bits;
@@ -194,13 +202,16 @@ __global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ de
         uint32_t keep = 0;  // bit j: record j's nonce exists and its key is in the window
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
-            const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
+            const uint64_t idx = base + (uint64_t)j * NT + threadIdx.x;
+            uint32_t nonce;
+            if constexpr (WM == kWinList) nonce = idx < N ? d.wlist[idx] : 0u;
+            else nonce = (uint32_t)idx;
             uint32_t h0, h1;
-            b3_finish<false>(pre, (uint32_t)nonce, 0u, h0, h1);
+            b3_finish<false>(pre, nonce, 0u, h0, h1);
             key[j] = key64_of(h0, h1);
-            const bool valid = nonce < N && in_window<WIN>(d, key[j]);
+            const bool valid = idx < N && (WM != kWinFilter || in_window<true>(d, key[j]));
             keep |= (valid ? 1u : 0u) << j;
-            rank[j] = bin_rank<AGG>(sm.hist, key_bin<WIN>(d, key[j], bits), valid);
+            rank[j] = bin_rank<AGG>(sm.hist, key_bin<true>(d, key[j], bits), valid);
         }
         __syncthreads();
         scan_and_claim<NT>(sm.hist, sm.loff, sm.gbase, sm.ws, nbins, cnt, 0u);
@@ -208,9 +219,10 @@ __global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ de
 #pragma unroll
         for (int j = 0; j < NPT; ++j) {
             if (keep >> j & 1u) {
-                const uint32_t pos = sm.loff[key_bin<WIN>(d, key[j], bits)] + rank[j];
+                const uint64_t idx = base + (uint64_t)j * NT + threadIdx.x;
+                const uint32_t pos = sm.loff[key_bin<true>(d, key[j], bits)] + rank[j];
                 sm.keys[pos] = key[j];
-                sm.nonces[pos] = (uint32_t)(base + (uint64_t)j * NT + threadIdx.x);
+                sm.nonces[pos] = WM == kWinList ? d.wlist[idx] : (uint32_t)idx;
             }
         }
         __syncthreads();
@@ -219,7 +231,7 @@ __global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ de
     bool overflow = false, hover = false;
     for (uint32_t i = threadIdx.x; i < count; i += NT) {
         const uint64_t k = sm.keys[i];
-        const uint32_t bin = WIN ? key_bin<WIN>(d, k, bits) : (bits ? (uint32_t)(k >> (64 - bits)) : 0u);
+        const uint32_t bin = WIN ? key_bin<true>(d, k, bits) : (bits ? (uint32_t)(k >> (64 - bits)) : 0u);
         const uint32_t g = sm.gbase[bin] + (i - sm.loff[bin]);
         if (g < cap) {
             const uint64_t at = (uint64_t)bin * cap + g;
@@ -234,12 +246,12 @@ __global__ void __launch_bounds__(NT) k_hash_scatter(const Desc *__restrict__ de
     if (hover) atomicOr(d.status, kStHaloOverflow);
 }
 
-template <int NT, int NPT, bool AGG, bool HALO, bool WIN>
+template <int NT, int NPT, bool AGG, bool HALO, int WM>
 static cudaError_t launch_hs(const Desc *descs, int nplots, const uint32_t *tile_start,
                              uint32_t total_tiles, int chunk, cudaStream_t s)
 {
     const size_t smem = sizeof(HashSmem<NT, NPT>);
-    auto fn = k_hash_scatter<NT, NPT, AGG, HALO, WIN>;
+    auto fn = k_hash_scatter<NT, NPT, AGG, HALO, WM>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<total_tiles, NT, smem, s>>>(descs, nplots, tile_start, chunk);
@@ -248,26 +260,30 @@ static cudaError_t launch_hs(const Desc *descs, int nplots, const uint32_t *tile
 
 // AGG (warp-aggregated ranks) pays off when a warp's 32 records fall into
 // few bins; the host picks it from the smallest bin count in the launch.
-// HALO instances carry the cross-bucket halo code and WIN instances the
-// window filter; plain launches carry neither.
-template <bool HALO, bool WIN>
+// HALO instances carry the cross-bucket halo code and window instances the
+// window filter or the nonce list; plain launches carry neither.  A list
+// launch holds one windowed plot (never cross-bucket).
+template <bool HALO, int WM>
 static cudaError_t launch_hs_agg(const Desc *descs, int nplots, const uint32_t *tile_start,
                                  uint32_t total_tiles, bool agg, int chunk, cudaStream_t s)
 {
     constexpr int T = kHashThreads, P = kHashNoncesPerThread;
-    return agg ? launch_hs<T, P, true, HALO, WIN>(descs, nplots, tile_start, total_tiles, chunk, s)
-               : launch_hs<T, P, false, HALO, WIN>(descs, nplots, tile_start, total_tiles, chunk, s);
+    return agg ? launch_hs<T, P, true, HALO, WM>(descs, nplots, tile_start, total_tiles, chunk, s)
+               : launch_hs<T, P, false, HALO, WM>(descs, nplots, tile_start, total_tiles, chunk, s);
 }
 
 cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *tile_start,
                                 uint32_t total_tiles, HashCfg cfg, int chunk, cudaStream_t s)
 {
     if (total_tiles == 0) return cudaSuccess;
+    if (cfg.list)
+        return cfg.halo ? cudaErrorInvalidValue
+                        : launch_hs_agg<false, kWinList>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s);
     if (cfg.win)
-        return cfg.halo ? launch_hs_agg<true, true>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s)
-                        : launch_hs_agg<false, true>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s);
-    return cfg.halo ? launch_hs_agg<true, false>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s)
-                    : launch_hs_agg<false, false>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s);
+        return cfg.halo ? launch_hs_agg<true, kWinFilter>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s)
+                        : launch_hs_agg<false, kWinFilter>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s);
+    return cfg.halo ? launch_hs_agg<true, kWinNone>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s)
+                    : launch_hs_agg<false, kWinNone>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s);
 }
 
 // ------------------------------------------------- hash + direct scatter
@@ -277,35 +293,43 @@ cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *t
 // a global atomic and stores key64 and nonce there.  No shared memory and
 // no second scatter pass; the claims and scattered stores run on the LSU
 // and L2 while the ALU pipe -- the kernel's bound -- keeps hashing.
-template <int NT, int NPT, bool HALO, bool WIN>
+template <int NT, int NPT, bool HALO, int WM>
 __global__ void __launch_bounds__(NT) k_hash_direct(const Desc *__restrict__ descs, int nplots,
                                                     const uint32_t *__restrict__ tile_start,
                                                     int chunk)
 {
+    constexpr bool WIN = WM != kWinNone;
     const int plot = find_plot(tile_start, nplots, blockIdx.x);
     const Desc &d = descs[plot];
-    uint64_t lo, N;  // this chunk's nonces: [lo, N)
+    uint64_t lo, N;  // this chunk's nonces: [lo, N), or (list) list entries [0, N)
     nonce_chunk(d, chunk, lo, N);
+    if (WM == kWinList) N = min(*d.wcount, d.listcap);
     const uint64_t base = lo + (uint64_t)(blockIdx.x - tile_start[plot]) * (NT * NPT);
+    if (WM == kWinList && base >= N) return;  // the grid covers the list's capacity
     const int bits = d.p;
     const uint32_t cap = d.cap2;
     uint32_t pre[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) pre[i] = d.pre1[i];
+    // the nonce of entry idx: the entry itself, or (list) the listed nonce
+    auto nonce_of = [&](uint64_t idx) -> uint32_t {
+        return WM == kWinList ? (idx < N ? d.wlist[idx] : 0u) : (uint32_t)idx;
+    };
     uint64_t key[NPT];
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
         uint32_t h0, h1;
-        b3_finish<false>(pre, (uint32_t)(base + (uint64_t)j * NT + threadIdx.x), 0u, h0, h1);
+        b3_finish<false>(pre, nonce_of(base + (uint64_t)j * NT + threadIdx.x), 0u, h0, h1);
         key[j] = key64_of(h0, h1);
     }
     uint32_t slot[NPT];
 #pragma unroll
     for (int j = 0; j < NPT; ++j) {
         const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
-        const uint32_t bin = WIN ? key_bin<WIN>(d, key[j], bits) : (bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u);
+        const uint32_t bin = WIN ? key_bin<true>(d, key[j], bits) : (bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u);
         // A record outside the window claims no slot: its slot reads as "none".
-        slot[j] = (nonce < N && in_window<WIN>(d, key[j])) ? atomicAdd(&d.cnt2[bin], 1u) : 0xffffffffu;
+        slot[j] = (nonce < N && in_window<WM == kWinFilter>(d, key[j])) ? atomicAdd(&d.cnt2[bin], 1u)
+                                                                         : 0xffffffffu;
     }
     bool overflow = false, hover = false;
 #pragma unroll
@@ -313,25 +337,25 @@ __global__ void __launch_bounds__(NT) k_hash_direct(const Desc *__restrict__ des
         const uint64_t nonce = base + (uint64_t)j * NT + threadIdx.x;
         if (nonce >= N) continue;
         if (WIN && slot[j] == 0xffffffffu) continue;
-        const uint32_t bin = WIN ? key_bin<WIN>(d, key[j], bits) : (bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u);
+        const uint32_t bin = WIN ? key_bin<true>(d, key[j], bits) : (bits ? (uint32_t)(key[j] >> (64 - bits)) : 0u);
         if (slot[j] < cap) {
             const uint64_t at = (uint64_t)bin * cap + slot[j];
             d.b_keys[at] = key[j];
-            d.b_nonces[at] = (uint32_t)nonce;
+            d.b_nonces[at] = nonce_of(nonce);
         } else {
             overflow = true;
         }
-        if (HALO) halo_add(d, bin, key[j], (uint32_t)nonce, hover);
+        if (HALO) halo_add(d, bin, key[j], nonce_of(nonce), hover);
     }
     if (overflow) atomicOr(d.status, kStSlot2Overflow);
     if (hover) atomicOr(d.status, kStHaloOverflow);
 }
 
-template <bool HALO, bool WIN>
+template <bool HALO, int WM>
 static cudaError_t launch_hd(const Desc *descs, int nplots, const uint32_t *tile_start,
                              uint32_t total_tiles, int chunk, cudaStream_t s)
 {
-    k_hash_direct<kHashThreads, kHashNoncesPerThread, HALO, WIN><<<total_tiles, kHashThreads, 0, s>>>(
+    k_hash_direct<kHashThreads, kHashNoncesPerThread, HALO, WM><<<total_tiles, kHashThreads, 0, s>>>(
         descs, nplots, tile_start, chunk);
     return cudaGetLastError();
 }
@@ -340,11 +364,14 @@ cudaError_t launch_hash_direct(const Desc *descs, int nplots, const uint32_t *ti
                                uint32_t total_tiles, int chunk, cudaStream_t s, HashCfg cfg)
 {
     if (total_tiles == 0) return cudaSuccess;
+    if (cfg.list)
+        return cfg.halo ? cudaErrorInvalidValue
+                        : launch_hd<false, kWinList>(descs, nplots, tile_start, total_tiles, chunk, s);
     if (cfg.win)
-        return cfg.halo ? launch_hd<true, true>(descs, nplots, tile_start, total_tiles, chunk, s)
-                        : launch_hd<false, true>(descs, nplots, tile_start, total_tiles, chunk, s);
-    return cfg.halo ? launch_hd<true, false>(descs, nplots, tile_start, total_tiles, chunk, s)
-                    : launch_hd<false, false>(descs, nplots, tile_start, total_tiles, chunk, s);
+        return cfg.halo ? launch_hd<true, kWinFilter>(descs, nplots, tile_start, total_tiles, chunk, s)
+                        : launch_hd<false, kWinFilter>(descs, nplots, tile_start, total_tiles, chunk, s);
+    return cfg.halo ? launch_hd<true, kWinNone>(descs, nplots, tile_start, total_tiles, chunk, s)
+                    : launch_hd<false, kWinNone>(descs, nplots, tile_start, total_tiles, chunk, s);
 }
 
 // ------------------------------------------------ Table-2 pair hashing
@@ -467,6 +494,91 @@ cudaError_t launch_t2_hash_slots(const Desc *descs, int nplots, const uint32_t *
 {
     if (total_tiles == 0) return cudaSuccess;
     k_t2_hash_slots<<<total_tiles, kT2HashThreads, 0, s>>>(descs, nplots, tile_start);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------ tiled plots: windows
+// The first pass of a tiled plot: the window (top c <= 8 bits of key64) of
+// every nonce, one byte each; four nonces per thread and one 32-bit store.
+__global__ void __launch_bounds__(256) k_window_ids(uint32_t k0, uint32_t k1, uint32_t k2,
+                                                    uint32_t k3, uint32_t k4, uint32_t k5,
+                                                    uint32_t k6, uint32_t k7, uint64_t N, int c,
+                                                    uint32_t *__restrict__ ids4)
+{
+    const uint32_t key[8] = {k0, k1, k2, k3, k4, k5, k6, k7};
+    uint32_t pre[16];
+    b3_key_setup(key, 4u, pre);
+    const uint64_t words = (N + 3) / 4;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) {
+        uint32_t packed = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint64_t nonce = 4 * i + j;
+            uint32_t h0, h1;
+            b3_finish<false>(pre, (uint32_t)nonce, 0u, h0, h1);
+            const uint32_t id = bswap32(h0) >> (32 - c);  // key64's top c bits
+            packed |= (nonce < N ? id : 0u) << (8 * j);
+        }
+        ids4[i] = packed;
+    }
+}
+
+cudaError_t launch_window_ids(const uint32_t key[8], uint64_t N, int c, uint8_t *ids, cudaStream_t s)
+{
+    if (N == 0 || c < 1 || c > 8) return cudaErrorInvalidValue;
+    uint64_t blocks = ((N + 3) / 4 + 255) / 256;
+    if (blocks > 152ull * 64) blocks = 152ull * 64;
+    k_window_ids<<<(unsigned)blocks, 256, 0, s>>>(key[0], key[1], key[2], key[3], key[4], key[5],
+                                                  key[6], key[7], N, c,
+                                                  reinterpret_cast<uint32_t *>(ids));
+    return cudaGetLastError();
+}
+
+// A window's nonces (wids[n] == win) listed into wlist in any order (the
+// partition sort orders records by (key64, nonce)): each CTA reads 4096
+// window ids, 16 per thread, ranks its matches with one block scan and
+// claims their places with one atomic on wcount.  Entries past the list's
+// capacity are dropped and reported.
+constexpr int kListThreads = 256;
+constexpr int kListPerThread = 16;
+
+__global__ void __launch_bounds__(kListThreads) k_window_list(const Desc *__restrict__ dp, uint64_t N)
+{
+    __shared__ uint32_t ws[kListThreads / 32 + 1];
+    __shared__ uint32_t s_base;
+    const Desc &d = *dp;
+    const uint64_t n0 = ((uint64_t)blockIdx.x * kListThreads + threadIdx.x) * kListPerThread;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (n0 < N) v = *reinterpret_cast<const uint4 *>(d.wids + n0);  // ids rounded up to 16 bytes
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t match = 0;  // bit b: nonce n0 + b is in the window
+#pragma unroll
+    for (int b = 0; b < kListPerThread; ++b) {
+        const bool m = n0 + b < N && ((w[b >> 2] >> (8 * (b & 3))) & 0xffu) == d.win;
+        match |= (m ? 1u : 0u) << b;
+    }
+    uint32_t total;
+    const uint32_t r = block_exclusive_scan_u32<kListThreads>((uint32_t)__popc(match), ws, &total);
+    if (threadIdx.x == 0) s_base = total ? atomicAdd(d.wcount, total) : 0u;
+    __syncthreads();
+    uint32_t at = s_base + r;
+    bool over = false;
+    for (int b = 0; b < kListPerThread; ++b) {
+        if (!(match >> b & 1u)) continue;
+        if (at < d.listcap) d.wlist[at] = (uint32_t)(n0 + b);
+        else over = true;
+        ++at;
+    }
+    if (over) atomicOr(d.status, kStWinList);
+}
+
+cudaError_t launch_window_list(const Desc *desc, uint64_t N, cudaStream_t s)
+{
+    const uint64_t per = (uint64_t)kListThreads * kListPerThread;
+    const uint64_t blocks = (N + per - 1) / per;
+    if (blocks == 0 || blocks > 0x7FFFFFFFull) return cudaErrorInvalidValue;
+    k_window_list<<<(unsigned)blocks, kListThreads, 0, s>>>(desc, N);
     return cudaGetLastError();
 }
 

@@ -141,6 +141,12 @@ void fill_desc(const vx_plot *p, Desc *d)
     d->pk = pl.pk;
     d->wbits = pl.wbits;
     d->win = pl.win;
+    if (p->wids && pl.wbits) {
+        d->wids = p->wids;
+        d->listcap = pl.listcap;
+        d->wlist = reinterpret_cast<uint32_t *>(p->d_t2);  // free until the sort writes pairs
+        d->wcount = reinterpret_cast<uint32_t *>(p->d_scratch + pl.o_wcount);
+    }
     if (pl.p2 > 0) {
         d->a_keys = reinterpret_cast<uint64_t *>(p->d_t1);
         d->a_nonces = reinterpret_cast<uint32_t *>(p->d_t1 + pl.regionA_keys);
@@ -184,7 +190,7 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
     const int W = n + 1;
     enum { A_STG = 0, A_DIR = 8, A_S2 = 16, A_PC = 24, A_T2H = 32, A_SCAN = 40, A_PART = 41 };
     static_assert(A_PART + 1 == vx::kTileArrays, "tile arrays");
-    bool fuse = true, slots = true, halo = false, win = false;
+    bool fuse = true, slots = true, halo = false, win = false, list = false;
     L->G = L->C = 1;
     L->max_cap2 = 0;
     L->max_dbits = 1;
@@ -197,6 +203,11 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
         slots = slots && pl.pair_slots;
         halo = halo || pl.scope != 0;
         win = win || pl.wbits != 0;
+        if (plots[i]->wids && pl.wbits) {
+            // a listed window runs alone, its hash in one nonce chunk
+            if (n != 1 || pl.hchunks != 1) return VX_EINVAL;
+            list = true;
+        }
         L->G = std::max(L->G, pl.hchunks);
         L->C = std::max(L->C, pl.pchunks);
         L->max_cap2 = std::max(L->max_cap2, pl.cap2 + pl.hcap);
@@ -211,7 +222,7 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
         uint64_t cnt[vx::kTileArrays] = {};
         const bool staged = pl.mode == kScatterStaged;
         for (int g = 0; g < vx::kMaxChunks && g < pl.hchunks; ++g) {
-            cnt[(staged ? A_STG : A_DIR) + g] = pl.tiles_hash;
+            cnt[(staged ? A_STG : A_DIR) + g] = list ? pl.tiles_list : pl.tiles_hash;
             if (staged && pl.p2 > 0) cnt[A_S2 + g] = pl.tiles_s2;
         }
         const uint64_t np = 1ull << pl.p;
@@ -238,6 +249,8 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
     L->pair_slots = slots;
     L->halo = halo;
     L->win = win;
+    L->list = list;
+    L->list_N = list ? plots[0]->plan.N : 0;
     for (int g = 0; g < vx::kMaxChunks; ++g) {
         L->t_staged[g] = d + (A_STG + g) * W;
         L->t_direct[g] = d + (A_DIR + g) * W;
@@ -300,7 +313,8 @@ int map_status(uint32_t st)
     if (st & vx::kStTimeout) return VX_ETIMEDOUT;
     if (st & vx::kStBadTicket) return VX_ECUDA;
     if (st & (vx::kStSlot1Overflow | vx::kStSlot2Overflow | vx::kStCountMismatch |
-              vx::kStPartitionTooBig | vx::kStPairSlot | vx::kStHaloOverflow | vx::kStSort2))
+              vx::kStPartitionTooBig | vx::kStPairSlot | vx::kStHaloOverflow | vx::kStSort2 |
+              vx::kStWinList))
         return VX_EOVERFLOW;
     if (st & vx::kStT2Capacity) return VX_ENOMEM;
     return VX_OK;
@@ -317,6 +331,7 @@ std::string status_text(uint32_t st)
     if (st & vx::kStPairSlot) s += "a partition's pairs exceed its pair slot (use t2_placement 1); ";
     if (st & vx::kStHaloOverflow) s += "a partition's cross-bucket halo exceeds its capacity; ";
     if (st & vx::kStSort2) s += "sorting Table 2: a slot overflowed or records were lost; ";
+    if (st & vx::kStWinList) s += "a window's nonce list exceeded its capacity; ";
     if (st & vx::kStTimeout) s += "device wait timed out; ";
     if (st & vx::kStBadTicket) s += "work ticket out of range (state not reset); ";
     return s;
@@ -355,16 +370,20 @@ cudaError_t launch_front(const LaunchSet &L, const vx::Lanes &ln, const vx::Trac
 {
     const cudaStream_t A = ln.main, B = ln.aux;
     VX_LAUNCH(KID_SETUP, A, vx::launch_key_setup(L.descs, L.n, A));
+    if (L.list) {  // the window's nonces, listed from the window ids
+        const cudaError_t e = vx::launch_window_list(L.descs, L.list_N, A);
+        if (e != cudaSuccess) return e;
+    }
     bool any_s2 = false;
     for (int g = 0; g < L.G; ++g) any_s2 = any_s2 || L.n_s2[g] > 0;
     const bool ov = B && L.G > 1 && any_s2;
     for (int g = 0; g < L.G; ++g) {
         if (L.n_staged[g])
             VX_LAUNCH(KID_STAGED, A, vx::launch_hash_scatter(L.descs, L.n, L.t_staged[g], L.n_staged[g],
-                                                             vx::HashCfg{L.agg, L.halo, L.win}, g, A));
+                                                             vx::HashCfg{L.agg, L.halo, L.win, L.list}, g, A));
         if (L.n_direct[g])
             VX_LAUNCH(KID_DIRECT, A, vx::launch_hash_direct(L.descs, L.n, L.t_direct[g], L.n_direct[g], g, A,
-                                                            vx::HashCfg{L.agg, L.halo, L.win}));
+                                                            vx::HashCfg{L.agg, L.halo, L.win, L.list}));
         if (L.n_s2[g]) {
             if (ov) {
                 cudaEventRecord(ln.sync[g], A);

@@ -40,6 +40,8 @@ struct LaunchSet {
     bool pair_slots;   // every plot uses the slot placement (t_t2h[0] = slot pair-hash grid)
     bool halo;         // some plot matches across buckets: kernels with the halo code
     bool win;          // some plot is a window: hash kernels with the window filter
+    bool list;         // the one plot hashes its window's nonce list (tiled plots)
+    uint64_t list_N;   // its nonce count (the list kernel's input)
     uint32_t max_cap2;
     int max_dbits;
     int max_p2;        // widest second scatter level of the launch
@@ -86,6 +88,8 @@ struct vx_plot {
     uint64_t t2_count = 0;
     bool t1_known = false;          // a window's Table-1 count, read by vx_sync
     uint64_t t1_count = 0;
+    const uint8_t *wids = nullptr;  // window id of every nonce (tiled plots): the
+                                    // window hashes its listed nonces only
     uint32_t status = 0;
     std::string err;
     // Second streams and fork/join events of the pipelined run.

@@ -35,6 +35,7 @@ constexpr uint32_t kStBadTicket = 1u << 6;
 constexpr uint32_t kStPairSlot = 1u << 7;     // a partition's pairs exceed its pair slot
 constexpr uint32_t kStHaloOverflow = 1u << 8; // a partition's halo exceeds its capacity
 constexpr uint32_t kStSort2 = 1u << 9;        // sorted Table 2: slot overflow or lost records
+constexpr uint32_t kStWinList = 1u << 10;     // a window's nonce list exceeds its capacity
 
 // ------------------------------------------------------ plot descriptor
 // One plot's plan and buffers.  The host fills everything but pre1/pre2,
@@ -61,7 +62,11 @@ struct Desc {
     int32_t pk;          // partition bits in key space (p + wbits): every key shift
     uint32_t wbits;      // window: the plot keeps the records whose top wbits
     uint32_t win;        //   key bits equal win (wbits 0: every record)
-    uint32_t pad0;
+    uint32_t listcap;    // window nonce list capacity (entries), if wids
+    const uint8_t *wids; // window id of every nonce (top wbits of key64), or null:
+                         //   the hash kernels then hash every nonce and filter
+    uint32_t *wlist;     // [listcap] the window's nonces, listed from wids
+    uint32_t *wcount;    // entries in wlist (zeroed by the key setup)
     uint32_t *halo_cnt;  // [2^p] halo fill counters
     uint64_t *halo_keys; // [2^p * hcap] records of partition f within D of its
     uint32_t *halo_nonces; //            lower edge (unsorted): f - 1's halo
@@ -495,6 +500,7 @@ struct HashCfg {
     bool agg;     // warp-aggregated histogram (few first-level bins)
     bool halo;    // some plot of the launch matches across buckets (halo code)
     bool win;     // some plot of the launch is a window (window filter)
+    bool list;    // the launch's one plot hashes its window's nonce list
 };
 cudaError_t launch_key_setup(Desc *descs, int nplots, cudaStream_t s);
 // Hash kernels and the second scatter level take one nonce chunk (of
@@ -544,6 +550,12 @@ struct Sort2Launch {
 };
 cudaError_t launch_sort2(const Sort2Desc *d_desc, const Sort2Launch &g, cudaStream_t s);
 size_t sort2_smem_bytes(uint32_t cap, int dbits);
+// Window id (top c <= 8 bits of key64) of every nonce 0 .. N-1, one byte
+// each at ids (16-byte aligned, N rounded up to 16 bytes).
+cudaError_t launch_window_ids(const uint32_t key[8], uint64_t N, int c, uint8_t *ids, cudaStream_t s);
+// Lists the nonces of one plot's window from its Desc::wids into Desc::wlist
+// (single plot; N nonces).
+cudaError_t launch_window_list(const Desc *desc, uint64_t N, cudaStream_t s);
 cudaError_t launch_hash_records(const uint32_t key[8], uint64_t nonce0, uint64_t count,
                                 uint32_t *out, cudaStream_t s);
 cudaError_t launch_pair_hash(const uint32_t key[8], const uint32_t *pairs, uint64_t count,

@@ -53,6 +53,7 @@ struct Plan {
     uint32_t tiles_staged, tiles_direct;   // tiles_hash of the kernel the mode uses, 0 for the other
     uint32_t tiles_scan, tiles_t2h;        // Table-1 offset scan chunks, pair-hash CTAs
     uint32_t tiles_t2s;                    // pair-hash CTAs reading pair slots
+    uint32_t listcap, tiles_list;          // window nonce list: capacity, hash CTAs over it
     uint64_t regionA_keys, regionB_keys;   // byte offset of the nonce array in each slot region
     uint64_t regionA_bytes, regionB_bytes;
     uint64_t t1_bytes, t2_bytes, scratch_bytes;
@@ -60,6 +61,7 @@ struct Plan {
         o_desc, o_tiles;
     uint64_t o_regionB;                    // final-partition slots (scratch buffer)
     uint64_t o_halo_cnt, o_halo_keys, o_halo_nonces;  // scope 1 halos (scratch buffer)
+    uint64_t o_wcount;                     // window nonce list entry counter (scratch buffer)
 };
 
 inline uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
@@ -297,7 +299,11 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     // partition slots can hold, so no write can pass the buffer's end.
     const uint64_t t1_rec = P.wbits ? std::min<uint64_t>(P.N, ((uint64_t)1 << P.p) * P.cap2) : P.N;
     const uint64_t t1_tab = 12 * t1_rec;
-    const uint64_t t2_tab = 16 * P.t2cap;
+    // A window of a tiled plot may hash from a list of its nonces (as many
+    // as its Table 1 can hold), kept in its Table-2 buffer until the sort.
+    P.listcap = P.wbits ? (uint32_t)std::min<uint64_t>(t1_rec, 0xFFFFFFFFull) : 0u;
+    P.tiles_list = (uint32_t)(((uint64_t)P.listcap + kPlanHashTile - 1) / kPlanHashTile);
+    const uint64_t t2_tab = std::max<uint64_t>(16 * P.t2cap, 4 * (uint64_t)P.listcap);
     P.t1_bytes = round_up((t1_tab > P.regionA_bytes ? t1_tab : P.regionA_bytes) + 256, 256);
     P.t2_bytes = round_up(t2_tab + 256, 256);
     // Scratch layout.
@@ -321,6 +327,7 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     P.o_halo_cnt = at; at = round_up(at + 4 * nh, 256);
     P.o_halo_keys = at; at = round_up(at + 8 * nh * P.hcap, 256);
     P.o_halo_nonces = at; at = round_up(at + 4 * nh * P.hcap, 256);
+    P.o_wcount = at; at = round_up(at + 4, 256);
     P.scratch_bytes = at;
     *pl = P;
     return VX_OK;

@@ -11,6 +11,12 @@
 // moving the 26 GB of unsorted records across the host link once, so
 // recomputing beats spilling the records and reading them back.
 //
+// A first pass hashes every nonce once and stores its window (one byte);
+// each window then lists its own nonces from those bytes and hashes only
+// them, so a plot of 2^c windows costs two hashes of every nonce, not 2^c.
+// (Without the byte array -- more than 8 window bits, or the hash split
+// into nonce chunks -- each window hashes every nonce and keeps its share.)
+//
 // Two window plots alternate: while one computes on the caller's stream, the
 // other's tables go to the host -- into the caller's memory on a copy stream
 // of the library's own, or (Table 2) appended to a flat plot file through
@@ -52,6 +58,12 @@ struct Sink {
     int fd = -1;
 };
 
+// Whether a tiled plot stores window ids (one byte per nonce) and lists
+// each window's nonces from them.
+bool use_ids(const vx::Plan &pl) { return pl.wbits >= 1 && pl.wbits <= 8 && pl.hchunks == 1; }
+
+uint64_t ids_bytes(const vx::Plan &pl) { return use_ids(pl) ? vx::round_up(pl.N, 256) : 0; }
+
 int tiled_run(int K, const uint8_t key[32], const vx_opts *opts, int window_bits, void *d_work,
               uint64_t work_bytes, void *host_t1, uint64_t host_t1_bytes, const Sink &sink,
               uint64_t *t1_count, uint64_t *t2_count, void *stream)
@@ -67,9 +79,13 @@ int tiled_run(int K, const uint8_t key[32], const vx_opts *opts, int window_bits
     const uint32_t nw = 1u << window_bits;
     const int nbuf = nw > 1 ? 2 : 1;
     // Window buffers: caller-owned work memory cut into nbuf sets of
-    // (Table 1, Table 2, scratch), or library-owned ones for this call.
+    // (Table 1, Table 2, scratch) and the window ids, or library-owned ones
+    // for this call.
     const uint64_t one = pl.t1_bytes + pl.t2_bytes + pl.scratch_bytes;
-    if (d_work && (work_bytes < one * nbuf || ((uintptr_t)d_work & 255u))) return VX_EINVAL;
+    const uint64_t idb = ids_bytes(pl);
+    if (d_work && (work_bytes < one * nbuf + idb || ((uintptr_t)d_work & 255u))) return VX_EINVAL;
+    uint8_t *ids = nullptr;
+    bool own_ids = false;
 
     vx_plot *P[2] = {nullptr, nullptr};
     cudaStream_t cs = nullptr;
@@ -90,6 +106,24 @@ int tiled_run(int K, const uint8_t key[32], const vx_opts *opts, int window_bits
         if (cudaEventCreateWithFlags(&copied[i], cudaEventDisableTiming) != cudaSuccess) rc = VX_ECUDA;
 
     cudaStream_t s = (cudaStream_t)stream;
+    if (rc == VX_OK && idb) {
+        if (d_work) {
+            ids = (uint8_t *)d_work + one * nbuf;
+        } else if (cudaMalloc((void **)&ids, idb) == cudaSuccess) {
+            own_ids = true;
+        } else {
+            cudaGetLastError();
+            rc = VX_ENOMEM;
+        }
+        if (rc == VX_OK) {
+            uint32_t kw[8];
+            for (int i = 0; i < 8; ++i)
+                kw[i] = (uint32_t)key[4 * i] | ((uint32_t)key[4 * i + 1] << 8) |
+                        ((uint32_t)key[4 * i + 2] << 16) | ((uint32_t)key[4 * i + 3] << 24);
+            if (vx::launch_window_ids(kw, N, window_bits, ids, s) != cudaSuccess) rc = VX_ECUDA;
+            for (int i = 0; i < nbuf; ++i) P[i]->wids = ids;
+        }
+    }
     uint64_t off1 = 0, off2 = 0;
     bool t2_full = false;
     // Waits for window plot X (its own completion event only, so the window
@@ -142,7 +176,11 @@ int tiled_run(int K, const uint8_t key[32], const vx_opts *opts, int window_bits
 
     for (int i = 0; i < 2; ++i) {
         if (copied[i]) cudaEventDestroy(copied[i]);
-        vx_plot_destroy(P[i]);
+        vx_plot_destroy(P[i]);  // waits for the plot's own work
+    }
+    if (own_ids) {
+        cudaStreamSynchronize(s);
+        cudaFree(ids);
     }
     if (cs) cudaStreamDestroy(cs);
     return rc;
@@ -161,7 +199,7 @@ extern "C" int vx_plot_tiled_bytes(int K, const vx_opts *opts, int window_bits,
     if (vx::make_plan(K, &o, &pl, &why) != VX_OK) return VX_EINVAL;
     const uint64_t nw = 1ull << window_bits;
     const uint64_t one = pl.t1_bytes + pl.t2_bytes + pl.scratch_bytes;
-    if (device_bytes) *device_bytes = one * (nw > 1 ? 2 : 1);
+    if (device_bytes) *device_bytes = one * (nw > 1 ? 2 : 1) + ids_bytes(pl);
     if (host_t1_bytes) *host_t1_bytes = 12ull << K;
     if (host_t2_bytes) *host_t2_bytes = 16 * pl.t2cap * nw;
     return VX_OK;

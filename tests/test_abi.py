@@ -206,7 +206,7 @@ def test_window_plans_shrink_and_reject_cleanly(vx):
         assert t1 >= 12 * 2 ** 31 / 2 ** c and t2 >= 16 * E / 2 ** c
         assert sum(parts) < 1.25 * whole / 2 ** c + (64 << 20), (c, sum(parts), whole)
         dev, h1, h2 = vx.vx_plot_tiled_bytes(31, c)
-        assert dev == 2 * sum(parts)
+        assert dev == 2 * sum(parts) + 2 ** 31  # + one window-id byte per nonce
         assert h1 == 12 * 2 ** 31 and h2 >= 16 * E
     # c = 0 is the whole plot, one buffer
     assert vx.vx_plot_tiled_bytes(31, 0)[0] == whole

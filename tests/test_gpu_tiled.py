@@ -1,7 +1,10 @@
 """Windowed plots and chunked device-memory tiling vs the CPU oracle.
 
 A window (vx_opts.window_bits = c, window = w) keeps the records whose key64
-has top c bits == w: 2^(24-c) consecutive logical buckets.  The bucket-scope
+has top c bits == w: 2^(24-c) consecutive logical buckets.  A window plot of
+its own hashes every nonce and filters; vx_plot_tiled stores every nonce's
+window in a first pass and lets each window hash only its listed nonces
+(up to 8 window bits, hash in one nonce chunk).  The bucket-scope
 match never leaves a bucket, so a window's tables must equal the oracle's
 whole-plot tables restricted to those buckets, and vx_plot_tiled's host
 tables (all windows, in order) must equal the whole plot's, bit for bit.
@@ -102,6 +105,10 @@ TILED_CASES = [
     (19, 76, 2, dict(t2_placement=2)),
     (19, 77, 3, dict(fuse_pair_hash=1)),
     (13, 78, 7, dict(partition_log2=6)),                       # 128 windows of one partition
+    # windows that hash every nonce and filter (no window-id pass): the hash
+    # split into nonce chunks, and more than 8 window bits
+    (20, 83, 2, dict(pipeline_chunks=4, partition_log2=8)),
+    (16, 84, 9, dict(partition_log2=6)),
 ]
 
 
