@@ -174,14 +174,15 @@ int tiled_run(int K, const uint8_t key[32], const vx_opts *opts, int window_bits
     if (t1_count) *t1_count = off1;
     if (t2_count) *t2_count = off2;
 
+    // Nothing of this call may still run when it returns (the caller owns
+    // d_work): the window plots wait for their own work, the stream for the
+    // id pass queued before them.
     for (int i = 0; i < 2; ++i) {
         if (copied[i]) cudaEventDestroy(copied[i]);
-        vx_plot_destroy(P[i]);  // waits for the plot's own work
+        vx_plot_destroy(P[i]);
     }
-    if (own_ids) {
-        cudaStreamSynchronize(s);
-        cudaFree(ids);
-    }
+    if (ids) cudaStreamSynchronize(s);
+    if (own_ids) cudaFree(ids);
     if (cs) cudaStreamDestroy(cs);
     return rc;
 }
