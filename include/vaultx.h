@@ -300,6 +300,12 @@ int vx_plot_write(vx_plot *plot, const char *path, double *seconds_d2h, double *
 int vx_plot_tiled_bytes(int K, const vx_opts *opts, int window_bits, uint64_t *device_bytes,
                         uint64_t *host_t1_bytes, uint64_t *host_t2_bytes);
 
+/* The fewest window bits (0 .. 16) whose vx_plot_tiled_bytes device_bytes
+ * fit budget_bytes, into *window_bits.  VX_ENOMEM if none does (the
+ * partition bits bound the window bits), VX_EINVAL for bad arguments.  Host
+ * only. */
+int vx_plot_tiled_window_bits(int K, const vx_opts *opts, uint64_t budget_bytes, int *window_bits);
+
 /* A whole plot in device memory of about 2^(1 - window_bits) of its
  * footprint (chunked VRAM tiling, Sec. V future work): the 2^window_bits
  * windows of vx_opts.window_bits are built one after the other in two

@@ -206,6 +206,24 @@ extern "C" int vx_plot_tiled_bytes(int K, const vx_opts *opts, int window_bits,
     return VX_OK;
 }
 
+extern "C" int vx_plot_tiled_window_bits(int K, const vx_opts *opts, uint64_t budget_bytes,
+                                         int *window_bits)
+{
+    if (!window_bits) return VX_EINVAL;
+    // Fewest windows first: the device footprint falls with every extra bit
+    // (one bit is the exception: two half-plot buffers are no smaller than one
+    // whole plot), and each extra window costs a little time.
+    for (int c = 0; c <= 16; ++c) {
+        uint64_t dev = 0;
+        if (vx_plot_tiled_bytes(K, opts, c, &dev, nullptr, nullptr) != VX_OK) break;
+        if (dev <= budget_bytes) {
+            *window_bits = c;
+            return VX_OK;
+        }
+    }
+    return VX_ENOMEM;
+}
+
 extern "C" int vx_plot_tiled(int K, const uint8_t key[32], const vx_opts *opts, int window_bits,
                              void *d_work, uint64_t work_bytes, void *host_t1,
                              uint64_t host_t1_bytes, void *host_t2, uint64_t host_t2_bytes,

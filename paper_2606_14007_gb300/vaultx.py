@@ -107,6 +107,7 @@ def lib():
             "vx_sort_table2": (c_int, [vp, vp, u64, vp]),
             "vx_plot_batch": (c_int, [P(vp), c_int, vp]),
             "vx_plot_tiled_bytes": (c_int, [c_int, P(vx_opts), c_int, P(u64), P(u64), P(u64)]),
+            "vx_plot_tiled_window_bits": (c_int, [c_int, P(vx_opts), u64, P(c_int)]),
             "vx_plot_tiled": (c_int, [c_int, u8p, P(vx_opts), c_int, vp, u64, vp, u64, vp, u64, P(u64),
                                       P(u64), vp]),
             "vx_plot_tiled_write": (c_int, [c_int, u8p, P(vx_opts), c_int, vp, u64, ctypes.c_char_p, vp,
@@ -329,6 +330,14 @@ def vx_plot_tiled_bytes(K: int, window_bits: int, opts: vx_opts | None = None) -
     return a.value, b.value, c.value
 
 
+def vx_plot_tiled_window_bits(K: int, budget_bytes: int, opts: vx_opts | None = None) -> int:
+    """The fewest window bits whose tiled device footprint fits budget_bytes."""
+    c = ctypes.c_int()
+    _check(lib().vx_plot_tiled_window_bits(K, ctypes.byref(opts) if opts else None, budget_bytes,
+                                           ctypes.byref(c)), "vx_plot_tiled_window_bits")
+    return c.value
+
+
 def vx_plot_tiled(K: int, key: bytes, window_bits: int, host_t1: int, host_t1_bytes: int,
                   host_t2: int, host_t2_bytes: int, opts: vx_opts | None = None, stream=None,
                   check: bool = True, d_work: int = 0, work_bytes: int = 0):
@@ -362,13 +371,16 @@ def vx_plot_tiled_write(K: int, key: bytes, window_bits: int, path: str, host_t1
     return rc, n1.value, n2.value, sec.value
 
 
-def plot_tiled(K: int, key: bytes, window_bits: int, opts: vx_opts | None = None, table1: bool = True,
-               pin: bool = True, stream=None, work=None):
+def plot_tiled(K: int, key: bytes, window_bits: int | None, opts: vx_opts | None = None,
+               table1: bool = True, pin: bool = True, stream=None, work=None, budget: int = 0):
     """vx_plot_tiled into fresh host tensors: returns (t1, t2), uint8 views
     shaped (records, 12) and (records, 16) (t1 None unless table1).  `work`:
     an optional uint8 device tensor of at least vx_plot_tiled_bytes' device
-    bytes for the window buffers."""
+    bytes for the window buffers.  window_bits None: the fewest that fit
+    `budget` bytes of device memory."""
     import torch
+    if window_bits is None:
+        window_bits = vx_plot_tiled_window_bits(K, budget, opts)
     _, h1, h2 = vx_plot_tiled_bytes(K, window_bits, opts)
     t1 = torch.empty(h1 if table1 else 0, dtype=torch.uint8, pin_memory=pin)
     t2 = torch.empty(h2, dtype=torch.uint8, pin_memory=pin)

@@ -257,3 +257,18 @@ def test_server_rejects_window_options(vx):
     with pytest.raises(vx.VxError) as ei:
         vx.vx_serve_create(o)
     assert ei.value.code == vx.VX_EINVAL
+
+
+def test_tiled_window_bits_fit_a_budget(vx):
+    # The fewest window bits whose two window buffers (and window ids) fit.
+    for K, budget in [(31, 100 << 30), (31, 60 << 30), (31, 30 << 30), (32, 120 << 30), (32, 60 << 30),
+                      (20, 1 << 40)]:
+        c = vx.vx_plot_tiled_window_bits(K, budget)
+        assert vx.vx_plot_tiled_bytes(K, c)[0] <= budget, (K, budget, c)
+        for smaller in range(c):
+            assert vx.vx_plot_tiled_bytes(K, smaller)[0] > budget, (K, budget, smaller)
+    assert vx.vx_plot_tiled_window_bits(31, 1 << 40) == 0        # the whole plot fits
+    assert vx.vx_plot_tiled_window_bits(31, 60 << 30) == 2       # two quarter-plot windows + ids
+    with pytest.raises(vx.VxError) as ei:                        # no window count fits 1 MB
+        vx.vx_plot_tiled_window_bits(31, 1 << 20)
+    assert ei.value.code == vx.VX_ENOMEM
