@@ -328,8 +328,11 @@ int vx_plot_tiled_window_bits(int K, const vx_opts *opts, uint64_t budget_bytes,
  * NULL) get the record counts.  Returns VX_OK; VX_ENOMEM if Table 2 did not
  * fit host_t2_bytes (*t2_count is then the size needed; Table 1 is
  * complete) or a window buffer could not be allocated; a window's
- * VX_EOVERFLOW / VX_ETIMEDOUT stops the plot.  Synchronous.  The paper
- * names the direction; the window scheme is this library's. */
+ * VX_EOVERFLOW / VX_ETIMEDOUT stops the plot; VX_EINVAL for window bits the
+ * planner rejects, opts that already name a window, a d_work shorter than
+ * device_bytes or not 256-byte aligned, or a host_t1 shorter than 12 * 2^K.
+ * Synchronous.  The paper names the direction; the window scheme is this
+ * library's. */
 int vx_plot_tiled(int K, const uint8_t key[32], const vx_opts *opts, int window_bits,
                   void *d_work, uint64_t work_bytes, void *host_t1, uint64_t host_t1_bytes,
                   void *host_t2, uint64_t host_t2_bytes, uint64_t *t1_count, uint64_t *t2_count,
