@@ -482,9 +482,12 @@ def vx_serve_destroy(srv):
 class Plot:
     """One plot with torch-allocated device buffers bound to it.
 
-    ``Plot(K, key).run()`` issues vx_table1 + vx_match on the current torch
-    stream; ``sync()`` waits and returns the Table-2 count; ``t1`` / ``t2``
-    are zero-copy uint8 views shaped (records, 12) / (records, 16).
+    ``Plot(K, key).run()`` issues the fused plot (``run_split()``: vx_table1
+    + vx_match) on the current torch stream; ``sync()`` waits and returns the
+    Table-2 count; ``t1`` / ``t2`` are zero-copy uint8 views shaped
+    (records, 12) / (records, 16).  With ``vx_opts.window_bits`` the plot is
+    one window of the whole plot, and ``t1`` holds the window's records
+    (their count is known after ``sync()``).
     """
 
     def __init__(self, K: int, key: bytes, opts: vx_opts | None = None, device=None):
