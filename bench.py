@@ -258,13 +258,14 @@ def main():
     ap.add_argument("--e2e-copy-streams", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="plain",
-                    choices=["plain", "batch", "large", "serve", "write", "sort2", "tiled"],
+                    choices=["plain", "batch", "large", "serve", "write", "sort2", "tiled", "plotfile"],
                     help="plain: the K=31 headline; batch: 64 mixed-K plots batched vs plain; "
                          "large: 4 x K=29 + 8 x K=27 batched vs plain; serve: Poisson requests "
                          "through the continuous-batching server vs one at a time; write: plots "
                          "written to flat Table-2 files, serial vs overlapped with the next plot; "
                          "sort2: Table 2 of a K plot sorted by hash2; tiled: a K plot built "
-                         "window by window into pinned host memory vs the whole plot and its copy")
+                         "window by window into pinned host memory vs the whole plot and its copy; "
+                         "plotfile: one K plot file end to end (plot, write, fsync), whole and tiled")
     ap.add_argument("--partition-log2", type=int, default=0)
     ap.add_argument("--scatter-mode", type=int, default=0)
     ap.add_argument("--fuse-pair-hash", type=int, default=0)
@@ -975,6 +976,74 @@ def run_tiled_file(vx, args):
             "timing": "wall clock around each synchronous call, median of steps", "data": "synthetic"}
 
 
+def run_plotfile(vx, args):
+    """One K plot file end to end, as the paper's totals count it (plot +
+    write): a warm whole plot (vaultx.Plot), vx_plot_write and an fsync of
+    the file; then the same file from vx_plot_tiled_write (window bits
+    --window-bits, window buffers preallocated) and an fsync.  Skipped unless
+    the directory has 2.5x the file free; the file is deleted after each
+    leg."""
+    import shutil
+    import tempfile
+    import torch
+    from paper_2606_14007_gb300.inputs import plot_key
+    K, c = args.K, args.window_bits
+    base = args.tiled_file or tempfile.gettempdir()
+    os.makedirs(base, exist_ok=True)
+    st = os.statvfs(base)
+    free = st.f_bavail * st.f_frsize
+    need = 2.5 * 16 * (1 << K)
+    out = {"mode": "plotfile", "metric": "plot file end to end, seconds", "unit": "s", "K": K,
+           "higher_is_better": False, "dir_free_gb": round(free / 1e9, 1), "data": "synthetic"}
+    if free < need:
+        out["skipped"] = "less than %.0f GB free in %s" % (need / 1e9, base)
+        return out
+    d = tempfile.mkdtemp(prefix="vx_plotfile_", dir=base)
+    path = os.path.join(d, "plot%d.bin" % K)
+
+    def fsync(p_):
+        fd = os.open(p_, os.O_RDONLY)
+        os.fsync(fd)
+        os.close(fd)
+
+    try:
+        p = vx.Plot(K, plot_key(K))
+        p.run()
+        p.sync()                          # warm-up, not timed
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p.run()
+        n2 = p.sync()
+        t1 = time.perf_counter()
+        vx.vx_plot_write(p.handle, path)
+        t2 = time.perf_counter()
+        fsync(path)
+        t3 = time.perf_counter()
+        size = os.path.getsize(path)
+        p.close()
+        del p
+        torch.cuda.empty_cache()
+        os.remove(path)
+        out["whole"] = {"plot_s": t1 - t0, "write_s": t2 - t1, "fsync_s": t3 - t2, "total_s": t3 - t0,
+                        "file_bytes": size, "write_GBps": size / (t2 - t1) / 1e9,
+                        "device_bytes": sum(vx.vx_plot_required_bytes(K))}
+        dev, _, _ = vx.vx_plot_tiled_bytes(K, c)
+        work = torch.empty(dev, dtype=torch.uint8, device="cuda")
+        t0 = time.perf_counter()
+        _, _, m2, _ = vx.vx_plot_tiled_write(K, plot_key(K), c, path, d_work=work.data_ptr(),
+                                             work_bytes=work.numel())
+        t1 = time.perf_counter()
+        fsync(path)
+        t2 = time.perf_counter()
+        out["tiled"] = {"window_bits": c, "device_bytes": dev, "write_call_s": t1 - t0,
+                        "fsync_s": t2 - t1, "total_s": t2 - t0, "file_bytes": os.path.getsize(path),
+                        "same_size": os.path.getsize(path) == size and m2 == n2}
+        out["value"] = out["whole"]["total_s"]
+    finally:
+        shutil.rmtree(d, ignore_errors=True)
+    return out
+
+
 def run_mode(args):
     import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -997,6 +1066,8 @@ def run_mode(args):
         out = run_sort2(vx, args)
     elif args.mode == "tiled":
         out = run_tiled_file(vx, args) if args.tiled_file else run_tiled(vx, args)
+    elif args.mode == "plotfile":
+        out = run_plotfile(vx, args)
     else:
         out = run_serve(vx, args)
     if int(os.environ.get("RANK", "0")) == 0:
