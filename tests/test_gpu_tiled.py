@@ -17,6 +17,7 @@ pytestmark = pytest.mark.gpu
 
 from oracle import oracle as orc  # noqa: E402
 from paper_2606_14007_gb300.inputs import plot_key  # noqa: E402
+from window_slices import oracle_windows  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -32,22 +33,6 @@ def oracle_tables(K, key, D=None):
     r1 = orc.table1(K, key)
     r2 = orc.match(key, r1, orc.default_distance(K) if D is None else D)
     return r1, r2
-
-
-def window_of_t1(r1, c):
-    key64 = np.ascontiguousarray(r1[:, 4:12]).view(">u8").ravel().astype(np.uint64)
-    return (key64 >> np.uint64(64 - c)).astype(np.int64), key64
-
-
-def oracle_windows(r1, r2, c):
-    """[(Table-1 slice, Table-2 slice, first bucket-offset)] of the 2^c windows."""
-    w1, key64 = window_of_t1(r1, c)
-    nonce = np.ascontiguousarray(r1[:, :4]).view("<u4").ravel()
-    key_of = np.empty(r1.shape[0], dtype=np.uint64)
-    key_of[nonce] = key64
-    a = np.ascontiguousarray(r2[:, :4]).view("<u4").ravel()
-    w2 = (key_of[a] >> np.uint64(64 - c)).astype(np.int64)
-    return [(r1[w1 == w], r2[w2 == w]) for w in range(1 << c)]
 
 
 STAGED = dict(scatter_mode=1)

@@ -353,3 +353,27 @@ def test_sort_table2_is_an_ordered_permutation():
     # key2 is the big-endian reading of the hash bytes the record carries
     r = s[len(s) // 2]
     assert int(orc.table2_key(s[len(s) // 2: len(s) // 2 + 1])[0]) == int.from_bytes(r[8:].tobytes(), "big")
+
+
+def test_window_slices_partition_the_plot():
+    # The expected tables of window plots (tests/window_slices.py) partition
+    # the whole plot's tables in order: concatenated over the windows they
+    # are Table 1 and Table 2; every record of slice w has key64's top c bits
+    # == w, and both records of every pair of slice w lie in window w.
+    from window_slices import oracle_windows, window_of_t1
+    K, key = 14, plot_key(321)
+    r1 = orc.table1(K, key)
+    r2 = orc.match(key, r1, orc.default_distance(K))
+    for c in (1, 2, 3, 5):
+        sl = oracle_windows(r1, r2, c)
+        assert np.array_equal(np.concatenate([s1 for s1, _ in sl]), r1)
+        assert np.array_equal(np.concatenate([s2 for _, s2 in sl]), r2)
+        win_of_nonce = {}
+        for w, (s1, _) in enumerate(sl):
+            ws, _ = window_of_t1(s1, c)
+            assert (ws == w).all()
+            for n in np.ascontiguousarray(s1[:, :4]).view("<u4").ravel():
+                win_of_nonce[int(n)] = w
+        for w, (_, s2) in enumerate(sl):
+            ab = np.ascontiguousarray(s2[:, :8]).view("<u4")
+            assert all(win_of_nonce[int(a)] == w and win_of_nonce[int(b)] == w for a, b in ab)
