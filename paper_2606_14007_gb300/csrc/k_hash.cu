@@ -1,5 +1,7 @@
 // k_hash.cu -- key setup, Table-1 hashing fused with the first bucketing
-// scatter, and the stand-alone hash / pair-hash kernels.
+// scatter (also for one window of a plot: filtering every nonce's key, or
+// hashing the window's listed nonces), the window-id and window-list passes
+// of tiled plots, and the stand-alone hash / pair-hash kernels.
 //
 // Paper: Sec. III-A/III-B (one keyed BLAKE3 per nonce, little-endian nonce,
 // bucket index from the hash prefix).  The paper's kernel claims one bucket
