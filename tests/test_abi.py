@@ -272,3 +272,32 @@ def test_tiled_window_bits_fit_a_budget(vx):
     with pytest.raises(vx.VxError) as ei:                        # no window count fits 1 MB
         vx.vx_plot_tiled_window_bits(31, 1 << 20)
     assert ei.value.code == vx.VX_ENOMEM
+
+
+def test_window_planner_sweep(vx):
+    # Every K and every window count the planner accepts: a window's buffers
+    # hold its share of the tables (Table 1 at least 12 B per expected record,
+    # Table 2 at least 16 B per expected pair and, for a window, its nonce
+    # list of 4 B per expected record), and from 2 window bits on each extra
+    # bit shrinks the tiled footprint.  Anything else is VX_EINVAL.
+    for K in range(1, 33):
+        p = max(0, min(21, K - 11))
+        prev = None
+        for c in range(0, min(p, 16) + 2):
+            try:
+                t1, t2, sc = vx.vx_plot_required_bytes(K, vx.make_opts(window_bits=c, window=0))
+            except vx.VxError as e:
+                assert e.code == vx.VX_EINVAL and c > min(p, 16), (K, c)
+                continue
+            assert c <= min(p, 16)
+            recs = 2 ** K / 2 ** c
+            lam = 2 ** K / 2 ** 24
+            u = min(1.0, 2.0 ** (64 - K) / 2 ** 40)
+            pairs = 2 ** 24 * lam * lam / 2 * (2 * u - u * u) / 2 ** c
+            assert t1 >= 12 * recs and t2 >= 16 * pairs, (K, c, t1, t2)
+            if c:
+                assert t2 >= 4 * recs, (K, c, t2)  # the window's nonce list
+            dev = vx.vx_plot_tiled_bytes(K, c)[0]
+            if prev is not None and c >= 3:
+                assert dev < prev, (K, c, dev, prev)
+            prev = dev
