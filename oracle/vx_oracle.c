@@ -26,9 +26,10 @@
  * specification (messages of at most 64 bytes), which is all the plotter
  * needs.  Pinning status: the G function, the round's column/diagonal
  * pattern and the IV are pinned against hashlib's BLAKE2s, which shares
- * them; the BLAKE3 message permutation, the domain flags and the
- * output fold are parity unpinned (no BLAKE3 test vectors or independent
- * BLAKE3 implementation are reachable from this build).
+ * them; the whole compression (message permutation, counter, block-length
+ * and flag words, output fold) reproduces the published BLAKE3 digests of
+ * the empty input and of "abc"; the keyed mode is that compression with the
+ * key as chaining value and the KEYED_HASH flag (tests/test_oracle_pins.py).
  */
 #include <stdint.h>
 #include <stdlib.h>

@@ -3,6 +3,11 @@
 * BLAKE3's G function, round pattern and IV are the ones BLAKE2s uses
   (BLAKE3 spec Sec. 2.2; RFC 7693 Sec. 3.1-3.2).  BLAKE2s assembled from the
   oracle's own round function and IV must reproduce hashlib.blake2s.
+* The whole BLAKE3 compression (message permutation, counter / block-length
+  / flag words, seven-round schedule, output fold) must reproduce the
+  published BLAKE3 digests of the empty input and of "abc"
+  (tests/golden/blake3_vectors.json).  The keyed mode is that compression
+  with the key as chaining value and the KEYED_HASH flag.
 * Table 1 order (R5, R6) must equal numpy's lexsort of the big-endian key64
   and nonce; bucket offsets must equal numpy's bincount + cumsum.
 * The match (R8, R9, R11) must equal an O(n^2) numpy scan, satisfy
@@ -72,6 +77,42 @@ def test_round_and_iv_reproduce_blake2s(seed):
         assert _blake2s_from_oracle(msg) == hashlib.blake2s(msg).digest()
         key = rng.integers(0, 256, 32, dtype=np.uint8).tobytes()
         assert _blake2s_from_oracle(msg, key) == hashlib.blake2s(msg, key=key).digest()
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("case", _golden("blake3_vectors.json")["hash"],
+                         ids=lambda c: repr(c["input_ascii"]))
+def test_compress_reproduces_published_blake3_digests(case):
+    # One-chunk, one-block BLAKE3 hash (spec Sec. 2.2-2.4): chaining value =
+    # IV, counter 0, block_len = message length, flags CHUNK_START | CHUNK_END
+    # | ROOT; the digest is output words 0..7, little-endian.  The empty input
+    # pins block_len 0, "abc" block_len 3 and a nonzero message word.
+    fl = _golden("blake3_vectors.json")["flags"]
+    msg = case["input_ascii"].encode()
+    block = np.frombuffer(msg.ljust(64, b"\0"), dtype="<u4").astype(np.uint32)
+    out = orc.compress(orc.iv(), block, 0, len(msg),
+                       fl["CHUNK_START"] | fl["CHUNK_END"] | fl["ROOT"])
+    assert out[:8].astype("<u4").tobytes().hex() == case["digest"]
+
+
+@pytest.mark.parametrize("n", [0, 1, 4, 8, 33, 64])
+def test_keyed_hash_is_compress_with_key_and_keyed_flag(n):
+    # keyed_hash (spec Sec. 2.3): the key's eight LE words are the chaining
+    # value and every block carries KEYED_HASH; one chunk of one block for
+    # messages of at most 64 bytes.
+    fl = _golden("blake3_vectors.json")["flags"]
+    rng = np.random.default_rng(100 + n)
+    key = rng.integers(0, 256, 32, dtype=np.uint8).tobytes()
+    msg = rng.integers(0, 256, n, dtype=np.uint8).tobytes()
+    cv = np.frombuffer(key, dtype="<u4").astype(np.uint32)
+    block = np.frombuffer(msg.ljust(64, b"\0"), dtype="<u4").astype(np.uint32)
+    out = orc.compress(cv, block, 0, n,
+                       fl["CHUNK_START"] | fl["CHUNK_END"] | fl["ROOT"] | fl["KEYED_HASH"])
+    assert orc.keyed_hash(key, msg, 32) == out[:8].astype("<u4").tobytes()
 
 
 def test_keyed_hash_shapes():
