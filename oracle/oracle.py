@@ -84,6 +84,8 @@ def lib():
             L.orc_match_global_bruteforce.argtypes = [u8p, ctypes.c_uint64, ctypes.c_uint64, u32p,
                                                       ctypes.c_uint64]
             L.orc_match_global_bruteforce.restype = ctypes.c_int64
+            L.orc_pair_hash_mt.argtypes = [u8p, u8p, ctypes.c_uint64, ctypes.c_size_t, u8p,
+                                           ctypes.c_int]
             _lib = L
     return _lib
 
@@ -201,6 +203,48 @@ def match(key: bytes, t1: np.ndarray, D: int) -> np.ndarray:
                           t1.shape[0], D, _p(out, ctypes.c_uint8), n)
     assert got == n
     return out
+
+
+def match_unhashed(t1: np.ndarray, D: int) -> np.ndarray:
+    """Table 2 without its hashes: the {a, b} pairs of :func:`match` in the
+    same order, hash2 bytes zero (fill them with :func:`pair_hash`)."""
+    t1 = np.ascontiguousarray(t1, dtype=np.uint8)
+    L = lib()
+    tp = _p(t1, ctypes.c_uint8)
+    n = int(L.orc_match(None, tp, t1.shape[0], D, None, 0))
+    out = np.zeros((n, T2_BYTES), dtype=np.uint8)
+    got = L.orc_match(None, tp, t1.shape[0], D, _p(out, ctypes.c_uint8), n)
+    assert got == n
+    return out
+
+
+def pair_hash(key: bytes, recs: np.ndarray, threads: int = 1) -> np.ndarray:
+    """hash2 (R10) of every row of recs (rows of 8 or more bytes: LE32 a,
+    LE32 b, ...), shape (rows, 8) uint8, hashed on `threads` threads."""
+    recs = np.ascontiguousarray(recs, dtype=np.uint8)
+    if recs.ndim != 2 or recs.shape[1] < 8:
+        raise ValueError("pair rows must hold at least 8 bytes")
+    out = np.zeros((recs.shape[0], 8), dtype=np.uint8)
+    lib().orc_pair_hash_mt(_p(_key_arr(key), ctypes.c_uint8), _p(recs, ctypes.c_uint8),
+                           recs.shape[0], recs.shape[1], _p(out, ctypes.c_uint8), threads)
+    return out
+
+
+def table1_mt(K: int, key: bytes, threads: int) -> np.ndarray:
+    """The sorted Table 1 of :func:`table1` for larger K: the records hashed
+    in nonce order on `threads` threads, then numpy's stable sort on key64
+    as the sorting step (stable, so equal key64 keep nonce order: R6)."""
+    recs = hash_range(key, 0, 1 << K, threads)
+    order = np.argsort(key64(recs), kind="stable")
+    return recs[order]
+
+
+def plot_mt(K: int, key: bytes, threads: int, D: int | None = None):
+    """(Table 1, Table 2) of :func:`plot`, with hashing on `threads` threads."""
+    t1 = table1_mt(K, key, threads)
+    t2 = match_unhashed(t1, default_distance(K) if D is None else D)
+    t2[:, 8:] = pair_hash(key, t2, threads)
+    return t1, t2
 
 
 def match_bruteforce(recs_unsorted: np.ndarray, D: int) -> np.ndarray:

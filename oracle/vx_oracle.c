@@ -277,7 +277,9 @@ uint64_t orc_default_distance(int K)
 /* Walks Table 1 bucket by bucket; inside a bucket, for each record i scans
  * j = i+1, i+2, ... while j is in the same bucket and key64_j - key64_i < D
  * (R8, R9), emitting {a, b, hash2} in that order (R10, R11).  Returns the
- * number of pairs; only the first `cap` are written (t2 may be NULL). */
+ * number of pairs; only the first `cap` are written (t2 may be NULL).
+ * With key NULL the hash2 bytes are left as they are, for a caller that
+ * hashes the pairs afterwards with orc_pair_hash_mt. */
 int64_t orc_match(const uint8_t key[32], const uint8_t *t1, uint64_t n, uint64_t D,
                   uint8_t *t2, uint64_t cap)
 {
@@ -298,7 +300,7 @@ int64_t orc_match(const uint8_t key[32], const uint8_t *t1, uint64_t n, uint64_t
                     memcpy(msg, t1 + 12 * x, 4);
                     memcpy(msg + 4, t1 + 12 * y, 4);
                     memcpy(out, msg, 8);
-                    orc_keyed_hash(key, msg, 8, out + 8, 8);
+                    if (key) orc_keyed_hash(key, msg, 8, out + 8, 8);
                 }
                 count++;
             }
@@ -392,6 +394,49 @@ int64_t orc_match_global_bruteforce(const uint8_t *recs, uint64_t n, uint64_t D,
         }
     }
     return (int64_t)count;
+}
+
+/* hash2 of a list of pairs (R10): for record i of `recs` (stride bytes
+ * apart, LE32 a at byte 0 and LE32 b at byte 4), out[8 i .. 8 i + 7] = the
+ * first 8 bytes of BLAKE3-keyed(key, LE32(a) || LE32(b)).  The list is cut
+ * into nthreads contiguous ranges, one POSIX thread each. */
+struct pair_job {
+    const uint8_t *key, *recs;
+    size_t stride;
+    uint8_t *out;
+    uint64_t lo, hi;
+};
+
+static void *pair_job_run(void *arg)
+{
+    struct pair_job *j = (struct pair_job *)arg;
+    for (uint64_t i = j->lo; i < j->hi; i++)
+        orc_keyed_hash(j->key, j->recs + j->stride * i, 8, j->out + 8 * i, 8);
+    return NULL;
+}
+
+int orc_pair_hash_mt(const uint8_t key[32], const uint8_t *recs, uint64_t n, size_t stride,
+                     uint8_t *out, int nthreads)
+{
+    if (stride < 8) return -1;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 512) nthreads = 512;
+    pthread_t tid[512];
+    int started[512];
+    struct pair_job jobs[512];
+    for (int t = 0; t < nthreads; t++) {
+        jobs[t].key = key;
+        jobs[t].recs = recs;
+        jobs[t].stride = stride;
+        jobs[t].out = out;
+        jobs[t].lo = n * (uint64_t)t / (uint64_t)nthreads;
+        jobs[t].hi = n * (uint64_t)(t + 1) / (uint64_t)nthreads;
+        started[t] = pthread_create(&tid[t], NULL, pair_job_run, &jobs[t]) == 0;
+        if (!started[t]) pair_job_run(&jobs[t]);
+    }
+    for (int t = 0; t < nthreads; t++)
+        if (started[t]) pthread_join(tid[t], NULL);
+    return 0;
 }
 
 int orc_abi_version(void) { return 1; }

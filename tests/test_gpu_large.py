@@ -1,17 +1,29 @@
-"""Full-size plots (K=27 and K=31, the configuration bench.py times), checked
-through properties that hold at any size, computed on the device with torch
-independently of the kernels, plus sampled recomputation by the oracle:
+"""Full-size plots over K = 23 ... 32, compared with the oracle.
+
+K = 23 ... 27: both tables element by element against the oracle's
+(hashes on every host core, numpy's stable sort as the sorting step, the
+oracle's match, the oracle's pair hash on every host core).
+
+K = 27 ... 31 (K=31 is the configuration bench.py times): properties that
+hold at any size, computed on the device with torch independently of the
+kernels, plus every record's hash and every pair's hash2 recomputed by the
+oracle.  Together these fix both tables bit for bit:
 
 Table 1: strictly increasing in (key64, nonce); every nonce exactly once;
-sampled records' hash bytes equal the oracle's keyed hash.
+every record's hash bytes equal the oracle's keyed hash of its nonce.  The
+oracle's Table 1 is the unique (key64, nonce)-sorted list of those records.
 Table 2: every entry (a, b) has pos(a) < pos(b) in Table 1, the same logical
 bucket (bucket scope) and key64_b - key64_a < D; entries strictly increasing
 in (pos(a), pos(b)); their number equals an independent count of qualifying
-pairs; sampled hash2 equal the oracle's; the count is within the closed-form
-expectation 2^24 (lambda - 1/2), or C(N,2) 2D / 2^64 for the cross-bucket
-match.
+pairs; every hash2 equals the oracle's.  The oracle's Table 2 is the unique
+(i, j)-ordered list of all qualifying pairs, so the two are equal.  The
+count is also checked against the closed-form expectation 2^24 (lambda -
+1/2), or C(N,2) 2D / 2^64 for the cross-bucket match.
+
+K = 32 (beyond the paper's range) keeps the sampled recomputation.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -23,6 +35,7 @@ from oracle import oracle as orc  # noqa: E402
 from paper_2606_14007_gb300.inputs import plot_key  # noqa: E402
 
 CHUNK = 1 << 27
+THREADS = os.cpu_count() or 1
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +54,7 @@ def fields(t1_rows):
     return nonce, hi, lo
 
 
-def check_plot(vx, K, seed, scope=0, **kw):
+def check_plot(vx, K, seed, scope=0, every_hash=True, **kw):
     # scope 1: the cross-bucket match (no same-bucket condition; E|T2| ~ N)
     key = plot_key(seed)
     N = 1 << K
@@ -49,7 +62,7 @@ def check_plot(vx, K, seed, scope=0, **kw):
     p.run()
     n2 = p.sync()
     t1 = p.t1
-    check_tables(K, key, seed, t1, p.t2, n2, scope)
+    check_tables(K, key, seed, t1, p.t2, n2, scope, every_hash=every_hash)
     # first and last records of Table 1 and Table 2, and the bucket offsets
     off = p.offsets()
     assert int(off[0]) == 0 and int(off[-1]) == N
@@ -59,9 +72,35 @@ def check_plot(vx, K, seed, scope=0, **kw):
     torch.cuda.empty_cache()
 
 
-def check_tables(K, key, seed, t1, t2, n2, scope=0):
+def first_diff(got, ref):
+    bad = np.nonzero((got != ref).any(axis=1))[0]
+    return int(bad[0]) if bad.size else -1
+
+
+def check_every_hash(key, t1, t2, n2, pos):
+    """Every Table-1 record's hash bytes against the oracle's keyed hash of
+    its nonce (records found through pos, nonce -> Table-1 position), and
+    every Table-2 record's hash2 against the oracle's pair hash of its
+    (a, b); the oracle runs on every host core, chunk by chunk."""
+    N = t1.shape[0]
+    for s in range(0, N, CHUNK):
+        e = min(N, s + CHUNK)
+        ref = orc.hash_range(key, s, e, THREADS)[:, 4:]
+        got = t1[pos[s:e].long(), 4:].cpu().numpy()
+        d = first_diff(got, ref)
+        assert d < 0, "Table-1 hash of nonce %d differs from the oracle" % (s + d)
+    for s in range(0, n2, CHUNK):
+        e = min(n2, s + CHUNK)
+        rows = t2[s:e].cpu().numpy()
+        ref = orc.pair_hash(key, rows, THREADS)
+        d = first_diff(rows[:, 8:], ref)
+        assert d < 0, "Table-2 hash2 of record %d differs from the oracle" % (s + d)
+
+
+def check_tables(K, key, seed, t1, t2, n2, scope=0, every_hash=True):
     """The properties of a whole plot's tables t1 (2^K x 12) and t2 (n2 x 16),
-    uint8 tensors on the device."""
+    uint8 tensors on the device; with every_hash, every hash recomputed by
+    the oracle, else 3000 sampled records and pairs."""
     N = 1 << K
     D = 1 << (64 - K)
     assert t1.shape[0] == N and t2.shape[0] == n2
@@ -130,24 +169,45 @@ def check_tables(K, key, seed, t1, t2, n2, scope=0):
         order = (i[1:] > i[:-1]) | ((i[1:] == i[:-1]) & (j[1:] > j[:-1]))
         assert bool(order.all()), "Table 2 out of (i, j) order"
         last = (i[-1:], j[-1:])
-    # sampled oracle recomputation
-    rng = np.random.default_rng(seed)
-    rows = torch.from_numpy(rng.integers(0, N, 3000)).to(dev)
-    t1s = t1[rows].cpu().numpy()
-    for r in t1s:
-        assert r[4:].tobytes() == orc.keyed_hash(key, r[:4].tobytes(), 8)
-    rows = torch.from_numpy(rng.integers(0, n2, 3000)).to(dev)
-    for r in t2[rows].cpu().numpy():
-        assert r[8:].tobytes() == orc.keyed_hash(key, r[:8].tobytes(), 8)
+    if every_hash:
+        check_every_hash(key, t1, t2, n2, pos)
+    else:
+        rng = np.random.default_rng(seed)
+        rows = torch.from_numpy(rng.integers(0, N, 3000)).to(dev)
+        for r in t1[rows].cpu().numpy():
+            assert r[4:].tobytes() == orc.keyed_hash(key, r[:4].tobytes(), 8)
+        rows = torch.from_numpy(rng.integers(0, n2, 3000)).to(dev)
+        for r in t2[rows].cpu().numpy():
+            assert r[8:].tobytes() == orc.keyed_hash(key, r[:8].tobytes(), 8)
     del counts, pos
 
 
-def test_plot_k27_properties(vx):
-    check_plot(vx, 27, 27)
+@pytest.mark.parametrize("K", [23, 24, 25, 26, 27])
+def test_plot_equals_oracle_elementwise(vx, K):
+    # The small-K parity test's comparison at K = 23 ... 27 (key from seed K,
+    # as bench.py's plots): whole tables and the bucket offsets.
+    key = plot_key(K)
+    p = vx.Plot(K, key)
+    p.run()
+    n2 = p.sync()
+    g1 = p.t1.cpu().numpy()
+    g2 = p.t2.cpu().numpy()
+    off = p.offsets().cpu().numpy()
+    p.close()
+    torch.cuda.empty_cache()
+    r1, r2 = orc.plot_mt(K, key, THREADS)
+    assert g1.shape == r1.shape
+    d = first_diff(g1, r1)
+    assert d < 0, "Table 1 differs from the oracle at record %d" % d
+    assert n2 == r2.shape[0], (n2, r2.shape[0])
+    d = first_diff(g2, r2)
+    assert d < 0, "Table 2 differs from the oracle at record %d" % d
+    assert np.array_equal(off.astype(np.uint64), orc.bucket_offsets(r1))
 
 
-def test_plot_k31_properties(vx):
-    check_plot(vx, 31, 31)
+@pytest.mark.parametrize("K", [27, 28, 29, 30, 31])
+def test_plot_bit_exact_by_properties(vx, K):
+    check_plot(vx, K, K)
 
 
 def test_plot_k27_cross_bucket_properties(vx):

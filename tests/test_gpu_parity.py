@@ -348,6 +348,9 @@ def test_plot_write_file(vx, tmp_path):
     path = str(tmp_path / "plot.bin")
     d2h, total = vx.vx_plot_write(p.handle, path)
     data = np.fromfile(path, dtype=np.uint8).reshape(-1, 16)
+    # The file is Table 2 in its order, no header (R12): the oracle's table.
+    _, r2 = oracle_plot(K, key)
+    assert np.array_equal(data, r2)
     assert np.array_equal(data, p.t2.cpu().numpy())
     assert total >= d2h >= 0
     p.close()

@@ -418,3 +418,28 @@ def test_window_slices_partition_the_plot():
         for w, (_, s2) in enumerate(sl):
             ab = np.ascontiguousarray(s2[:, :8]).view("<u4")
             assert all(win_of_nonce[int(a)] == w and win_of_nonce[int(b)] == w for a, b in ab)
+
+
+@pytest.mark.parametrize("K,seed", [(1, 7), (9, 8), (15, 9)])
+def test_multithreaded_plot_equals_plain_plot(K, seed):
+    # plot_mt (hashing on several threads, numpy's stable sort, the match
+    # without hashes, then the pair hash on several threads) is the plain
+    # single-threaded oracle rearranged: the same tables byte for byte.
+    key = plot_key(seed)
+    t1, t2 = orc.plot(K, key)
+    for threads in (1, 3, 8):
+        m1, m2 = orc.plot_mt(K, key, threads)
+        assert np.array_equal(m1, t1) and np.array_equal(m2, t2)
+
+
+def test_pair_hash_rows():
+    key = plot_key(11)
+    rng = np.random.default_rng(11)
+    rows = rng.integers(0, 256, (257, 16), dtype=np.uint8)
+    for threads in (1, 4):
+        h = orc.pair_hash(key, rows, threads)
+        for i in range(rows.shape[0]):
+            assert h[i].tobytes() == orc.keyed_hash(key, rows[i, :8].tobytes(), 8)
+    assert orc.pair_hash(key, rows[:, :8], 2).tobytes() == orc.pair_hash(key, rows, 1).tobytes()
+    with pytest.raises(ValueError):
+        orc.pair_hash(key, rows[:, :7])
