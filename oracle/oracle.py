@@ -86,6 +86,9 @@ def lib():
             L.orc_match_global_bruteforce.restype = ctypes.c_int64
             L.orc_pair_hash_mt.argtypes = [u8p, u8p, ctypes.c_uint64, ctypes.c_size_t, u8p,
                                            ctypes.c_int]
+            L.orc_table1_mt.argtypes = [ctypes.c_int, u8p, u8p, u8p, ctypes.c_int]
+            L.orc_match_mt.argtypes = [u8p, u8p, ctypes.c_uint64, ctypes.c_uint64, u8p, ctypes.c_int]
+            L.orc_match_mt.restype = ctypes.c_int64
             _lib = L
     return _lib
 
@@ -205,19 +208,6 @@ def match(key: bytes, t1: np.ndarray, D: int) -> np.ndarray:
     return out
 
 
-def match_unhashed(t1: np.ndarray, D: int) -> np.ndarray:
-    """Table 2 without its hashes: the {a, b} pairs of :func:`match` in the
-    same order, hash2 bytes zero (fill them with :func:`pair_hash`)."""
-    t1 = np.ascontiguousarray(t1, dtype=np.uint8)
-    L = lib()
-    tp = _p(t1, ctypes.c_uint8)
-    n = int(L.orc_match(None, tp, t1.shape[0], D, None, 0))
-    out = np.zeros((n, T2_BYTES), dtype=np.uint8)
-    got = L.orc_match(None, tp, t1.shape[0], D, _p(out, ctypes.c_uint8), n)
-    assert got == n
-    return out
-
-
 def pair_hash(key: bytes, recs: np.ndarray, threads: int = 1) -> np.ndarray:
     """hash2 (R10) of every row of recs (rows of 8 or more bytes: LE32 a,
     LE32 b, ...), shape (rows, 8) uint8, hashed on `threads` threads."""
@@ -230,20 +220,37 @@ def pair_hash(key: bytes, recs: np.ndarray, threads: int = 1) -> np.ndarray:
     return out
 
 
-def table1_mt(K: int, key: bytes, threads: int) -> np.ndarray:
-    """The sorted Table 1 of :func:`table1` for larger K: the records hashed
-    in nonce order on `threads` threads, then numpy's stable sort on key64
-    as the sorting step (stable, so equal key64 keep nonce order: R6)."""
-    recs = hash_range(key, 0, 1 << K, threads)
-    order = np.argsort(key64(recs), kind="stable")
-    return recs[order]
+def table1_allcores(K: int, key: bytes, threads: int) -> np.ndarray:
+    """The sorted Table 1 with every step on `threads` threads: hashing, a
+    grouping pass by the top key byte, and qsort of each group."""
+    n = 1 << K
+    out = np.empty((n, REC_BYTES), dtype=np.uint8)
+    scratch = np.empty((n, REC_BYTES), dtype=np.uint8)
+    rc = lib().orc_table1_mt(K, _p(_key_arr(key), ctypes.c_uint8), _p(out, ctypes.c_uint8),
+                             _p(scratch, ctypes.c_uint8), threads)
+    if rc:
+        raise ValueError("bad K")
+    return out
 
 
-def plot_mt(K: int, key: bytes, threads: int, D: int | None = None):
-    """(Table 1, Table 2) of :func:`plot`, with hashing on `threads` threads."""
-    t1 = table1_mt(K, key, threads)
-    t2 = match_unhashed(t1, default_distance(K) if D is None else D)
-    t2[:, 8:] = pair_hash(key, t2, threads)
+def match_allcores(key: bytes, t1: np.ndarray, D: int, threads: int) -> np.ndarray:
+    """Table 2 of :func:`match`, Table 1 cut into runs of whole buckets, one
+    per thread."""
+    t1 = np.ascontiguousarray(t1, dtype=np.uint8)
+    L = lib()
+    kp, tp = _p(_key_arr(key), ctypes.c_uint8), _p(t1, ctypes.c_uint8)
+    n = int(L.orc_match_mt(kp, tp, t1.shape[0], D, None, threads))
+    out = np.empty((n, T2_BYTES), dtype=np.uint8)
+    got = L.orc_match_mt(kp, tp, t1.shape[0], D, _p(out, ctypes.c_uint8), threads)
+    assert got == n
+    return out
+
+
+def plot_allcores(K: int, key: bytes, threads: int, D: int | None = None):
+    """(Table 1, Table 2) of :func:`plot` with every stage on `threads`
+    threads (the all-core CPU baseline)."""
+    t1 = table1_allcores(K, key, threads)
+    t2 = match_allcores(key, t1, default_distance(K) if D is None else D, threads)
     return t1, t2
 
 

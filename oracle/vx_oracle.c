@@ -277,9 +277,7 @@ uint64_t orc_default_distance(int K)
 /* Walks Table 1 bucket by bucket; inside a bucket, for each record i scans
  * j = i+1, i+2, ... while j is in the same bucket and key64_j - key64_i < D
  * (R8, R9), emitting {a, b, hash2} in that order (R10, R11).  Returns the
- * number of pairs; only the first `cap` are written (t2 may be NULL).
- * With key NULL the hash2 bytes are left as they are, for a caller that
- * hashes the pairs afterwards with orc_pair_hash_mt. */
+ * number of pairs; only the first `cap` are written (t2 may be NULL). */
 int64_t orc_match(const uint8_t key[32], const uint8_t *t1, uint64_t n, uint64_t D,
                   uint8_t *t2, uint64_t cap)
 {
@@ -300,7 +298,7 @@ int64_t orc_match(const uint8_t key[32], const uint8_t *t1, uint64_t n, uint64_t
                     memcpy(msg, t1 + 12 * x, 4);
                     memcpy(msg + 4, t1 + 12 * y, 4);
                     memcpy(out, msg, 8);
-                    if (key) orc_keyed_hash(key, msg, 8, out + 8, 8);
+                    orc_keyed_hash(key, msg, 8, out + 8, 8);
                 }
                 count++;
             }
@@ -394,6 +392,126 @@ int64_t orc_match_global_bruteforce(const uint8_t *recs, uint64_t n, uint64_t D,
         }
     }
     return (int64_t)count;
+}
+
+/* ------------------------------------------------------------------ */
+/* All-core variants (the VaultX CPU plotter's threading, Sec. II-B):   */
+/* the same tables, the work split over POSIX threads.                  */
+/* ------------------------------------------------------------------ */
+
+struct sort_job {
+    uint8_t *recs;
+    const uint64_t *start; /* group g holds records start[g] .. start[g+1]-1 */
+    int g0, step, ngroups;
+};
+
+static void *sort_job_run(void *arg)
+{
+    struct sort_job *j = (struct sort_job *)arg;
+    for (int g = j->g0; g < j->ngroups; g += j->step) {
+        uint64_t lo = j->start[g], hi = j->start[g + 1];
+        if (hi - lo > 1) qsort(j->recs + 12 * lo, (size_t)(hi - lo), 12, rec_cmp);
+    }
+    return NULL;
+}
+
+/* Table 1 on nthreads threads: the records hashed in nonce order into
+ * `scratch` (orc_hash_range_mt), moved into t1 grouped by the top 8 bits of
+ * key64 (a counting pass; key64 order between groups is group order), then
+ * each group sorted by (key64, nonce) with qsort, groups spread over the
+ * threads.  Both buffers hold 2^K records. */
+int orc_table1_mt(int K, const uint8_t key[32], uint8_t *t1, uint8_t *scratch, int nthreads)
+{
+    if (K < 1 || K > 32) return -1;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 512) nthreads = 512;
+    const uint64_t n = 1ull << K;
+    orc_hash_range_mt(key, 0, n, scratch, nthreads);
+    uint64_t start[257], fill[256];
+    memset(start, 0, sizeof start);
+    for (uint64_t i = 0; i < n; i++) start[(rec_key64(scratch + 12 * i) >> 56) + 1]++;
+    for (int g = 0; g < 256; g++) start[g + 1] += start[g];
+    for (int g = 0; g < 256; g++) fill[g] = start[g];
+    for (uint64_t i = 0; i < n; i++) {
+        const uint8_t *r = scratch + 12 * i;
+        memcpy(t1 + 12 * fill[rec_key64(r) >> 56]++, r, 12);
+    }
+    pthread_t tid[512];
+    int started[512];
+    struct sort_job jobs[512];
+    for (int t = 0; t < nthreads; t++) {
+        jobs[t].recs = t1;
+        jobs[t].start = start;
+        jobs[t].g0 = t;
+        jobs[t].step = nthreads;
+        jobs[t].ngroups = 256;
+        started[t] = pthread_create(&tid[t], NULL, sort_job_run, &jobs[t]) == 0;
+        if (!started[t]) sort_job_run(&jobs[t]);
+    }
+    for (int t = 0; t < nthreads; t++)
+        if (started[t]) pthread_join(tid[t], NULL);
+    return 0;
+}
+
+struct match_job {
+    const uint8_t *key, *t1;
+    uint64_t lo, hi, D, off, count;
+    uint8_t *t2;
+};
+
+static void *match_job_run(void *arg)
+{
+    struct match_job *j = (struct match_job *)arg;
+    j->count = (uint64_t)orc_match(j->key, j->t1 + 12 * j->lo, j->hi - j->lo, j->D,
+                                   j->t2 ? j->t2 + 16 * j->off : NULL, j->t2 ? j->count : 0);
+    return NULL;
+}
+
+/* orc_match on nthreads threads.  Table 1 is cut into nthreads runs of whole
+ * logical buckets (a cut moves forward to the next bucket start), so the
+ * pairs of run t are orc_match of that run alone; a counting pass gives each
+ * run its place in Table 2, a second pass writes the pairs there.  Returns
+ * the number of pairs; t2 (NULL: count only) must hold all of them. */
+int64_t orc_match_mt(const uint8_t key[32], const uint8_t *t1, uint64_t n, uint64_t D, uint8_t *t2,
+                     int nthreads)
+{
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 512) nthreads = 512;
+    uint64_t cut[513];
+    cut[0] = 0;
+    for (int t = 1; t < nthreads; t++) {
+        uint64_t c = n * (uint64_t)t / (uint64_t)nthreads;
+        if (c < cut[t - 1]) c = cut[t - 1];
+        while (c > 0 && c < n && (rec_key64(t1 + 12 * c) >> 40) == (rec_key64(t1 + 12 * (c - 1)) >> 40))
+            c++;
+        cut[t] = c;
+    }
+    cut[nthreads] = n;
+    pthread_t tid[512];
+    int started[512];
+    struct match_job jobs[512];
+    for (int pass = 0; pass < (t2 ? 2 : 1); pass++) {
+        uint64_t off = 0;
+        for (int t = 0; t < nthreads; t++) {
+            if (pass == 1) {
+                jobs[t].off = off;
+                off += jobs[t].count;
+            }
+            jobs[t].key = key;
+            jobs[t].t1 = t1;
+            jobs[t].lo = cut[t];
+            jobs[t].hi = cut[t + 1];
+            jobs[t].D = D;
+            jobs[t].t2 = pass == 1 ? t2 : NULL;
+            started[t] = pthread_create(&tid[t], NULL, match_job_run, &jobs[t]) == 0;
+            if (!started[t]) match_job_run(&jobs[t]);
+        }
+        for (int t = 0; t < nthreads; t++)
+            if (started[t]) pthread_join(tid[t], NULL);
+    }
+    uint64_t total = 0;
+    for (int t = 0; t < nthreads; t++) total += jobs[t].count;
+    return (int64_t)total;
 }
 
 /* hash2 of a list of pairs (R10): for record i of `recs` (stride bytes

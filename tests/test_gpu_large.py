@@ -1,8 +1,7 @@
 """Full-size plots over K = 23 ... 32, compared with the oracle.
 
-K = 23 ... 27: both tables element by element against the oracle's
-(hashes on every host core, numpy's stable sort as the sorting step, the
-oracle's match, the oracle's pair hash on every host core).
+K = 23 ... 27: both tables element by element against the oracle's, run
+on every host core (its all-core variant, pinned to the plain oracle).
 
 K = 27 ... 31 (K=31 is the configuration bench.py times): properties that
 hold at any size, computed on the device with torch independently of the
@@ -195,7 +194,7 @@ def test_plot_equals_oracle_elementwise(vx, K):
     off = p.offsets().cpu().numpy()
     p.close()
     torch.cuda.empty_cache()
-    r1, r2 = orc.plot_mt(K, key, THREADS)
+    r1, r2 = orc.plot_allcores(K, key, THREADS)
     assert g1.shape == r1.shape
     d = first_diff(g1, r1)
     assert d < 0, "Table 1 differs from the oracle at record %d" % d

@@ -420,18 +420,6 @@ def test_window_slices_partition_the_plot():
             assert all(win_of_nonce[int(a)] == w and win_of_nonce[int(b)] == w for a, b in ab)
 
 
-@pytest.mark.parametrize("K,seed", [(1, 7), (9, 8), (15, 9)])
-def test_multithreaded_plot_equals_plain_plot(K, seed):
-    # plot_mt (hashing on several threads, numpy's stable sort, the match
-    # without hashes, then the pair hash on several threads) is the plain
-    # single-threaded oracle rearranged: the same tables byte for byte.
-    key = plot_key(seed)
-    t1, t2 = orc.plot(K, key)
-    for threads in (1, 3, 8):
-        m1, m2 = orc.plot_mt(K, key, threads)
-        assert np.array_equal(m1, t1) and np.array_equal(m2, t2)
-
-
 def test_pair_hash_rows():
     key = plot_key(11)
     rng = np.random.default_rng(11)
@@ -443,3 +431,16 @@ def test_pair_hash_rows():
     assert orc.pair_hash(key, rows[:, :8], 2).tobytes() == orc.pair_hash(key, rows, 1).tobytes()
     with pytest.raises(ValueError):
         orc.pair_hash(key, rows[:, :7])
+
+
+@pytest.mark.parametrize("K,seed,D", [(1, 12, None), (10, 13, None), (16, 14, None),
+                                      (16, 15, 1 << 37)])
+def test_allcore_plot_equals_plain_plot(K, seed, D):
+    # plot_allcores (threaded hash, grouping by the top key byte, threaded
+    # qsort per group, match over runs of whole buckets) = the plain oracle.
+    key = plot_key(seed)
+    t1 = orc.table1(K, key)
+    t2 = orc.match(key, t1, orc.default_distance(K) if D is None else D)
+    for threads in (1, 2, 7, 16):
+        a1, a2 = orc.plot_allcores(K, key, threads, D)
+        assert np.array_equal(a1, t1) and np.array_equal(a2, t2)
