@@ -32,7 +32,6 @@ if ROOT not in sys.path:
 
 METRIC = "Blake3 nonces/s and K=31 plot seconds on 1 GB300; % INT/HBM roofline; batched vs plain"
 UNIT = "nonces/s"
-SMS = 152
 SMSP_PER_SM = 4
 LANES = 32
 # Algorithmic 32-bit integer operations of one keyed BLAKE3 compression as
@@ -55,10 +54,16 @@ def peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
 
 
-def int_peak_ops(sm_mhz: float) -> float:
+def device_sms(device=0) -> int:
+    """Streaming multiprocessors of the CUDA device (152 on a GB300)."""
+    import torch
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
+
+
+def int_peak_ops(sm_mhz: float, sms: int) -> float:
     """Integer-issue peak: every SM sub-partition issues one 32-lane warp
-    instruction per clock (152 SMs x 4 x 32 lanes x clock)."""
-    return SMS * SMSP_PER_SM * LANES * sm_mhz * 1e6
+    instruction per clock (SMs x 4 x 32 lanes x clock)."""
+    return sms * SMSP_PER_SM * LANES * sm_mhz * 1e6
 
 
 class ClockSampler:
@@ -114,6 +119,31 @@ class ClockSampler:
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def free_port() -> int:
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        return so.getsockname()[1]
+
+
+def spawn_ranks(nproc: int, argv: list[str], env: dict | None = None) -> int:
+    """Runs the python script argv[0] with arguments argv[1:] as nproc ranks
+    on this node (torch.distributed.run, rendezvous on 127.0.0.1, one process
+    per GPU; each reads RANK / LOCAL_RANK / WORLD_SIZE / MASTER_* from its
+    environment).  Returns the launcher's exit code (non-zero if any rank
+    failed)."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           "--nproc-per-node", str(nproc), "--master-addr", "127.0.0.1",
+           "--master-port", str(free_port()), *argv]
+    return subprocess.call(cmd, env=env)
+
+
+def rank_env():
+    """(world, rank, local rank) of this process, from the launcher's env."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def reduce_max(value: float, world: int, device) -> float:
@@ -183,33 +213,34 @@ def ncu_traffic(kernel: str, K: int):
 
 
 def cpu_baseline(K_sample: int = 24, K_single: int = 20):
-    """The CPU oracle, as it stands: one plot of 2^K_sample nonces with the
-    hash on all host cores and sort and match on one core, and one plot of
-    2^K_single nonces entirely on one core."""
+    """The CPU oracle, as it stands, on the host cores: one plot of
+    2^K_sample nonces with every stage on all cores (its all-core variant:
+    threaded hashing, grouped threaded sort, match over runs of whole
+    buckets), and one plot of 2^K_single nonces with the plain oracle on one
+    core."""
     from oracle import oracle as orc
     from paper_2606_14007_gb300.inputs import plot_key
     orc.build()
-
-    def one(K, threads):
-        key = plot_key(1000 + K)
-        t0 = time.perf_counter()
-        recs = orc.hash_range(key, 0, 1 << K, threads=threads)
-        t1 = orc.sort_table1(recs)
-        t2 = orc.match(key, t1, orc.default_distance(K))
-        return time.perf_counter() - t0, t2.shape[0]
-
     threads = os.cpu_count() or 1
-    dt, _ = one(K_sample, threads)
-    dt1, _ = one(K_single, 1)
+    key = plot_key(1000 + K_sample)
+    t0 = time.perf_counter()
+    orc.plot_allcores(K_sample, key, threads)
+    dt = time.perf_counter() - t0
+    key = plot_key(1000 + K_single)
+    t0 = time.perf_counter()
+    orc.plot(K_single, key)
+    dt1 = time.perf_counter() - t0
     return {"value": (1 << K_sample) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "one K=%d plot (2^%d nonces): keyed BLAKE3 on %d threads, qsort and match "
-                      "(incl. pair hashing) on 1 thread; %.1f s" % (K_sample, K_sample, threads, dt),
+            "sample": "one K=%d plot (2^%d nonces) with every stage (hash, sort, match incl. pair "
+                      "hashing) on all %d host cores; %.1f s" % (K_sample, K_sample, threads, dt),
             "single_thread": {"value": (1 << K_single) / dt1, "unit": UNIT, "cores": 1,
-                              "sample": "one K=%d plot entirely on 1 thread; %.1f s" % (K_single, dt1)}}
+                              "sample": "one K=%d plot entirely on 1 thread (plain oracle); %.1f s"
+                                        % (K_single, dt1)}}
 
 
 def run_reference(args):
-    """CPU oracle as the reference arm: one K=22 plot per step."""
+    """CPU oracle as the reference arm: one K=22 plot per step, every stage
+    on all host cores (the oracle's all-core variant)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -220,10 +251,7 @@ def run_reference(args):
     threads = os.cpu_count() or 1
 
     def step(i):
-        key = plot_key(2000 + i)
-        recs = orc.hash_range(key, 0, 1 << Ks, threads=threads)
-        t1 = orc.sort_table1(recs)
-        orc.match(key, t1, orc.default_distance(Ks))
+        orc.plot_allcores(Ks, plot_key(2000 + i), threads)
 
     for i in range(args.warmup):
         step(i)
@@ -240,7 +268,7 @@ def run_reference(args):
         "config": {"workload": "plain plot, bounded sample: one K=22 plot per step on the CPU oracle",
                    "K": Ks, "key_seeds": "2000+i"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": "one K=22 plot per step: hash on %d threads, sort + match on 1" % threads},
+                         "sample": "one K=22 plot per step, every stage on %d host cores" % threads},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -258,14 +286,17 @@ def main():
     ap.add_argument("--e2e-copy-streams", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="plain",
-                    choices=["plain", "batch", "large", "serve", "write", "sort2", "tiled", "plotfile"],
+                    choices=["plain", "batch", "large", "serve", "write", "sort2", "tiled", "plotfile",
+                             "hashpeak", "sweep"],
                     help="plain: the K=31 headline; batch: 64 mixed-K plots batched vs plain; "
                          "large: 4 x K=29 + 8 x K=27 batched vs plain; serve: Poisson requests "
                          "through the continuous-batching server vs one at a time; write: plots "
                          "written to flat Table-2 files, serial vs overlapped with the next plot; "
                          "sort2: Table 2 of a K plot sorted by hash2; tiled: a K plot built "
                          "window by window into pinned host memory vs the whole plot and its copy; "
-                         "plotfile: one K plot file end to end (plot, write, fsync), whole and tiled")
+                         "plotfile: one K plot file end to end (plot, write, fsync), whole and tiled; "
+                         "hashpeak: the hash-only ceiling (no record stores); sweep: per-K plot "
+                         "times and kernel split for K=22 and 27..31 beside the oracle")
     ap.add_argument("--partition-log2", type=int, default=0)
     ap.add_argument("--scatter-mode", type=int, default=0)
     ap.add_argument("--fuse-pair-hash", type=int, default=0)
@@ -296,17 +327,32 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.gpus < 1:
+        ap.error("--gpus must be >= 1")
     if args.impl == "reference":
         return run_reference(args)
     if args.mode != "plain":
+        if args.gpus != 1 or "WORLD_SIZE" in os.environ:
+            ap.error("--mode %s runs on one GPU (--gpus 1, no launcher)" % args.mode)
         return run_mode(args)
 
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        # Started without a launcher: run the N replica ranks ourselves, one
+        # GPU each, every rank plotting its own keys (no data-path collective).
+        have = torch.cuda.device_count()
+        if have < args.gpus:
+            print("bench.py: --gpus %d but %d CUDA device(s) visible" % (args.gpus, have),
+                  file=sys.stderr)
+            return 2
+        return spawn_ranks(args.gpus, [os.path.abspath(__file__), *sys.argv[1:]])
+    world, rank, local = rank_env()
+    if world != args.gpus:
+        print("bench.py: --gpus %d but the launcher started %d rank(s)" % (args.gpus, world),
+              file=sys.stderr)
+        return 2
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -358,7 +404,8 @@ def main():
     pk = {}
     pk_peak = peaks()
     hbm_peak = pk_peak["hbm_gbs"]
-    int_peak = int_peak_ops(pk_peak["sm_max_mhz"])
+    sms = device_sms(local)
+    int_peak = int_peak_ops(pk_peak["sm_max_mhz"], sms)
     # Algorithmic work per launch: a hash kernel does one compression per
     # nonce and writes 12 B per record; the second scatter level reads and
     # writes 12 B per record; sort+match reads 12 B and writes 12 B per
@@ -395,10 +442,17 @@ def main():
         ach = pk[dom]["int_tops"] * 1e12
         roof = {"kernel": dom, "bound": "alu", "achieved": ach / 1e12, "peak": int_peak / 1e12,
                 "unit": "Tops/s (32-bit integer)", "frac": ach / int_peak,
-                "peak_basis": "152 SMs x 4 sub-partitions x 32 lanes x %.0f MHz (max SM clock, %s)"
-                              % (pk_peak["sm_max_mhz"], pk_peak["source"]),
+                "peak_basis": "%d SMs (device) x 4 sub-partitions x 32 lanes x %.0f MHz (max SM clock, %s)"
+                              % (sms, pk_peak["sm_max_mhz"], pk_peak["source"]),
                 "work_per_launch": algo_ops[dom],
                 "traffic": ncu_traffic(dom, K)}
+        ceil = hash_ceiling(vx, stream, sms)
+        roof["peak_measured"] = {
+            "value": ceil["int_ops_per_s"] / 1e12, "unit": "Tops/s (32-bit integer)",
+            "frac": ach / ceil["int_ops_per_s"],
+            "source": "vx_hash_peak in this run: the same keyed BLAKE3 in the Table-1 kernel's shape "
+                      "with no record stores, 2^31 nonces, best grid of 2..16 CTAs/SM (%d), %.2f ms"
+                      % (ceil["ctas_per_sm"], ceil["ms_per_2^31"])}
         ent = ncu_entry(dom, K)
         if ent and "alu_pipe_pct" in ent:
             # the integer (ALU) pipe's own occupancy, from the committed ncu
@@ -540,6 +594,104 @@ def _timed(fn, stream):
     b.record(stream)
     torch.cuda.synchronize()
     return a.elapsed_time(b)
+
+
+def hash_ceiling(vx, stream, sms: int, K: int = 31, reps: int = 3):
+    """The hash-only ceiling: vx_hash_peak over 2^K nonces (no record
+    stores) at grids of 2, 3, 4, 8 and 16 CTAs per SM, best of `reps` timed
+    launches each after one untimed one; returns the best rate and the
+    sweep."""
+    import torch
+    from paper_2606_14007_gb300.inputs import plot_key
+    key = plot_key(K)
+    N = 1 << K
+    sweep = {}
+    for per_sm in (2, 3, 4, 8, 16):
+        words = 256 * per_sm * sms
+        fold = torch.empty(words, dtype=torch.int32, device="cuda")
+        vx.vx_hash_peak(key, 0, N, fold.data_ptr(), words, stream)
+        best = min(_timed(lambda: vx.vx_hash_peak(key, 0, N, fold.data_ptr(), words, stream), stream)
+                   for _ in range(reps))
+        sweep[str(per_sm)] = best
+        del fold
+    per_sm, ms = min(sweep.items(), key=lambda kv: kv[1])
+    ops = INT_OPS_PER_COMPRESSION * N / (ms / 1e3)
+    return {"compressions_per_s": N / (ms / 1e3), "int_ops_per_s": ops, "ms_per_2^%d" % K: ms,
+            "ctas_per_sm": int(per_sm), "sweep_ms": sweep}
+
+
+def run_hashpeak(vx, args):
+    import torch
+    stream = torch.cuda.current_stream()
+    sms = device_sms(int(os.environ.get("LOCAL_RANK", "0")))
+    pk = peaks()
+    c = hash_ceiling(vx, stream, sms, args.K)
+    nominal = int_peak_ops(pk["sm_max_mhz"], sms)
+    c.update({"mode": "hashpeak", "K": args.K, "sms": sms,
+              "nominal_int_ops_per_s": nominal, "frac_of_nominal": c["int_ops_per_s"] / nominal,
+              "note": "keyed BLAKE3 of 2^K nonces in the Table-1 kernel's shape with no record "
+                      "stores (vx_hash_peak); %d int32 ops per compression" % INT_OPS_PER_COMPRESSION})
+    return c
+
+
+def run_sweep(vx, args):
+    """Per-K results: for K = 22 and 27 .. 31 one plain plot per step (key
+    from seed K), device ms per plot (CUDA events on the launching stream,
+    `steps` timed after `warmup`), nonces/s, the per-kernel split, and
+    T(k+1)/T(k); beside them the oracle on the host cores: single-thread
+    (plain oracle) measured at K = 20 .. 23, all cores (its all-core
+    variant) measured at K = 20 .. 27, larger K extrapolated as N log N from
+    the largest measured K and labelled so."""
+    import torch
+    from oracle import oracle as orc
+    from paper_2606_14007_gb300.inputs import plot_key
+    stream = torch.cuda.current_stream()
+    rows = []
+    for K in (22, 27, 28, 29, 30, 31):
+        plot = vx.Plot(K, plot_key(K), plot_opts(vx, args))
+        for _ in range(args.warmup):
+            plot.run(stream)
+        plot.sync()
+        vx.vx_plot_profile(plot.handle, args.steps)
+        ms = _timed(lambda: [vx.vx_plot_run(plot.handle, stream) for _ in range(args.steps)], stream)
+        ms /= args.steps
+        n2 = plot.sync()
+        per_kernel, runs = vx.vx_plot_profile_read(plot.handle)
+        vx.vx_plot_profile(plot.handle, 0)
+        split = {k: v / max(1, runs) for k, v in per_kernel.items() if v > 0}
+        rows.append({"K": K, "plot_ms": ms, "nonces_per_s": (1 << K) / (ms / 1e3),
+                     "table2_records": n2, "kernel_ms": split})
+        plot.close()
+        del plot
+        torch.cuda.empty_cache()
+    for a, b in zip(rows, rows[1:]):
+        if b["K"] == a["K"] + 1:
+            b["ratio_vs_prev_K"] = b["plot_ms"] / a["plot_ms"]
+    orc.build()
+    threads = os.cpu_count() or 1
+    single, allc = {}, {}
+    for K in (20, 21, 22, 23):
+        t0 = time.perf_counter()
+        orc.plot(K, plot_key(K))
+        single[K] = time.perf_counter() - t0
+    for K in range(20, 28):
+        t0 = time.perf_counter()
+        orc.plot_allcores(K, plot_key(K), threads)
+        allc[K] = time.perf_counter() - t0
+
+    def est(meas, K):
+        if K in meas:
+            return {"s": meas[K], "measured": True}
+        k0 = max(meas)
+        return {"s": meas[k0] * 2 ** (K - k0) * K / k0, "measured": False}
+
+    for r in rows:
+        r["oracle_1_thread"] = est(single, r["K"])
+        r["oracle_all_cores"] = est(allc, r["K"])
+        r["gpu_over_oracle_all_cores"] = r["oracle_all_cores"]["s"] / (r["plot_ms"] / 1e3)
+    return {"mode": "sweep", "rows": rows, "oracle_cores": threads,
+            "note": "device plot time per K (vx_plot_run, tables resident in HBM); oracle seconds "
+                    "with measured=false are extrapolated as N log N from the largest measured K"}
 
 
 def run_batch_compare(vx, mix, steps, warmup, name, label, tune=False):
@@ -1068,6 +1220,10 @@ def run_mode(args):
         out = run_tiled_file(vx, args) if args.tiled_file else run_tiled(vx, args)
     elif args.mode == "plotfile":
         out = run_plotfile(vx, args)
+    elif args.mode == "hashpeak":
+        out = run_hashpeak(vx, args)
+    elif args.mode == "sweep":
+        out = run_sweep(vx, args)
     else:
         out = run_serve(vx, args)
     if int(os.environ.get("RANK", "0")) == 0:

@@ -433,6 +433,18 @@ const char *vx_kernel_name(int k);
 int vx_hash_nonces(const uint8_t key[32], uint64_t nonce0, uint64_t count, void *d_out,
                    void *stream);
 
+/* Measurement of the hash's ceiling, not a step of the path: keyed BLAKE3
+ * of nonces nonce0 .. nonce0+count-1 in the Table-1 hash kernel's shape
+ * (256 threads, 8 nonces per thread and step), with no record stores; each
+ * thread folds its hash words into one u32 of d_fold (device, 4-byte
+ * aligned, fold_words words, a nonzero multiple of 256: the grid is
+ * fold_words / 256 CTAs).  Timing it gives the integer-issue rate this
+ * instruction mix reaches with no memory work beside it, the ceiling the
+ * Table-1 hash (Sec. III-B) is compared with.  VX_EINVAL for a bad size or
+ * a nonce range beyond 2^32.  Asynchronous.  The paper has no counterpart. */
+int vx_hash_peak(const uint8_t key[32], uint64_t nonce0, uint64_t count, void *d_fold,
+                 uint32_t fold_words, void *stream);
+
 /* Pair hash of Table 2 on its own: for each of `count` pairs (a, b) at
  * d_pairs (device, 2 LE u32 each, 8-byte aligned) writes the 16-byte
  * Table-2 record {a, b, hash2[0..7]} to d_out (16-byte aligned),

@@ -616,6 +616,45 @@ cudaError_t launch_hash_records(const uint32_t key[8], uint64_t nonce0, uint64_t
     return cudaGetLastError();
 }
 
+// Hash-only ceiling of the Table-1 hash: keyed BLAKE3 of nonces nonce0 ..
+// nonce0 + count - 1 in the Table-1 kernel's shape (256 threads, 8 nonces
+// per thread and step, key state from the per-key setup), with no record
+// stores: each thread folds its hash words into one word, stored once.  It
+// measures how fast the integer pipes run this instruction mix with no
+// memory work beside it.  Grid-stride over tiles of 2048 nonces.
+__global__ void __launch_bounds__(256) k_hash_peak(uint32_t k0, uint32_t k1, uint32_t k2,
+                                                   uint32_t k3, uint32_t k4, uint32_t k5,
+                                                   uint32_t k6, uint32_t k7, uint64_t nonce0,
+                                                   uint64_t count, uint32_t *__restrict__ fold)
+{
+    constexpr int NPT = kHashNoncesPerThread;
+    constexpr uint64_t T = (uint64_t)kHashThreads * NPT;
+    const uint32_t key[8] = {k0, k1, k2, k3, k4, k5, k6, k7};
+    uint32_t pre[16];
+    b3_key_setup(key, 4u, pre);
+    uint32_t acc = 0;
+    const uint64_t tiles = (count + T - 1) / T;
+    for (uint64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+            const uint64_t i = t * T + (uint64_t)j * kHashThreads + threadIdx.x;
+            uint32_t h0, h1;
+            b3_finish<false>(pre, (uint32_t)(nonce0 + i), 0u, h0, h1);
+            acc ^= i < count ? (h0 ^ h1) : 0u;
+        }
+    }
+    fold[(uint64_t)blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+cudaError_t launch_hash_peak(const uint32_t key[8], uint64_t nonce0, uint64_t count, uint32_t *fold,
+                             uint32_t blocks, cudaStream_t s)
+{
+    if (blocks == 0) return cudaErrorInvalidValue;
+    k_hash_peak<<<blocks, kHashThreads, 0, s>>>(key[0], key[1], key[2], key[3], key[4], key[5],
+                                                key[6], key[7], nonce0, count, fold);
+    return cudaGetLastError();
+}
+
 // Table-2 records {a, b, g0, g1} of the pairs (a, b).
 __global__ void __launch_bounds__(256) k_pair_hash(uint32_t k0, uint32_t k1, uint32_t k2,
                                                    uint32_t k3, uint32_t k4, uint32_t k5,

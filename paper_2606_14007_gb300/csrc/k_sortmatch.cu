@@ -5,15 +5,24 @@
 // with a single-thread insertion sort; Sec. V names that O(n^2) sort as the
 // K=31 bottleneck and proposes a parallel radix sort.  Kept here: the
 // fusion (a partition never leaves shared memory between sort and match).
-// Changed: one CTA per physical partition (a run of whole logical buckets,
-// ~2048 records; five CTAs per SM), a counting-sort pass on the key bits
-// below the partition prefix followed by per-digit insertion sorts (about
-// one record per digit), and the partition's Table-2 base found by a
-// decoupled look-back over the partitions before it (partition order comes
-// from a ticket counter, so every partition a CTA waits on is already
-// running; every wait is bounded and a timeout poisons the chain instead of
+// Changed: a physical partition (a run of whole logical buckets, ~2048
+// records) per work item, a counting-sort pass on the key bits below the
+// partition prefix followed by per-digit insertion sorts (about one record
+// per digit), and the partition's Table-2 base found by a decoupled
+// look-back over the partitions before it (partition order comes from a
+// ticket counter, so every partition an item waits on is held by a running
+// CTA; every wait is bounded and a timeout poisons the chain instead of
 // hanging).  With the cross-bucket match (HALO instances) the next
 // partition's halo is sorted in behind the partition's records.
+//
+// Two front ends feed the same per-partition steps:
+//  * k_sortmatch_pipe (the default): persistent CTAs, three per SM at the
+//    default slot.  A CTA's next partition slot (keys and nonces, two
+//    contiguous runs) comes into shared memory by cp.async.bulk while the
+//    CTA sorts, matches and writes the current one, so no step waits on
+//    global memory: the slot lands during the previous item.
+//  * k_sortmatch_gl: one CTA per partition reading its slot from global
+//    memory, for slots too large to hold twice in shared memory.
 //
 // MODE kSortCount: the sort alone (Table 1 + per-partition pair counts),
 // used by the split vx_table1 / vx_match path.
@@ -33,123 +42,86 @@ namespace vx {
 
 enum { kSortCount = 0, kSortHash = 1, kSortEmit = 2, kSortSlots = 3 };
 constexpr uint32_t kSMList = 2048;  // pair-list window (entries), kSortHash only
-constexpr int kSMThreads = 256;
-// Tickets between a CTA and the partition whose slot it prefetches into L2:
-// about half of the CTAs resident at once (152 SMs x 5).  Measured at K=31:
-// 38.7 ms for 190..380, 39.0 ms for 760, 41.0 ms (no gain) from 1520 up.
-// Only the filled part is fetched (the whole slot cost 27% extra DRAM
-// reads), its fill count loaded at CTA start and used after step 1 so the
-// load's latency hides under the histogram.
+constexpr int kPipeThreads = 256;   // persistent front end
+constexpr int kGlThreads = 256;     // one-CTA-per-partition front end
+// Tickets between a CTA of the global-memory front end and the partition
+// whose slot it prefetches into L2: about half of the CTAs resident at once.
 constexpr uint32_t kSlotPrefetchAhead = 384;
 
-// Shared layout: sorted key64 [cap] | sorted nonce [cap] | rank within the
-// digit, u16 [cap] + digit counters [2^dbits], later overlaid by the
-// per-record pair count -> Table-2 offset [cap] | pair list (kSortHash) |
-// scan workspace.  The latency-bound sort runs five CTAs per SM (48
-// registers): measured 41.0 ms at K=31 against 44.8 ms with four.
+// Shared layout (bytes from the base), for slots of at most `cap` records
+// (a multiple of 4) and digits of at most `dbits` bits:
+//   raw keys [cap] | raw nonces [cap]        (pipelined front end only)
+//   sorted key64 [cap] | sorted nonce [cap]
+//   digit counters [2^dbits], dead after the digit runs are sorted, then
+//   overlaid by the per-record pair count -> Table-2 offset [cap]
+//   pair list [kSMList] (kSortHash) | scan workspace | mbarrier
 struct SMLayout {
-    size_t sn, rank, dcnt, start, list, ws, bytes;
-    __host__ __device__ SMLayout(uint32_t cap, int dbits, bool with_list)
+    size_t rk, rn, sk, sn, dc, list, ws, bar, bytes;
+    __host__ __device__ SMLayout(uint32_t cap, int dbits, bool with_list, bool with_raw)
     {
-        sn = (size_t)cap * 8;
-        rank = sn + (size_t)cap * 4;
-        dcnt = rank + (size_t)((cap + 1) & ~1u) * 2;
-        // The per-record pair counts (step 5 on) reuse the rank and digit-
-        // counter space, dead after step 4: 43.8 KiB at the default 2608-
-        // record slot, so five CTAs fit an SM's 228 KiB.
-        start = rank;
-        const size_t rd_end = dcnt + ((size_t)1 << dbits) * 4;
-        const size_t st_end = start + (size_t)cap * 4;
-        list = rd_end > st_end ? rd_end : st_end;
+        cap = (cap + 3u) & ~3u;
+        rk = 0;
+        rn = rk + (with_raw ? (size_t)cap * 8 : 0);
+        sk = rn + (with_raw ? (size_t)cap * 4 : 0);
+        sn = sk + (size_t)cap * 8;
+        dc = sn + (size_t)cap * 4;
+        const size_t dcb = ((size_t)1 << dbits) * 4, stb = (size_t)cap * 4;
+        list = dc + (dcb > stb ? dcb : stb);
         ws = list + (with_list ? (size_t)kSMList * 4 : 0);
-        bytes = ws + 40 * 4;
+        bar = (ws + 40 * 4 + 7) & ~(size_t)7;
+        bytes = bar + 8;
     }
 };
 
-template <int MODE, bool HALO>
-__global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 5)
-    k_sortmatch(const Desc *__restrict__ descs, int nplots, const uint32_t *__restrict__ tile_start)
+struct Part {
+    uint64_t *SK;
+    uint32_t *SN, *DC, *ST, *LS, *WS;
+};
+
+// The partition's records, read from `src` (shared or global memory), go
+// into SK / SN grouped by digit (the next `dbits` key bits below the
+// partition prefix), in arbitrary order inside a digit; DC[g] ends as the
+// end of digit g's run.  Ends with a barrier.
+template <int NT, class Src>
+__device__ __forceinline__ void place_by_digit(const Part &A, uint32_t n, int shift, uint32_t ndig,
+                                               const Src &src)
+{
+    const uint32_t dmask = ndig - 1u;
+    for (uint32_t i = threadIdx.x; i < n; i += NT) {
+        const uint32_t dg = (uint32_t)(src.key(i) >> shift) & dmask;
+        atomicAdd(&A.DC[dg], 1u);
+    }
+    __syncthreads();
+    block_scan_inplace_u32<NT>(A.DC, ndig, A.WS);  // counts -> run starts
+    for (uint32_t i = threadIdx.x; i < n; i += NT) {
+        const uint64_t k = src.key(i);
+        const uint32_t pos = atomicAdd(&A.DC[(uint32_t)(k >> shift) & dmask], 1u);
+        A.SK[pos] = k;
+        A.SN[pos] = src.nonce(i);
+    }
+    __syncthreads();
+}
+
+// Everything after the placement, for partition f (n records, Table-1
+// offset `off`) of plot d: the digit runs sorted by (key64, nonce), the
+// next partition's halo (HALO), the pair counts and their scan, Table 1,
+// then the mode's Table-2 output.  Starts and ends at a barrier; returns
+// nothing on failure (the status word says why), so a persistent caller
+// goes on to its next item.
+template <int MODE, bool HALO, int NT>
+__device__ __forceinline__ void finish_partition(const Desc &d, uint32_t f, uint32_t n, uint64_t off,
+                                                 uint32_t ndig, const Part &A, uint64_t *s_base,
+                                                 int *s_ok)
 {
     constexpr bool EMIT = MODE == kSortHash || MODE == kSortEmit;  // look-back placement
     constexpr bool SLOTS = MODE == kSortSlots;
-    constexpr int NT = kSMThreads;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ uint32_t s_f;
-    __shared__ uint64_t s_base;
-    __shared__ int s_ok;
-    const int plot = find_plot(tile_start, nplots, blockIdx.x);
-    const Desc &d = descs[plot];
-    if (EMIT) {
-        if (threadIdx.x == 0) s_f = atomicAdd(d.ticket, 1u);
-        __syncthreads();
-    }
-    const uint32_t f = EMIT ? s_f : (blockIdx.x - tile_start[plot]);
-    if (f >= (1u << d.p)) {  // only if the ticket was not reset: report, never index with it
-        if (threadIdx.x == 0) atomicOr(d.status, kStBadTicket);
-        return;
-    }
-    const uint32_t cap = d.cap2;
-    const int dbits = d.dbits;
-    // Warm L2 with the filled part of the slot of the partition
-    // kSlotPrefetchAhead tickets (CTAs) ahead, so that its CTA's first reads
-    // (steps 1, 3) hit L2; its fill count is read now and used after step 1.
-    const uint64_t fa = (uint64_t)f + kSlotPrefetchAhead;
-    const uint32_t nfa = (threadIdx.x == 0 && fa < (1ull << d.p)) ? min(d.cnt2[fa], cap) : 0u;
-    const uint32_t ndig = 1u << dbits;
-    const uint32_t hcap = HALO ? d.hcap : 0u;
-    const SMLayout L(cap + hcap, dbits, MODE == kSortHash);  // + the next partition's halo
-    uint64_t *SK = reinterpret_cast<uint64_t *>(smem_raw);
-    uint32_t *SN = reinterpret_cast<uint32_t *>(smem_raw + L.sn);
-    uint16_t *RK = reinterpret_cast<uint16_t *>(smem_raw + L.rank);
-    uint32_t *DC = reinterpret_cast<uint32_t *>(smem_raw + L.dcnt);
-    uint32_t *ST = reinterpret_cast<uint32_t *>(smem_raw + L.start);
-    uint32_t *LS = reinterpret_cast<uint32_t *>(smem_raw + L.list);
-    uint32_t *WS = reinterpret_cast<uint32_t *>(smem_raw + L.ws);
-
-    const uint32_t n = min(d.cnt2[f], cap);
-    const uint64_t off = d.t1off[f];
-    // The slot is read through the read-only path unless this kernel later
-    // overwrites it with the partition's pairs.
-    const uint64_t *ikeys = d.b_keys + (uint64_t)f * cap;
-    const uint32_t *inonces = d.b_nonces + (uint64_t)f * cap;
-    auto key_at = [&](uint32_t i) -> uint64_t { return SLOTS ? ikeys[i] : __ldg(ikeys + i); };
-    auto nonce_at = [&](uint32_t i) -> uint32_t { return SLOTS ? inonces[i] : __ldg(inonces + i); };
-    const int shift = 64 - d.pk - dbits;
-    const uint32_t dmask = ndig - 1u;
-
-    // 1. digit histogram (rank of each record within its digit)
-    for (uint32_t i = threadIdx.x; i < ndig; i += NT) DC[i] = 0u;
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n; i += NT) {
-        const uint32_t dg = (uint32_t)(key_at(i) >> shift) & dmask;
-        RK[i] = (uint16_t)atomicAdd(&DC[dg], 1u);
-    }
-    if (nfa) {
-        const uint32_t nk = (nfa + 1u) & ~1u, nn = (nfa + 3u) & ~3u;  // 16-byte multiples
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_keys + fa * cap),
-                     "r"(nk * 8u)
-                     : "memory");
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_nonces + fa * cap),
-                     "r"(nn * 4u)
-                     : "memory");
-    }
-    __syncthreads();
-    // 2. digit counters -> digit start positions
-    block_scan_inplace_u32<NT>(DC, ndig, WS);
-    // 3. place records at their digit position (the second read of the
-    //    slot hits L1/L2)
-    for (uint32_t i = threadIdx.x; i < n; i += NT) {
-        const uint64_t k = key_at(i);
-        const uint32_t pos = DC[(uint32_t)(k >> shift) & dmask] + RK[i];
-        SK[pos] = k;
-        SN[pos] = nonce_at(i);
-    }
-    __syncthreads();
+    uint64_t *SK = A.SK;
+    uint32_t *SN = A.SN;
     // 4. finish every digit run (about one record each) by insertion sort on
-    //    (key64, nonce)
+    //    (key64, nonce); run g is [DC[g-1], DC[g])
     for (uint32_t dg = threadIdx.x; dg < ndig; dg += NT) {
-        const uint32_t s0 = DC[dg];
-        const uint32_t s1 = dg + 1 < ndig ? DC[dg + 1] : n;
+        const uint32_t s0 = dg ? A.DC[dg - 1] : 0u;
+        const uint32_t s1 = A.DC[dg];
         for (uint32_t a = s0 + 1; a < s1; ++a) {
             const uint64_t kx = SK[a];
             const uint32_t nx = SN[a];
@@ -172,7 +144,8 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 5)
     //     sorted right after this partition's records, so the pair scan
     //     below runs on into it; records n .. nt - 1 start no pairs here.
     uint32_t nt = n;
-    if (HALO && hcap) {
+    if (HALO && d.hcap) {
+        const uint32_t hcap = d.hcap;
         const uint64_t fn = (uint64_t)f + 1;
         const uint32_t hc = fn < (1ull << d.p) ? min(d.halo_cnt[fn], hcap) : 0u;
         for (uint32_t h = threadIdx.x; h < hc; h += NT) {
@@ -199,7 +172,8 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 5)
     // 5. pairs starting at each record r: the later records up to
     //    lim = min(last key of r's logical bucket, key_r + D - 1), or
     //    key_r + D - 1 for the cross-bucket match; four probes per step
-    //    (key64 sorted ascending)
+    //    (key64 sorted ascending).  ST overlays the dead digit counters.
+    uint32_t *ST = A.ST;
     const uint64_t D = d.D;
     const bool global = HALO && d.scope != 0;
     for (uint32_t r = threadIdx.x; r < n; r += NT) {
@@ -222,74 +196,71 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 5)
     __syncthreads();
     // 6. counts -> per-record Table-2 offsets; the partition's pair count
     //    is published at once so later partitions are not held up
-    const uint32_t P = block_scan_inplace_u32<NT>(ST, n, WS);
+    const uint32_t P = block_scan_inplace_u32<NT>(ST, n, A.WS);
     const bool withhold = (d.test_flags & 1u) != 0;
     if (threadIdx.x == 0) {
         d.pairs[f] = P;  // lets vx_match re-run the match alone
         if (EMIT) lb_publish(d.lb, f, P, withhold);
     }
-    // 7. Table 1.  Records 12 B each: the head up to a 16-byte boundary and
-    //    the tail go word by word; the body goes as groups of 4 records =
-    //    three 16-byte stores per thread.  (Resolving the look-back in warp 0
-    //    while the other warps write Table 1 measured slower than this
-    //    order: 45.2 vs 44.8 ms at K=31.)
-    const uint64_t np = 1ull << d.p;
+    // 7. Table 1, 12-byte records {nonce, BE key64}: thread q writes output
+    //    words 4q .. 4q + 3 (one 16-byte store; a word is record w / 3,
+    //    field w % 3), so lanes read neighbouring records of SK / SN; the
+    //    words before the first 16-byte boundary and after the last one go
+    //    singly.
     {
-        constexpr uint32_t NW = NT;  // Table-1 writers
-        const uint32_t tw = threadIdx.x;
         uint32_t *__restrict__ t1w = reinterpret_cast<uint32_t *>(d.t1) + 3 * off;
-        const uint32_t head = min(n, (uint32_t)((4u - (uint32_t)(off & 3u)) & 3u));
-        const uint32_t groups = (n - head) / 4u;
-        const uint32_t tail0 = head + 4u * groups;
-        for (uint32_t r = tw; r < head + (n - tail0); r += NW) {
-            const uint32_t rr = r < head ? r : tail0 + (r - head);
-            const uint64_t k = SK[rr];
-            t1w[3 * rr] = SN[rr];
-            t1w[3 * rr + 1] = bswap32((uint32_t)(k >> 32));
-            t1w[3 * rr + 2] = bswap32((uint32_t)k);
+        const uint32_t nw = 3u * n;
+        const uint32_t head = min(nw, (uint32_t)((4u - (uint32_t)((3u * off) & 3u)) & 3u));
+        const uint32_t body = (nw - head) >> 2;  // 16-byte chunks
+        const uint32_t tail0 = head + 4u * body;
+        auto word = [&](uint32_t w) -> uint32_t {
+            const uint32_t r = w / 3u, c = w - 3u * r;
+            if (c == 0) return SN[r];
+            const uint64_t k = SK[r];
+            return bswap32(c == 1 ? (uint32_t)(k >> 32) : (uint32_t)k);
+        };
+        for (uint32_t w = threadIdx.x; w < head + (nw - tail0); w += NT) {
+            const uint32_t ww = w < head ? w : tail0 + (w - head);
+            t1w[ww] = word(ww);
         }
-        uint4 *__restrict__ body = reinterpret_cast<uint4 *>(t1w + 3 * head);
-        for (uint32_t g = tw; g < groups; g += NW) {
-            const uint32_t r = head + 4u * g;
-            uint32_t w[12];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const uint64_t k = SK[r + j];
-                w[3 * j] = SN[r + j];
-                w[3 * j + 1] = bswap32((uint32_t)(k >> 32));
-                w[3 * j + 2] = bswap32((uint32_t)k);
-            }
-            body[3 * g] = make_uint4(w[0], w[1], w[2], w[3]);
-            body[3 * g + 1] = make_uint4(w[4], w[5], w[6], w[7]);
-            body[3 * g + 2] = make_uint4(w[8], w[9], w[10], w[11]);
+        uint4 *__restrict__ t1v = reinterpret_cast<uint4 *>(t1w + head);
+        for (uint32_t q = threadIdx.x; q < body; q += NT) {
+            const uint32_t w = head + 4u * q;
+            t1v[q] = make_uint4(word(w), word(w + 1), word(w + 2), word(w + 3));
         }
     }
     if (SLOTS) {
         // 8. pairs into the slot (its records were read before the
         //    barriers above)
+        const uint32_t cap = d.cap2;
         const uint32_t capA = cap, capB = cap / 2u;
         if (P > capA + capB) {
             if (threadIdx.x == 0) atomicOr(d.status, kStPairSlot);
-            return;
-        }
-        uint2 *__restrict__ pa = reinterpret_cast<uint2 *>(d.b_keys + (uint64_t)f * cap);
-        uint2 *__restrict__ pb = reinterpret_cast<uint2 *>(d.b_nonces + (uint64_t)f * cap);
-        for (uint32_t r = threadIdx.x; r < n; r += NT) {
-            const uint32_t s0 = ST[r];
-            const uint32_t s1 = r + 1 < n ? ST[r + 1] : P;
-            const uint32_t a = SN[r];
-            for (uint32_t k = s0; k < s1; ++k) {
-                const uint2 v = make_uint2(a, SN[r + 1 + (k - s0)]);
-                if (k < capA)
-                    pa[k] = v;
-                else
-                    pb[k - capA] = v;
+        } else {
+            uint2 *__restrict__ pa = reinterpret_cast<uint2 *>(d.b_keys + (uint64_t)f * cap);
+            uint2 *__restrict__ pb = reinterpret_cast<uint2 *>(d.b_nonces + (uint64_t)f * cap);
+            for (uint32_t r = threadIdx.x; r < n; r += NT) {
+                const uint32_t s0 = ST[r];
+                const uint32_t s1 = r + 1 < n ? ST[r + 1] : P;
+                const uint32_t a = SN[r];
+                for (uint32_t k = s0; k < s1; ++k) {
+                    const uint2 v = make_uint2(a, SN[r + 1 + (k - s0)]);
+                    if (k < capA)
+                        pa[k] = v;
+                    else
+                        pb[k - capA] = v;
+                }
             }
         }
+        __syncthreads();
         return;
     }
-    if (!EMIT) return;
+    if (!EMIT) {
+        __syncthreads();
+        return;
+    }
     // 8. Table-2 base: resolve the look-back (warp 0)
+    const uint64_t np = 1ull << d.p;
     if (threadIdx.x < 32) {
         uint64_t excl = 0;
         int ok = lb_resolve(d.lb, f, P, d.status, d.spin_limit, withhold, &excl) ? 1 : 0;
@@ -302,48 +273,254 @@ __global__ void __launch_bounds__(kSMThreads, MODE == kSortHash ? 3 : 5)
                     ok = 0;
                 }
             }
-            s_base = excl;
-            s_ok = ok;
+            *s_base = excl;
+            *s_ok = ok;
         }
     }
     __syncthreads();
-    if (!s_ok) return;
-    uint4 *__restrict__ out = reinterpret_cast<uint4 *>(d.t2) + s_base;
-    if (MODE == kSortEmit) {
-        // 9a. {a, b, 0, 0} records in (i, j) order; hashes come later
-        for (uint32_t r = threadIdx.x; r < n; r += NT) {
-            const uint32_t s0 = ST[r];
-            const uint32_t s1 = r + 1 < n ? ST[r + 1] : P;
-            const uint32_t a = SN[r];
-            for (uint32_t k = s0; k < s1; ++k) out[k] = make_uint4(a, SN[r + 1 + (k - s0)], 0u, 0u);
-        }
-        return;
-    }
-    // 9b. hash here: list the pairs window by window, every lane hashes
-    uint32_t g[16];
+    if (*s_ok) {
+        uint4 *__restrict__ out = reinterpret_cast<uint4 *>(d.t2) + *s_base;
+        if (MODE == kSortEmit) {
+            // 9a. {a, b, 0, 0} records in (i, j) order; hashes come later
+            for (uint32_t r = threadIdx.x; r < n; r += NT) {
+                const uint32_t s0 = ST[r];
+                const uint32_t s1 = r + 1 < n ? ST[r + 1] : P;
+                const uint32_t a = SN[r];
+                for (uint32_t k = s0; k < s1; ++k) out[k] = make_uint4(a, SN[r + 1 + (k - s0)], 0u, 0u);
+            }
+        } else {
+            // 9b. hash here: list the pairs window by window, every lane hashes
+            uint32_t g[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) g[i] = d.pre2[i];
-    for (uint32_t w0 = 0; w0 < P; w0 += kSMList) {
-        const uint32_t w1 = min(P, w0 + kSMList);
-        for (uint32_t r = threadIdx.x; r < n; r += NT) {
-            const uint32_t s = ST[r];
-            const uint32_t e = r + 1 < n ? ST[r + 1] : P;
-            const uint32_t lo = max(s, w0), hi = min(e, w1);
-            for (uint32_t k = lo; k < hi; ++k) LS[k - w0] = r | ((r + 1 + (k - s)) << 16);
+            for (int i = 0; i < 16; ++i) g[i] = d.pre2[i];
+            uint32_t *LS = A.LS;
+            for (uint32_t w0 = 0; w0 < P; w0 += kSMList) {
+                const uint32_t w1 = min(P, w0 + kSMList);
+                for (uint32_t r = threadIdx.x; r < n; r += NT) {
+                    const uint32_t s = ST[r];
+                    const uint32_t e = r + 1 < n ? ST[r + 1] : P;
+                    const uint32_t lo = max(s, w0), hi = min(e, w1);
+                    for (uint32_t k = lo; k < hi; ++k) LS[k - w0] = r | ((r + 1 + (k - s)) << 16);
+                }
+                __syncthreads();
+                for (uint32_t q = threadIdx.x; q < w1 - w0; q += NT) {
+                    const uint32_t e = LS[q];
+                    const uint32_t a = SN[e & 0xffffu], b = SN[e >> 16];
+                    uint32_t h0, h1;
+                    b3_finish<true>(g, a, b, h0, h1);
+                    out[w0 + q] = make_uint4(a, b, h0, h1);
+                }
+                __syncthreads();
+            }
         }
-        __syncthreads();
-        for (uint32_t q = threadIdx.x; q < w1 - w0; q += NT) {
-            const uint32_t e = LS[q];
-            const uint32_t a = SN[e & 0xffffu], b = SN[e >> 16];
-            uint32_t h0, h1;
-            b3_finish<true>(g, a, b, h0, h1);
-            out[w0 + q] = make_uint4(a, b, h0, h1);
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ Part part_arrays(unsigned char *base, const SMLayout &L)
+{
+    Part A;
+    A.SK = reinterpret_cast<uint64_t *>(base + L.sk);
+    A.SN = reinterpret_cast<uint32_t *>(base + L.sn);
+    A.DC = reinterpret_cast<uint32_t *>(base + L.dc);
+    A.ST = A.DC;  // overlays the digit counters (dead once the runs are sorted)
+    A.LS = reinterpret_cast<uint32_t *>(base + L.list);
+    A.WS = reinterpret_cast<uint32_t *>(base + L.ws);
+    return A;
+}
+
+struct SmemSrc {
+    const uint64_t *k;
+    const uint32_t *n;
+    __device__ __forceinline__ uint64_t key(uint32_t i) const { return k[i]; }
+    __device__ __forceinline__ uint32_t nonce(uint32_t i) const { return n[i]; }
+};
+
+// A slot in global memory, read through the read-only path unless this
+// kernel later overwrites it with the partition's pairs (RO false).
+template <bool RO>
+struct GlobalSrc {
+    const uint64_t *k;
+    const uint32_t *n;
+    __device__ __forceinline__ uint64_t key(uint32_t i) const { return RO ? __ldg(k + i) : k[i]; }
+    __device__ __forceinline__ uint32_t nonce(uint32_t i) const { return RO ? __ldg(n + i) : n[i]; }
+};
+
+// ------------------------------------------------- persistent front end
+// Work item t of the launch (CTA b takes b, b + G, b + 2G, ...) belongs to
+// plot find_plot(t); its partition is the plot's next ticket (look-back
+// modes) or t - tile_start[plot].  A CTA takes the ticket of item k + 2
+// and reads the fill count of item k + 1 at the start of item k, and
+// starts item k + 1's slot copy once item k's slot has been placed, so
+// the global round trips and the copy overlap item k's work.  A CTA takes
+// tickets in its processing order and only while running, so the lowest
+// unpublished partition is always being worked on: the look-back chain
+// cannot stall on a CTA that is not resident.
+struct Item {
+    int plot;
+    uint32_t f;
+    bool ok;
+};
+
+template <bool EMIT>
+__device__ __forceinline__ Item take_item(const Desc *__restrict__ descs, int nplots,
+                                          const uint32_t *__restrict__ tile_start, uint32_t t)
+{
+    Item it;
+    it.plot = find_plot(tile_start, nplots, t);
+    const Desc &d = descs[it.plot];
+    it.f = EMIT ? atomicAdd(d.ticket, 1u) : t - __ldg(tile_start + it.plot);
+    it.ok = true;
+    return it;
+}
+
+template <int MODE, bool HALO>
+__global__ void __launch_bounds__(kPipeThreads, MODE == kSortHash ? 2 : 3)
+    k_sortmatch_pipe(const Desc *__restrict__ descs, int nplots, const uint32_t *__restrict__ tile_start,
+                     uint32_t items, uint32_t max_cap, int max_dbits)
+{
+    constexpr bool EMIT = MODE == kSortHash || MODE == kSortEmit;
+    constexpr int NT = kPipeThreads;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_plot;
+    __shared__ uint32_t s_f, s_n;
+    __shared__ int s_valid;
+    __shared__ uint64_t s_base;
+    __shared__ int s_ok;
+    const SMLayout L(max_cap, max_dbits, MODE == kSortHash, true);
+    const Part A = part_arrays(smem_raw, L);
+    uint64_t *RK = reinterpret_cast<uint64_t *>(smem_raw + L.rk);
+    uint32_t *RN = reinterpret_cast<uint32_t *>(smem_raw + L.rn);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + L.bar);
+    const uint32_t G = gridDim.x;
+
+    // Thread 0's pipeline: the item after the current one (its ticket and,
+    // from the start of the current item on, its fill count) and the one
+    // after that (its ticket).
+    Item nx{0, 0, false}, nn{0, 0, false};
+    uint32_t nx_n = 0;
+    // Starts the copy of item `it` (n records) into the raw arrays and
+    // publishes it as the next item; an invalid or empty item completes the
+    // barrier phase with no copy.
+    auto launch_copy = [&](const Item &it, uint32_t n) {
+        // Only if the ticket was not reset: report, never index with it.
+        const bool valid = it.ok && it.f < (1u << descs[it.plot].p);
+        if (it.ok && !valid) atomicOr(descs[it.plot].status, kStBadTicket);
+        const uint32_t cnt = valid ? n : 0u;
+        const uint32_t nk = (cnt + 1u) & ~1u, nnz = (cnt + 3u) & ~3u;  // 16-byte multiples
+        // The raw arrays were last read by ordinary loads: order those before
+        // the copy engine's writes.
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar, nk * 8u + nnz * 4u);
+        if (cnt) {
+            const Desc &d = descs[it.plot];
+            bulk_g2s(RK, d.b_keys + (uint64_t)it.f * d.cap2, nk * 8u, bar);
+            bulk_g2s(RN, d.b_nonces + (uint64_t)it.f * d.cap2, nnz * 4u, bar);
         }
-        __syncthreads();
+        s_plot = it.plot;
+        s_f = it.f;
+        s_n = cnt;
+        s_valid = valid ? 1 : 0;
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        if (blockIdx.x < items) {
+            const Item i0 = take_item<EMIT>(descs, nplots, tile_start, blockIdx.x);
+            const uint32_t n0 = i0.f < (1u << descs[i0.plot].p) ? descs[i0.plot].cnt2[i0.f] : 0u;
+            if (blockIdx.x + G < items) nx = take_item<EMIT>(descs, nplots, tile_start, blockIdx.x + G);
+            launch_copy(i0, min(n0, descs[i0.plot].cap2));
+        }
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    for (uint32_t t = blockIdx.x; t < items; t += G, phase ^= 1u) {
+        const int plot = s_plot;
+        const uint32_t f = s_f, n = s_n;
+        const bool valid = s_valid != 0;
+        const Desc &d = descs[plot];
+        if (threadIdx.x == 0) {
+            if (nx.ok) {
+                const Desc &dn = descs[nx.plot];
+                nx_n = nx.f < (1u << dn.p) ? min(dn.cnt2[nx.f], dn.cap2) : 0u;
+            }
+            if (t + 2 * G < items) nn = take_item<EMIT>(descs, nplots, tile_start, t + 2 * G);
+        }
+        const uint32_t ndig = 1u << d.dbits;
+        for (uint32_t i = threadIdx.x; i < ndig; i += NT) A.DC[i] = 0u;
+        const uint64_t off = valid ? d.t1off[f] : 0ull;
+        // The slot copy was started during the previous item (or above).
+        if (!__syncthreads_and(mbar_wait(bar, phase, d.spin_limit))) {
+            if (threadIdx.x == 0) atomicOr(d.status, kStTimeout);
+            mbar_wait(bar, phase, d.spin_limit);  // let it land before the CTA exits
+            return;
+        }
+        if (valid) place_by_digit<NT>(A, n, 64 - d.pk - d.dbits, ndig, SmemSrc{RK, RN});
+        // The raw slot is dead: start the next item's copy into it.
+        if (threadIdx.x == 0) {
+            if (nx.ok) launch_copy(nx, nx_n);
+            nx = nn;
+            nn.ok = false;
+        }
+        if (valid) {
+            finish_partition<MODE, HALO, NT>(d, f, n, off, ndig, A, &s_base, &s_ok);
+        } else {
+            __syncthreads();
+        }
     }
 }
 
-size_t sortmatch_smem_bytes(uint32_t cap, int dbits) { return SMLayout(cap, dbits, true).bytes; }
+// ------------------------------------- one CTA per partition front end
+template <int MODE, bool HALO>
+__global__ void __launch_bounds__(kGlThreads, MODE == kSortHash ? 2 : 3)
+    k_sortmatch_gl(const Desc *__restrict__ descs, int nplots, const uint32_t *__restrict__ tile_start)
+{
+    constexpr bool EMIT = MODE == kSortHash || MODE == kSortEmit;
+    constexpr int NT = kGlThreads;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint32_t s_f;
+    __shared__ uint64_t s_base;
+    __shared__ int s_ok;
+    const int plot = find_plot(tile_start, nplots, blockIdx.x);
+    const Desc &d = descs[plot];
+    if (EMIT) {
+        if (threadIdx.x == 0) s_f = atomicAdd(d.ticket, 1u);
+        __syncthreads();
+    }
+    const uint32_t f = EMIT ? s_f : (blockIdx.x - tile_start[plot]);
+    if (f >= (1u << d.p)) {  // only if the ticket was not reset: report, never index with it
+        if (threadIdx.x == 0) atomicOr(d.status, kStBadTicket);
+        return;
+    }
+    const uint32_t cap = d.cap2;
+    const SMLayout L(cap + (HALO ? d.hcap : 0u), d.dbits, MODE == kSortHash, false);
+    const Part A = part_arrays(smem_raw, L);
+    const uint32_t ndig = 1u << d.dbits;
+    for (uint32_t i = threadIdx.x; i < ndig; i += NT) A.DC[i] = 0u;
+    // Warm L2 with the filled part of the slot kSlotPrefetchAhead tickets
+    // ahead, so that its CTA's reads hit L2.
+    const uint64_t fa = (uint64_t)f + kSlotPrefetchAhead;
+    if (threadIdx.x == 0 && fa < (1ull << d.p)) {
+        const uint32_t nfa = min(d.cnt2[fa], cap);
+        if (nfa) {
+            const uint32_t nk = (nfa + 1u) & ~1u, nn = (nfa + 3u) & ~3u;  // 16-byte multiples
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_keys + fa * cap),
+                         "r"(nk * 8u)
+                         : "memory");
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_nonces + fa * cap),
+                         "r"(nn * 4u)
+                         : "memory");
+        }
+    }
+    const uint32_t n = min(d.cnt2[f], cap);
+    const uint64_t off = d.t1off[f];
+    __syncthreads();
+    place_by_digit<NT>(A, n, 64 - d.pk - d.dbits, ndig,
+                       GlobalSrc<MODE != kSortSlots>{d.b_keys + (uint64_t)f * cap,
+                                                     d.b_nonces + (uint64_t)f * cap});
+    finish_partition<MODE, HALO, NT>(d, f, n, off, ndig, A, &s_base, &s_ok);
+}
+
+size_t sortmatch_smem_bytes(uint32_t cap, int dbits) { return SMLayout(cap, dbits, true, false).bytes; }
 
 uint32_t sortmatch_max_cap() { return 16384u; }
 
@@ -352,11 +529,26 @@ static cudaError_t launch_sm(const Desc *descs, int nplots, const uint32_t *tile
                              uint32_t total_tiles, cudaStream_t s, uint32_t max_cap, int max_dbits)
 {
     if (total_tiles == 0) return cudaSuccess;
-    const size_t smem = SMLayout(max_cap, max_dbits, MODE == kSortHash).bytes;
-    auto fn = k_sortmatch<MODE, HALO>;
+    const size_t pipe = SMLayout(max_cap, max_dbits, MODE == kSortHash, true).bytes;
+    if (pipe <= kMaxSmemPerCta) {
+        auto fn = k_sortmatch_pipe<MODE, HALO>;
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pipe);
+        if (e != cudaSuccess) return e;
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPipeThreads, pipe)) != cudaSuccess)
+            return e;
+        const uint64_t want = (uint64_t)(per_sm > 0 ? per_sm : 1) * (uint64_t)sms;
+        const uint32_t grid = (uint32_t)(want < total_tiles ? want : total_tiles);
+        fn<<<grid, kPipeThreads, pipe, s>>>(descs, nplots, tile_start, total_tiles, max_cap, max_dbits);
+        return cudaGetLastError();
+    }
+    const size_t smem = SMLayout(max_cap, max_dbits, MODE == kSortHash, false).bytes;
+    auto fn = k_sortmatch_gl<MODE, HALO>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<total_tiles, kSMThreads, smem, s>>>(descs, nplots, tile_start);
+    fn<<<total_tiles, kGlThreads, smem, s>>>(descs, nplots, tile_start);
     return cudaGetLastError();
 }
 

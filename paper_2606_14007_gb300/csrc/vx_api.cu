@@ -1046,6 +1046,19 @@ int vx_hash_nonces(const uint8_t key[32], uint64_t nonce0, uint64_t count, void 
     return e == cudaSuccess ? VX_OK : VX_ECUDA;
 }
 
+int vx_hash_peak(const uint8_t key[32], uint64_t nonce0, uint64_t count, void *d_fold,
+                 uint32_t fold_words, void *stream)
+{
+    if (!key || !d_fold || !aligned(d_fold, 4) || fold_words == 0 || fold_words % 256 != 0)
+        return VX_EINVAL;
+    if (count > (1ull << 32) || nonce0 + count > (1ull << 32)) return VX_EINVAL;
+    uint32_t w[8];
+    key_words(key, w);
+    cudaError_t e = vx::launch_hash_peak(w, nonce0, count, (uint32_t *)d_fold, fold_words / 256,
+                                         (cudaStream_t)stream);
+    return e == cudaSuccess ? VX_OK : VX_ECUDA;
+}
+
 int vx_pair_hash(const uint8_t key[32], const void *d_pairs, uint64_t count, void *d_out,
                  void *stream)
 {

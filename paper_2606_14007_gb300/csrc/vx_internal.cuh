@@ -560,6 +560,10 @@ cudaError_t launch_hash_records(const uint32_t key[8], uint64_t nonce0, uint64_t
                                 uint32_t *out, cudaStream_t s);
 cudaError_t launch_pair_hash(const uint32_t key[8], const uint32_t *pairs, uint64_t count,
                              uint4 *out, cudaStream_t s);
+// Hash-only ceiling: `blocks` CTAs of kHashThreads fold their hashes into
+// fold[blocks * kHashThreads].
+cudaError_t launch_hash_peak(const uint32_t key[8], uint64_t nonce0, uint64_t count, uint32_t *fold,
+                             uint32_t blocks, cudaStream_t s);
 size_t sort_smem_bytes(uint32_t cap, int dbits);
 size_t match_smem_bytes(uint32_t cap);
 constexpr int kHashThreads = 256;

@@ -116,6 +116,7 @@ def lib():
             "vx_plot_run_noalloc": (c_int, [c_int, u8p, P(vx_opts), vp, vp, u64, vp, P(u64)]),
             "vx_hash_nonces": (c_int, [u8p, u64, u64, vp, vp]),
             "vx_pair_hash": (c_int, [u8p, vp, u64, vp, vp]),
+            "vx_hash_peak": (c_int, [u8p, u64, u64, vp, u32, vp]),
             "vx_test_fail_next_allocs": (c_int, [c_int]),
             "vx_plot_profile": (c_int, [vp, c_int]),
             "vx_plot_profile_read": (c_int, [vp, P(ctypes.c_double), c_int, P(c_int), P(c_int)]),
@@ -407,6 +408,12 @@ def vx_plot_run_noalloc(K: int, key: bytes, d_t1: int, d_t2: int, t2_capacity: i
 def vx_hash_nonces(key: bytes, nonce0: int, count: int, d_out: int, stream=None):
     return _check(lib().vx_hash_nonces(_key(key), nonce0, count, d_out, _stream(stream)),
                   "vx_hash_nonces")
+
+
+def vx_hash_peak(key: bytes, nonce0: int, count: int, d_fold: int, fold_words: int, stream=None):
+    """Hash-only ceiling: count keyed hashes, folded per thread into d_fold."""
+    return _check(lib().vx_hash_peak(_key(key), nonce0, count, d_fold, fold_words, _stream(stream)),
+                  "vx_hash_peak")
 
 
 def vx_pair_hash(key: bytes, d_pairs: int, count: int, d_out: int, stream=None):

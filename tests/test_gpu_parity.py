@@ -62,6 +62,21 @@ def test_hash_row_matches_oracle(vx):
         assert np.array_equal(got, ref), (nonce0, count)
 
 
+def test_hash_peak_fold_matches_oracle(vx):
+    # The hash-only ceiling kernel hashes what it is asked to: the XOR of its
+    # per-thread folds is the XOR of h0 ^ h1 over every nonce, whatever the
+    # grid (its 2048-nonce tiles end in a ragged one here).
+    key = plot_key(4)
+    nonce0, count = 7000, 300001
+    ref = orc.hash_range(key, nonce0, nonce0 + count, threads=4)[:, 4:].copy().view("<u4")
+    want = int(np.bitwise_xor.reduce(ref[:, 0] ^ ref[:, 1]))
+    for blocks in (1, 3, 152):
+        fold = torch.zeros(256 * blocks, dtype=torch.int32, device="cuda")
+        vx.vx_hash_peak(key, nonce0, count, fold.data_ptr(), 256 * blocks)
+        got = int(np.bitwise_xor.reduce(fold.cpu().numpy().view(np.uint32)))
+        assert got == want, blocks
+
+
 def test_pair_hash_row_matches_oracle(vx):
     key = plot_key(4)
     rng = np.random.default_rng(5)

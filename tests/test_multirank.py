@@ -49,3 +49,34 @@ def test_single_rank_aggregate_has_no_collective():
     import bench
     value, ms_step = bench.aggregate(1 << 10, 4, 8.0, 1, "cpu")
     assert ms_step == 2.0 and value == pytest.approx((1 << 10) * 4 / 0.008)
+
+
+def test_launcher_starts_two_gloo_ranks(capfd):
+    # bench.spawn_ranks is the path `bench.py --gpus N` takes without an
+    # outer launcher: N ranks under torch.distributed.run on 127.0.0.1.
+    import json
+
+    import bench
+    child = os.path.join(os.path.dirname(os.path.abspath(__file__)), "rank_child.py")
+    rc = bench.spawn_ranks(2, [child])
+    out = capfd.readouterr().out
+    assert rc == 0, out
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["world"] == 2
+    assert d["ms_step"] == pytest.approx(250.0 / 5)
+    assert d["value"] == pytest.approx((1 << 20) * 5 * 2 / 0.25)
+
+
+def test_gpus_beyond_visible_devices_fails_loudly():
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    n = max(2, torch.cuda.device_count() + 1)
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--gpus", str(n),
+                        "--steps", "1", "--warmup", "3"], cwd=root, env=env,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0
+    assert "CUDA device" in r.stderr
