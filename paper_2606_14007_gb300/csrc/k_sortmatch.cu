@@ -6,21 +6,28 @@
 // K=31 bottleneck and proposes a parallel radix sort.  Kept here: the
 // fusion (a partition never leaves shared memory between sort and match).
 // Changed: a physical partition (a run of whole logical buckets, ~2048
-// records) per work item, a counting-sort pass on the key bits below the
-// partition prefix followed by per-digit insertion sorts (about one record
-// per digit), and the partition's Table-2 base found by a decoupled
-// look-back over the partitions before it (partition order comes from a
-// ticket counter, so every partition an item waits on is held by a running
-// CTA; every wait is bounded and a timeout poisons the chain instead of
-// hanging).  With the cross-bucket match (HALO instances) the next
-// partition's halo is sorted in behind the partition's records.
+// records) per work item, a counting sort on the key bits below the
+// partition prefix (about one record per digit) whose digit runs are then
+// ordered by (key64, nonce), and the partition's Table-2 base found by a
+// decoupled look-back over the partitions before it (partition order comes
+// from a ticket counter, so every partition an item waits on is held by a
+// running CTA; every wait is bounded and a timeout poisons the chain
+// instead of hanging).  With the cross-bucket match (HALO instances) the
+// next partition's halo is sorted in behind the partition's records.
 //
-// Two front ends feed the same per-partition steps:
+// After the sort every step walks the sorted records in chunks of 32, one
+// record per lane, each warp over its own run of chunks: the pair counts
+// (lanes probe the records after theirs), their warp scans, the Table-1
+// words (coalesced 4-byte stores) and the pair emission.  So no thread
+// walks a data-dependent list alone while its warp waits.
+//
+// Two front ends feed the same steps:
 //  * k_sortmatch_pipe (the default): persistent CTAs, three per SM at the
 //    default slot.  A CTA's next partition slot (keys and nonces, two
 //    contiguous runs) comes into shared memory by cp.async.bulk while the
-//    CTA sorts, matches and writes the current one, so no step waits on
-//    global memory: the slot lands during the previous item.
+//    CTA matches and writes the current one; the sort runs between two
+//    shared buffers, so a digit run is ordered by ranking its records, not
+//    by one thread's insertion sort.
 //  * k_sortmatch_gl: one CTA per partition reading its slot from global
 //    memory, for slots too large to hold twice in shared memory.
 //
@@ -41,6 +48,7 @@
 namespace vx {
 
 enum { kSortCount = 0, kSortHash = 1, kSortEmit = 2, kSortSlots = 3 };
+#define SLOTS_MODE(m) ((m) == kSortSlots)
 constexpr uint32_t kSMList = 2048;  // pair-list window (entries), kSortHash only
 constexpr int kPipeThreads = 256;   // persistent front end
 constexpr int kGlThreads = 256;     // one-CTA-per-partition front end
@@ -50,21 +58,25 @@ constexpr uint32_t kSlotPrefetchAhead = 384;
 
 // Shared layout (bytes from the base), for slots of at most `cap` records
 // (a multiple of 4) and digits of at most `dbits` bits:
-//   raw keys [cap] | raw nonces [cap]        (pipelined front end only)
-//   sorted key64 [cap] | sorted nonce [cap]
-//   digit counters [2^dbits], dead after the digit runs are sorted, then
-//   overlaid by the per-record pair count -> Table-2 offset [cap]
+//   buffer X: key64 [cap] | nonce [cap]
+//   buffer Y: key64 [cap] | nonce [cap]     (pipelined front end only)
+//   digit counters [2^dbits], dead once the digit runs are ordered, then
+//   overlaid by the per-record pair count -> pair offset [cap]
 //   pair list [kSMList] (kSortHash) | scan workspace | mbarrier
+// The pipelined front end alternates the two buffers: an item's slot lands
+// in one, is placed by digit into the other, and comes back sorted into the
+// first, so the second is free for the next item's slot while the first
+// holds the sorted partition.
 struct SMLayout {
-    size_t rk, rn, sk, sn, dc, list, ws, bar, bytes;
-    __host__ __device__ SMLayout(uint32_t cap, int dbits, bool with_list, bool with_raw)
+    size_t xk, xn, yk, yn, dc, list, ws, bar, bytes;
+    __host__ __device__ SMLayout(uint32_t cap, int dbits, bool with_list, bool two)
     {
         cap = (cap + 3u) & ~3u;
-        rk = 0;
-        rn = rk + (with_raw ? (size_t)cap * 8 : 0);
-        sk = rn + (with_raw ? (size_t)cap * 4 : 0);
-        sn = sk + (size_t)cap * 8;
-        dc = sn + (size_t)cap * 4;
+        xk = 0;
+        xn = xk + (size_t)cap * 8;
+        yk = xn + (size_t)cap * 4;
+        yn = yk + (two ? (size_t)cap * 8 : 0);
+        dc = yn + (two ? (size_t)cap * 4 : 0);
         const size_t dcb = ((size_t)1 << dbits) * 4, stb = (size_t)cap * 4;
         list = dc + (dcb > stb ? dcb : stb);
         ws = list + (with_list ? (size_t)kSMList * 4 : 0);
@@ -78,13 +90,121 @@ struct Part {
     uint32_t *SN, *DC, *ST, *LS, *WS;
 };
 
-// The partition's records, read from `src` (shared or global memory), go
-// into SK / SN grouped by digit (the next `dbits` key bits below the
-// partition prefix), in arbitrary order inside a digit; DC[g] ends as the
-// end of digit g's run.  Ends with a barrier.
+__device__ __forceinline__ bool rec_less(uint64_t ka, uint32_t na, uint64_t kb, uint32_t nb)
+{
+    return ka < kb || (ka == kb && na < nb);
+}
+
+// ---------------------------------------------------------------- sorts
+// Both leave the partition's n records sorted by (key64, nonce) in a
+// shared buffer.  DC (2^dbits zeroed counters) is the digit table; both
+// start after a barrier and end with one.
+
+// Inclusive scan of one u32 per lane.
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= (uint32_t)o) x += y;
+    }
+    return x;
+}
+
+// Exclusive scan of the M digit counters in place.  When M is 32 * NW * R'
+// with R' <= R (whole rows of 32 counters, the same number per warp), warp w scans its
+// R' rows of 32 counters as R' independent warp scans and adds the row and
+// warp prefixes; otherwise the general block scan.  Ends with a barrier.
+template <int NT, int R>
+__device__ __forceinline__ void counts_to_starts(uint32_t *DC, uint32_t M, uint32_t *WS)
+{
+    constexpr uint32_t NW = NT / 32;
+    if (M < 32u * NW || M > 32u * NW * R || M % (32u * NW) != 0) {
+        block_scan_inplace_u32<NT>(DC, M, WS);
+        return;
+    }
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t rows = M / (32u * NW);
+    uint32_t *row0 = DC + warp * rows * 32u + lane;
+    uint32_t v[R], incl[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[j] = (uint32_t)j < rows ? row0[32 * j] : 0u;
+#pragma unroll
+    for (int j = 0; j < R; ++j) incl[j] = warp_incl_scan(v[j]);
+    uint32_t run = 0;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const uint32_t t = __shfl_sync(0xffffffffu, incl[j], 31);
+        incl[j] += run - v[j];  // exclusive inside the warp's rows
+        run += t;
+    }
+    if (lane == 0) WS[warp] = run;
+    __syncthreads();
+    uint32_t carry = 0;
+#pragma unroll
+    for (uint32_t w = 0; w < NW; ++w) carry += w < warp ? WS[w] : 0u;
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+        if ((uint32_t)j < rows) row0[32 * j] = carry + incl[j];
+    __syncthreads();
+}
+
+// Ping-pong sort of the n records in buffer X (keys XK, nonces XN):
+// digit histogram, scan, then each record placed by digit into buffer Y (a
+// digit's run in arrival order); then every position of Y, 32 per warp
+// step, finds its record's rank inside its run (runs hold about one
+// record; a run of L compares L records) and writes the record to that
+// place of X.  X ends sorted, Y is free.
+template <int NT>
+__device__ __forceinline__ void sort_pingpong(const Part &A, uint64_t *XK, uint32_t *XN, uint64_t *YK,
+                                              uint32_t *YN, uint32_t n, int shift, uint32_t ndig)
+{
+    constexpr uint32_t NW = NT / 32;
+    const uint32_t dmask = ndig - 1u;
+#pragma unroll 4
+    for (uint32_t i = threadIdx.x; i < n; i += NT) atomicAdd(&A.DC[(uint32_t)(XK[i] >> shift) & dmask], 1u);
+    __syncthreads();
+    counts_to_starts<NT, 8>(A.DC, ndig, A.WS);
+#pragma unroll 4
+    for (uint32_t i = threadIdx.x; i < n; i += NT) {
+        const uint64_t k = XK[i];
+        const uint32_t pos = atomicAdd(&A.DC[(uint32_t)(k >> shift) & dmask], 1u);
+        YK[pos] = k;
+        YN[pos] = XN[i];
+    }
+    __syncthreads();
+    // DC[g] is now the end of run g: run g is [DC[g-1], DC[g])
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t nch = (n + 31u) >> 5;
+    for (uint32_t c = warp; c < nch; c += NW) {
+        const uint32_t p = 32u * c + lane;
+        if (p < n) {
+            const uint64_t k = YK[p];
+            const uint32_t nn = YN[p];
+            const uint32_t g = (uint32_t)(k >> shift) & dmask;
+            const uint32_t s = g ? A.DC[g - 1] : 0u;
+            const uint32_t e = A.DC[g];
+            uint32_t dst = s;
+            if (e - s == 2) {  // the most common run of more than one record
+                const uint32_t q = p == s ? s + 1 : s;
+                dst += rec_less(YK[q], YN[q], k, nn) ? 1u : 0u;
+            } else if (e - s > 2) {
+                for (uint32_t q = s; q < e; ++q) dst += rec_less(YK[q], YN[q], k, nn) ? 1u : 0u;
+            }
+            XK[dst] = k;
+            XN[dst] = nn;
+        }
+    }
+    __syncthreads();
+}
+
+// Generic sort (any n): records from `src` (global memory) go into SK / SN
+// grouped by digit, a digit's run in arrival order, then one thread per
+// digit finishes its run (about one record) by insertion sort.
 template <int NT, class Src>
-__device__ __forceinline__ void place_by_digit(const Part &A, uint32_t n, int shift, uint32_t ndig,
-                                               const Src &src)
+__device__ __forceinline__ void sort_generic(const Part &A, uint32_t n, int shift, uint32_t ndig,
+                                             const Src &src)
 {
     const uint32_t dmask = ndig - 1u;
     for (uint32_t i = threadIdx.x; i < n; i += NT) {
@@ -100,25 +220,9 @@ __device__ __forceinline__ void place_by_digit(const Part &A, uint32_t n, int sh
         A.SN[pos] = src.nonce(i);
     }
     __syncthreads();
-}
-
-// Everything after the placement, for partition f (n records, Table-1
-// offset `off`) of plot d: the digit runs sorted by (key64, nonce), the
-// next partition's halo (HALO), the pair counts and their scan, Table 1,
-// then the mode's Table-2 output.  Starts and ends at a barrier; returns
-// nothing on failure (the status word says why), so a persistent caller
-// goes on to its next item.
-template <int MODE, bool HALO, int NT>
-__device__ __forceinline__ void finish_partition(const Desc &d, uint32_t f, uint32_t n, uint64_t off,
-                                                 uint32_t ndig, const Part &A, uint64_t *s_base,
-                                                 int *s_ok)
-{
-    constexpr bool EMIT = MODE == kSortHash || MODE == kSortEmit;  // look-back placement
-    constexpr bool SLOTS = MODE == kSortSlots;
+    // DC[g] is now the end of run g, i.e. run g is [DC[g-1], DC[g])
     uint64_t *SK = A.SK;
     uint32_t *SN = A.SN;
-    // 4. finish every digit run (about one record each) by insertion sort on
-    //    (key64, nonce); run g is [DC[g-1], DC[g])
     for (uint32_t dg = threadIdx.x; dg < ndig; dg += NT) {
         const uint32_t s0 = dg ? A.DC[dg - 1] : 0u;
         const uint32_t s1 = A.DC[dg];
@@ -126,12 +230,9 @@ __device__ __forceinline__ void finish_partition(const Desc &d, uint32_t f, uint
             const uint64_t kx = SK[a];
             const uint32_t nx = SN[a];
             uint32_t b = a;
-            while (b > s0) {
-                const uint64_t ky = SK[b - 1];
-                const uint32_t ny = SN[b - 1];
-                if (ky < kx || (ky == kx && ny < nx)) break;
-                SK[b] = ky;
-                SN[b] = ny;
+            while (b > s0 && !rec_less(SK[b - 1], SN[b - 1], kx, nx)) {
+                SK[b] = SK[b - 1];
+                SN[b] = SN[b - 1];
                 --b;
             }
             SK[b] = kx;
@@ -139,10 +240,30 @@ __device__ __forceinline__ void finish_partition(const Desc &d, uint32_t f, uint
         }
     }
     __syncthreads();
-    // 4b. cross-bucket match: the next partition's halo (its records within
-    //     D of its lower edge, collected while the slots were filled) goes
-    //     sorted right after this partition's records, so the pair scan
-    //     below runs on into it; records n .. nt - 1 start no pairs here.
+}
+
+// ------------------------------------------------ match and the tables
+
+// Everything after the sort, for partition f (n sorted records, Table-1
+// offset `off`) of plot d: the next partition's halo (HALO), the pair
+// counts and their scan, Table 1, then the mode's Table-2 output.  Starts
+// and ends at a barrier; on failure (the status word says why) it skips
+// the output, so a persistent caller goes on to its next item.
+template <int MODE, bool HALO, int NT>
+__device__ __forceinline__ void match_and_write(const Desc &d, uint32_t f, uint32_t n, uint64_t off,
+                                                const Part &A, uint64_t *s_base, int *s_ok)
+{
+    constexpr bool EMIT = MODE == kSortHash || MODE == kSortEmit;  // look-back placement
+    constexpr bool SLOTS = MODE == kSortSlots;
+    constexpr uint32_t NW = NT / 32;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint64_t *SK = A.SK;
+    uint32_t *SN = A.SN;
+    uint32_t *ST = A.ST;  // overlays the dead digit counters
+    // 1. cross-bucket match: the next partition's halo (its records within
+    //    D of its lower edge, collected while the slots were filled) goes
+    //    sorted right after this partition's records, so the pair scan
+    //    below runs on into it; records n .. nt - 1 start no pairs here.
     uint32_t nt = n;
     if (HALO && d.hcap) {
         const uint32_t hcap = d.hcap;
@@ -158,7 +279,7 @@ __device__ __forceinline__ void finish_partition(const Desc &d, uint32_t f, uint
                 const uint64_t kx = SK[a];
                 const uint32_t nx = SN[a];
                 uint32_t b = a;
-                for (; b > n && (SK[b - 1] > kx || (SK[b - 1] == kx && SN[b - 1] > nx)); --b) {
+                for (; b > n && !rec_less(SK[b - 1], SN[b - 1], kx, nx); --b) {
                     SK[b] = SK[b - 1];
                     SN[b] = SN[b - 1];
                 }
@@ -169,149 +290,152 @@ __device__ __forceinline__ void finish_partition(const Desc &d, uint32_t f, uint
         __syncthreads();
         nt = n + hc;
     }
-    // 5. pairs starting at each record r: the later records up to
-    //    lim = min(last key of r's logical bucket, key_r + D - 1), or
-    //    key_r + D - 1 for the cross-bucket match; four probes per step
-    //    (key64 sorted ascending).  ST overlays the dead digit counters.
-    uint32_t *ST = A.ST;
+    // 2. per chunk of 32 sorted records (one per lane; warp w takes chunks
+    //    [c0, c1)): the pairs starting at each record r, i.e. the later
+    //    records up to lim = min(last key of r's logical bucket,
+    //    key_r + D - 1), or key_r + D - 1 for the cross-bucket match, four
+    //    probes per step; and the lane's Table-1 record {nonce, BE key64},
+    //    three 4-byte stores (a warp's stores cover its chunk's 384 bytes).
+    const uint32_t nch = (n + 31u) >> 5;
+    const uint32_t c0 = warp * nch / NW, c1 = (warp + 1) * nch / NW;
     const uint64_t D = d.D;
     const bool global = HALO && d.scope != 0;
-    for (uint32_t r = threadIdx.x; r < n; r += NT) {
-        const uint64_t k = SK[r];
-        const uint64_t last_in_bucket = global ? ~0ull : (k | ((1ull << 40) - 1));
-        uint64_t reach = k + (D - 1);
-        if (reach < k) reach = ~0ull;  // saturate
-        const uint64_t lim = reach < last_in_bucket ? reach : last_in_bucket;
-        uint32_t c = 0;
-        for (uint32_t q = r + 1; q < nt; q += 4) {
-            const bool m0 = SK[q] <= lim;
-            const bool m1 = m0 && q + 1 < nt && SK[q + 1] <= lim;
-            const bool m2 = m1 && q + 2 < nt && SK[q + 2] <= lim;
-            const bool m3 = m2 && q + 3 < nt && SK[q + 3] <= lim;
-            c += (uint32_t)m0 + (uint32_t)m1 + (uint32_t)m2 + (uint32_t)m3;
-            if (!m3) break;
+    uint32_t *__restrict__ t1w = reinterpret_cast<uint32_t *>(d.t1) + 3 * off;
+    uint32_t wsum = 0;
+    for (uint32_t c = c0; c < c1; ++c) {
+        const uint32_t r = 32u * c + lane;
+        uint32_t cnt = 0;
+        if (r < n) {
+            const uint64_t k = SK[r];
+            t1w[3u * r] = SN[r];
+            t1w[3u * r + 1] = bswap32((uint32_t)(k >> 32));
+            t1w[3u * r + 2] = bswap32((uint32_t)k);
+            const uint64_t last_in_bucket = global ? ~0ull : (k | ((1ull << 40) - 1));
+            uint64_t reach = k + (D - 1);
+            if (reach < k) reach = ~0ull;  // saturate
+            const uint64_t lim = reach < last_in_bucket ? reach : last_in_bucket;
+            for (uint32_t q = r + 1; q < nt; q += 4) {
+                const bool m0 = SK[q] <= lim;
+                const bool m1 = m0 && q + 1 < nt && SK[q + 1] <= lim;
+                const bool m2 = m1 && q + 2 < nt && SK[q + 2] <= lim;
+                const bool m3 = m2 && q + 3 < nt && SK[q + 3] <= lim;
+                cnt += (uint32_t)m0 + (uint32_t)m1 + (uint32_t)m2 + (uint32_t)m3;
+                if (!m3) break;
+            }
+            ST[r] = cnt;
         }
-        ST[r] = c;
+        wsum += __reduce_add_sync(0xffffffffu, cnt);
     }
+    if (lane == 0) A.WS[warp] = wsum;
     __syncthreads();
-    // 6. counts -> per-record Table-2 offsets; the partition's pair count
-    //    is published at once so later partitions are not held up
-    const uint32_t P = block_scan_inplace_u32<NT>(ST, n, A.WS);
+    uint32_t P = 0, carry = 0;  // the partition's pairs; those before this warp's chunks
+#pragma unroll
+    for (uint32_t w = 0; w < NW; ++w) {
+        const uint32_t t = A.WS[w];
+        carry += w < warp ? t : 0u;
+        P += t;
+    }
     const bool withhold = (d.test_flags & 1u) != 0;
     if (threadIdx.x == 0) {
         d.pairs[f] = P;  // lets vx_match re-run the match alone
         if (EMIT) lb_publish(d.lb, f, P, withhold);
     }
-    // 7. Table 1, 12-byte records {nonce, BE key64}: thread q writes output
-    //    words 4q .. 4q + 3 (one 16-byte store; a word is record w / 3,
-    //    field w % 3), so lanes read neighbouring records of SK / SN; the
-    //    words before the first 16-byte boundary and after the last one go
-    //    singly.
-    {
-        uint32_t *__restrict__ t1w = reinterpret_cast<uint32_t *>(d.t1) + 3 * off;
-        const uint32_t nw = 3u * n;
-        const uint32_t head = min(nw, (uint32_t)((4u - (uint32_t)((3u * off) & 3u)) & 3u));
-        const uint32_t body = (nw - head) >> 2;  // 16-byte chunks
-        const uint32_t tail0 = head + 4u * body;
-        auto word = [&](uint32_t w) -> uint32_t {
-            const uint32_t r = w / 3u, c = w - 3u * r;
-            if (c == 0) return SN[r];
-            const uint64_t k = SK[r];
-            return bswap32(c == 1 ? (uint32_t)(k >> 32) : (uint32_t)k);
-        };
-        for (uint32_t w = threadIdx.x; w < head + (nw - tail0); w += NT) {
-            const uint32_t ww = w < head ? w : tail0 + (w - head);
-            t1w[ww] = word(ww);
-        }
-        uint4 *__restrict__ t1v = reinterpret_cast<uint4 *>(t1w + head);
-        for (uint32_t q = threadIdx.x; q < body; q += NT) {
-            const uint32_t w = head + 4u * q;
-            t1v[q] = make_uint4(word(w), word(w + 1), word(w + 2), word(w + 3));
-        }
+    if (MODE == kSortCount) {
+        __syncthreads();
+        return;
     }
-    if (SLOTS) {
-        // 8. pairs into the slot (its records were read before the
-        //    barriers above)
-        const uint32_t cap = d.cap2;
-        const uint32_t capA = cap, capB = cap / 2u;
-        if (P > capA + capB) {
-            if (threadIdx.x == 0) atomicOr(d.status, kStPairSlot);
-        } else {
-            uint2 *__restrict__ pa = reinterpret_cast<uint2 *>(d.b_keys + (uint64_t)f * cap);
-            uint2 *__restrict__ pb = reinterpret_cast<uint2 *>(d.b_nonces + (uint64_t)f * cap);
-            for (uint32_t r = threadIdx.x; r < n; r += NT) {
-                const uint32_t s0 = ST[r];
-                const uint32_t s1 = r + 1 < n ? ST[r + 1] : P;
-                const uint32_t a = SN[r];
-                for (uint32_t k = s0; k < s1; ++k) {
-                    const uint2 v = make_uint2(a, SN[r + 1 + (k - s0)]);
-                    if (k < capA)
-                        pa[k] = v;
+    // 3. the Table-2 base: the look-back (warp 0), or the partition's slot
+    bool ok = true;
+    uint64_t base = 0;
+    if (EMIT) {
+        if (threadIdx.x < 32) {
+            uint64_t excl = 0;
+            int got = lb_resolve(d.lb, f, P, d.status, d.spin_limit, withhold, &excl) ? 1 : 0;
+            if (threadIdx.x == 0) {
+                if (got) {
+                    const uint64_t np = 1ull << d.p;
+                    d.t2off[f] = excl;
+                    if (f + 1 == np) d.t2off[np] = excl + P;
+                    if (excl + P > d.t2cap) {
+                        atomicOr(d.status, kStT2Capacity);
+                        got = 0;
+                    }
+                }
+                *s_base = excl;
+                *s_ok = got;
+            }
+        }
+        __syncthreads();
+        ok = *s_ok != 0;
+        base = *s_base;
+    } else if (P > d.cap2 + d.cap2 / 2u) {
+        if (threadIdx.x == 0) atomicOr(d.status, kStPairSlot);
+        ok = false;
+    }
+    // 4. the pairs, in (i, j) order: chunk by chunk, a lane's record r
+    //    starts its cnt pairs (r, r + 1 + j) at its scanned offset.  Slot
+    //    placement: when the pairs fit the key array of shared memory (dead
+    //    since step 2) they are listed there and leave in one bulk copy
+    //    (thread 0's bulk group; the caller waits for its read before the
+    //    buffer is written again), else they go straight to the slot.
+    uint4 *__restrict__ out = reinterpret_cast<uint4 *>(d.t2) + base;
+    uint2 *__restrict__ pa = reinterpret_cast<uint2 *>(d.b_keys + (uint64_t)f * d.cap2);
+    uint2 *__restrict__ pb = reinterpret_cast<uint2 *>(d.b_nonces + (uint64_t)f * d.cap2);
+    const uint32_t capA = d.cap2;
+    const bool staged = SLOTS && P < capA;
+    uint2 *SP = reinterpret_cast<uint2 *>(SK);
+    if (ok) {
+        for (uint32_t c = c0; c < c1; ++c) {
+            const uint32_t r = 32u * c + lane;
+            const uint32_t cnt = r < n ? ST[r] : 0u;
+            const uint32_t incl = warp_incl_scan(cnt);
+            const uint32_t at = carry + incl - cnt;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+            if (MODE == kSortHash) {
+                if (r < n) ST[r] = at;  // offsets for the listing below
+                continue;
+            }
+            const uint32_t a = r < n ? SN[r] : 0u;
+            for (uint32_t j = 0; __any_sync(0xffffffffu, j < cnt); ++j) {
+                if (j < cnt) {
+                    const uint32_t b = SN[r + 1 + j];
+                    const uint32_t x = at + j;
+                    if (SLOTS)
+                        *(staged ? SP + x : x < capA ? pa + x : pb + (x - capA)) = make_uint2(a, b);
                     else
-                        pb[k - capA] = v;
+                        out[x] = make_uint4(a, b, 0u, 0u);
                 }
             }
         }
-        __syncthreads();
-        return;
-    }
-    if (!EMIT) {
-        __syncthreads();
-        return;
-    }
-    // 8. Table-2 base: resolve the look-back (warp 0)
-    const uint64_t np = 1ull << d.p;
-    if (threadIdx.x < 32) {
-        uint64_t excl = 0;
-        int ok = lb_resolve(d.lb, f, P, d.status, d.spin_limit, withhold, &excl) ? 1 : 0;
-        if (threadIdx.x == 0) {
-            if (ok) {
-                d.t2off[f] = excl;
-                if (f + 1 == np) d.t2off[np] = excl + P;
-                if (excl + P > d.t2cap) {
-                    atomicOr(d.status, kStT2Capacity);
-                    ok = 0;
-                }
-            }
-            *s_base = excl;
-            *s_ok = ok;
+        if (staged) {
+            __syncthreads();
+            if (threadIdx.x == 0 && P) bulk_s2g(pa, SP, ((P + 1u) & ~1u) * 8u);
         }
     }
-    __syncthreads();
-    if (*s_ok) {
-        uint4 *__restrict__ out = reinterpret_cast<uint4 *>(d.t2) + *s_base;
-        if (MODE == kSortEmit) {
-            // 9a. {a, b, 0, 0} records in (i, j) order; hashes come later
-            for (uint32_t r = threadIdx.x; r < n; r += NT) {
-                const uint32_t s0 = ST[r];
-                const uint32_t s1 = r + 1 < n ? ST[r + 1] : P;
-                const uint32_t a = SN[r];
-                for (uint32_t k = s0; k < s1; ++k) out[k] = make_uint4(a, SN[r + 1 + (k - s0)], 0u, 0u);
-            }
-        } else {
-            // 9b. hash here: list the pairs window by window, every lane hashes
-            uint32_t g[16];
+    if (MODE == kSortHash && ok) {
+        // hash here: list the pairs window by window, every lane hashes
+        __syncthreads();
+        uint32_t g[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i) g[i] = d.pre2[i];
-            uint32_t *LS = A.LS;
-            for (uint32_t w0 = 0; w0 < P; w0 += kSMList) {
-                const uint32_t w1 = min(P, w0 + kSMList);
-                for (uint32_t r = threadIdx.x; r < n; r += NT) {
-                    const uint32_t s = ST[r];
-                    const uint32_t e = r + 1 < n ? ST[r + 1] : P;
-                    const uint32_t lo = max(s, w0), hi = min(e, w1);
-                    for (uint32_t k = lo; k < hi; ++k) LS[k - w0] = r | ((r + 1 + (k - s)) << 16);
-                }
-                __syncthreads();
-                for (uint32_t q = threadIdx.x; q < w1 - w0; q += NT) {
-                    const uint32_t e = LS[q];
-                    const uint32_t a = SN[e & 0xffffu], b = SN[e >> 16];
-                    uint32_t h0, h1;
-                    b3_finish<true>(g, a, b, h0, h1);
-                    out[w0 + q] = make_uint4(a, b, h0, h1);
-                }
-                __syncthreads();
+        for (int i = 0; i < 16; ++i) g[i] = d.pre2[i];
+        uint32_t *LS = A.LS;
+        for (uint32_t w0 = 0; w0 < P; w0 += kSMList) {
+            const uint32_t w1 = min(P, w0 + kSMList);
+            for (uint32_t r = threadIdx.x; r < n; r += NT) {
+                const uint32_t s = ST[r];
+                const uint32_t e = r + 1 < n ? ST[r + 1] : P;
+                const uint32_t lo = max(s, w0), hi = min(e, w1);
+                for (uint32_t k = lo; k < hi; ++k) LS[k - w0] = r | ((r + 1 + (k - s)) << 16);
             }
+            __syncthreads();
+            for (uint32_t q = threadIdx.x; q < w1 - w0; q += NT) {
+                const uint32_t e = LS[q];
+                const uint32_t a = SN[e & 0xffffu], b = SN[e >> 16];
+                uint32_t h0, h1;
+                b3_finish<true>(g, a, b, h0, h1);
+                out[w0 + q] = make_uint4(a, b, h0, h1);
+            }
+            __syncthreads();
         }
     }
     __syncthreads();
@@ -320,21 +444,14 @@ __device__ __forceinline__ void finish_partition(const Desc &d, uint32_t f, uint
 __device__ __forceinline__ Part part_arrays(unsigned char *base, const SMLayout &L)
 {
     Part A;
-    A.SK = reinterpret_cast<uint64_t *>(base + L.sk);
-    A.SN = reinterpret_cast<uint32_t *>(base + L.sn);
+    A.SK = reinterpret_cast<uint64_t *>(base + L.xk);
+    A.SN = reinterpret_cast<uint32_t *>(base + L.xn);
     A.DC = reinterpret_cast<uint32_t *>(base + L.dc);
     A.ST = A.DC;  // overlays the digit counters (dead once the runs are sorted)
     A.LS = reinterpret_cast<uint32_t *>(base + L.list);
     A.WS = reinterpret_cast<uint32_t *>(base + L.ws);
     return A;
 }
-
-struct SmemSrc {
-    const uint64_t *k;
-    const uint32_t *n;
-    __device__ __forceinline__ uint64_t key(uint32_t i) const { return k[i]; }
-    __device__ __forceinline__ uint32_t nonce(uint32_t i) const { return n[i]; }
-};
 
 // A slot in global memory, read through the read-only path unless this
 // kernel later overwrites it with the partition's pairs (RO false).
@@ -351,11 +468,11 @@ struct GlobalSrc {
 // plot find_plot(t); its partition is the plot's next ticket (look-back
 // modes) or t - tile_start[plot].  A CTA takes the ticket of item k + 2
 // and reads the fill count of item k + 1 at the start of item k, and
-// starts item k + 1's slot copy once item k's slot has been placed, so
-// the global round trips and the copy overlap item k's work.  A CTA takes
-// tickets in its processing order and only while running, so the lowest
-// unpublished partition is always being worked on: the look-back chain
-// cannot stall on a CTA that is not resident.
+// starts item k + 1's slot copy once item k's slot has been sorted into
+// registers, so the global round trips and the copy overlap item k's work.
+// A CTA takes tickets in its processing order and only while running, so
+// the lowest unpublished partition is always being worked on: the
+// look-back chain cannot stall on a CTA that is not resident.
 struct Item {
     int plot;
     uint32_t f;
@@ -388,9 +505,11 @@ __global__ void __launch_bounds__(kPipeThreads, MODE == kSortHash ? 2 : 3)
     __shared__ uint64_t s_base;
     __shared__ int s_ok;
     const SMLayout L(max_cap, max_dbits, MODE == kSortHash, true);
-    const Part A = part_arrays(smem_raw, L);
-    uint64_t *RK = reinterpret_cast<uint64_t *>(smem_raw + L.rk);
-    uint32_t *RN = reinterpret_cast<uint32_t *>(smem_raw + L.rn);
+    Part A = part_arrays(smem_raw, L);
+    uint64_t *const XK = reinterpret_cast<uint64_t *>(smem_raw + L.xk);
+    uint32_t *const XN = reinterpret_cast<uint32_t *>(smem_raw + L.xn);
+    uint64_t *const YK = reinterpret_cast<uint64_t *>(smem_raw + L.yk);
+    uint32_t *const YN = reinterpret_cast<uint32_t *>(smem_raw + L.yn);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + L.bar);
     const uint32_t G = gridDim.x;
 
@@ -399,23 +518,23 @@ __global__ void __launch_bounds__(kPipeThreads, MODE == kSortHash ? 2 : 3)
     // after that (its ticket).
     Item nx{0, 0, false}, nn{0, 0, false};
     uint32_t nx_n = 0;
-    // Starts the copy of item `it` (n records) into the raw arrays and
-    // publishes it as the next item; an invalid or empty item completes the
-    // barrier phase with no copy.
-    auto launch_copy = [&](const Item &it, uint32_t n) {
+    // Starts the copy of item `it` (n records) into buffer b and publishes
+    // it as the next item; an invalid or empty item completes the barrier
+    // phase with no copy.
+    auto launch_copy = [&](const Item &it, uint32_t n, int b) {
         // Only if the ticket was not reset: report, never index with it.
         const bool valid = it.ok && it.f < (1u << descs[it.plot].p);
         if (it.ok && !valid) atomicOr(descs[it.plot].status, kStBadTicket);
         const uint32_t cnt = valid ? n : 0u;
         const uint32_t nk = (cnt + 1u) & ~1u, nnz = (cnt + 3u) & ~3u;  // 16-byte multiples
-        // The raw arrays were last read by ordinary loads: order those before
-        // the copy engine's writes.
+        // The buffer was last accessed by ordinary loads and stores: order
+        // those before the copy engine's writes.
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(bar, nk * 8u + nnz * 4u);
         if (cnt) {
             const Desc &d = descs[it.plot];
-            bulk_g2s(RK, d.b_keys + (uint64_t)it.f * d.cap2, nk * 8u, bar);
-            bulk_g2s(RN, d.b_nonces + (uint64_t)it.f * d.cap2, nnz * 4u, bar);
+            bulk_g2s(b ? YK : XK, d.b_keys + (uint64_t)it.f * d.cap2, nk * 8u, bar);
+            bulk_g2s(b ? YN : XN, d.b_nonces + (uint64_t)it.f * d.cap2, nnz * 4u, bar);
         }
         s_plot = it.plot;
         s_f = it.f;
@@ -428,12 +547,13 @@ __global__ void __launch_bounds__(kPipeThreads, MODE == kSortHash ? 2 : 3)
             const Item i0 = take_item<EMIT>(descs, nplots, tile_start, blockIdx.x);
             const uint32_t n0 = i0.f < (1u << descs[i0.plot].p) ? descs[i0.plot].cnt2[i0.f] : 0u;
             if (blockIdx.x + G < items) nx = take_item<EMIT>(descs, nplots, tile_start, blockIdx.x + G);
-            launch_copy(i0, min(n0, descs[i0.plot].cap2));
+            launch_copy(i0, min(n0, descs[i0.plot].cap2), 0);
         }
     }
     __syncthreads();
     uint32_t phase = 0;
-    for (uint32_t t = blockIdx.x; t < items; t += G, phase ^= 1u) {
+    int rb = 0;  // buffer holding the current item's slot, then its sorted records
+    for (uint32_t t = blockIdx.x; t < items; t += G, phase ^= 1u, rb ^= 1) {
         const int plot = s_plot;
         const uint32_t f = s_f, n = s_n;
         const bool valid = s_valid != 0;
@@ -446,27 +566,38 @@ __global__ void __launch_bounds__(kPipeThreads, MODE == kSortHash ? 2 : 3)
             if (t + 2 * G < items) nn = take_item<EMIT>(descs, nplots, tile_start, t + 2 * G);
         }
         const uint32_t ndig = 1u << d.dbits;
-        for (uint32_t i = threadIdx.x; i < ndig; i += NT) A.DC[i] = 0u;
+        if (ndig % 4u == 0) {
+            uint4 *D4 = reinterpret_cast<uint4 *>(A.DC);
+            for (uint32_t i = threadIdx.x; i < ndig / 4u; i += NT) D4[i] = make_uint4(0u, 0u, 0u, 0u);
+        } else {
+            for (uint32_t i = threadIdx.x; i < ndig; i += NT) A.DC[i] = 0u;
+        }
         const uint64_t off = valid ? d.t1off[f] : 0ull;
+        // The previous item's staged pairs must have left the buffer this
+        // item places its records into.
+        if (SLOTS_MODE(MODE) && threadIdx.x == 0) bulk_wait_all<true>();
         // The slot copy was started during the previous item (or above).
         if (!__syncthreads_and(mbar_wait(bar, phase, d.spin_limit))) {
             if (threadIdx.x == 0) atomicOr(d.status, kStTimeout);
             mbar_wait(bar, phase, d.spin_limit);  // let it land before the CTA exits
             return;
         }
-        if (valid) place_by_digit<NT>(A, n, 64 - d.pk - d.dbits, ndig, SmemSrc{RK, RN});
-        // The raw slot is dead: start the next item's copy into it.
+        A.SK = rb ? YK : XK;
+        A.SN = rb ? YN : XN;
+        if (valid) sort_pingpong<NT>(A, A.SK, A.SN, rb ? XK : YK, rb ? XN : YN, n, 64 - d.pk - d.dbits, ndig);
+        // The other buffer is free: start the next item's copy into it.
         if (threadIdx.x == 0) {
-            if (nx.ok) launch_copy(nx, nx_n);
+            if (nx.ok) launch_copy(nx, nx_n, rb ^ 1);
             nx = nn;
             nn.ok = false;
         }
         if (valid) {
-            finish_partition<MODE, HALO, NT>(d, f, n, off, ndig, A, &s_base, &s_ok);
+            match_and_write<MODE, HALO, NT>(d, f, n, off, A, &s_base, &s_ok);
         } else {
             __syncthreads();
         }
     }
+    if (SLOTS_MODE(MODE) && threadIdx.x == 0) bulk_wait_all<false>();
 }
 
 // ------------------------------------- one CTA per partition front end
@@ -514,10 +645,10 @@ __global__ void __launch_bounds__(kGlThreads, MODE == kSortHash ? 2 : 3)
     const uint32_t n = min(d.cnt2[f], cap);
     const uint64_t off = d.t1off[f];
     __syncthreads();
-    place_by_digit<NT>(A, n, 64 - d.pk - d.dbits, ndig,
-                       GlobalSrc<MODE != kSortSlots>{d.b_keys + (uint64_t)f * cap,
-                                                     d.b_nonces + (uint64_t)f * cap});
-    finish_partition<MODE, HALO, NT>(d, f, n, off, ndig, A, &s_base, &s_ok);
+    sort_generic<NT>(A, n, 64 - d.pk - d.dbits, ndig,
+                     GlobalSrc<MODE != kSortSlots>{d.b_keys + (uint64_t)f * cap, d.b_nonces + (uint64_t)f * cap});
+    match_and_write<MODE, HALO, NT>(d, f, n, off, A, &s_base, &s_ok);
+    if (SLOTS_MODE(MODE) && threadIdx.x == 0) bulk_wait_all<false>();
 }
 
 size_t sortmatch_smem_bytes(uint32_t cap, int dbits) { return SMLayout(cap, dbits, true, false).bytes; }

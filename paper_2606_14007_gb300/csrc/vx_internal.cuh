@@ -474,6 +474,29 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// Bulk shared -> global copy (addresses 16-byte aligned, bytes % 16 == 0)
+// in the issuing thread's bulk group; the thread first makes the CTA's
+// ordinary shared-memory writes visible to the copy engine.
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                 "r"(smem_u32(src)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// Waits until the issuing thread's bulk copies have read their shared
+// memory (READ) or are complete.
+template <bool READ>
+__device__ __forceinline__ void bulk_wait_all()
+{
+    if (READ)
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    else
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 // Waits for phase `parity` of the mbarrier; gives up after `limit` polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit)
 {

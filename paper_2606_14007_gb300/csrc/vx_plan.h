@@ -224,10 +224,13 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     P.dbits = db;
     P.agg = (P.p2 > 0 ? P.p1 : P.p) <= kAggMaxBits;
 
-    // Table-2 placement.  Automatic = look-back: measured on GB300 at K=31
-    // the slot placement's sort runs slower (its slot reads cannot take the
-    // read-only path, and the look-back waits it removes were already hidden
-    // by the other resident CTAs), 164.3 vs 162.2 ms per plot.
+    // Table-2 placement: look-back (pairs at their final offsets, each
+    // partition waiting for the pair counts of the ones before it) or slots
+    // (pairs staged in the partition's own slot, no waits, a scan and the
+    // slot pair hash place them).  Automatic takes the slots whenever a
+    // partition's pairs fit its pair slot with a wide margin (decided below,
+    // once the expected pair count is known): the slots move 8 bytes per
+    // pair less each way and the sort never waits on another partition.
     if (opts.t2_placement > kPlaceSlots) {
         *why = "t2_placement must be 0 (auto), 1 (look-back) or 2 (slots)";
         return VX_EINVAL;
@@ -261,12 +264,18 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
         P.hcap = (uint32_t)hc;
     }
 
+    const double E = (P.scope ? expected_pairs_global(P.N, P.D) : expected_pairs(P.N, P.D)) /
+                     std::ldexp(1.0, (int)P.wbits);
     if (opts.t2_capacity) {
         P.t2cap = opts.t2_capacity;
     } else {
-        const double E = (P.scope ? expected_pairs_global(P.N, P.D) : expected_pairs(P.N, P.D)) /
-                         std::ldexp(1.0, (int)P.wbits);
         P.t2cap = round_up((uint64_t)std::ceil(E + 24.0 * std::sqrt(E) + 4096.0), 256);
+    }
+    if (opts.t2_placement == kPlaceAuto && !P.fuse_pair_hash && P.pchunks == 1) {
+        // A partition's pairs sum over its buckets' pairs, more spread than
+        // Poisson: the margin takes 12 sigma of a variance four times the mean.
+        const double Ep = E / std::ldexp(1.0, P.p);
+        P.pair_slots = Ep + 12.0 * std::sqrt(4.0 * Ep) + 64.0 <= (double)(P.cap2 + P.cap2 / 2u);
     }
     // Grids (tile sizes are the kernels' compile-time tiles).
     // Grids per chunk (a chunk of the hash covers 2^K / hchunks nonces).

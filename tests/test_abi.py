@@ -113,14 +113,24 @@ def test_create_and_destroy_without_device(vx):
 
 
 def test_kernel_mask_follows_plan(vx):
-    h = vx.vx_plot_create(31, bytes(32))
-    assert vx.vx_plot_kernel_mask(h) == ["key_setup", "hash_staged", "scatter2", "scan_counts",
-                                         "sortmatch", "pairhash"]
+    slots = ["key_setup", "hash_staged", "scatter2", "scan_counts", "scan_pairs", "sortmatch",
+             "pairhash"]
+    lookback = ["key_setup", "hash_staged", "scatter2", "scan_counts", "sortmatch", "pairhash"]
+    h = vx.vx_plot_create(31, bytes(32), vx.make_opts(t2_placement=1))
+    assert vx.vx_plot_kernel_mask(h) == lookback
     vx.vx_plot_destroy(h)
     h = vx.vx_plot_create(31, bytes(32), vx.make_opts(t2_placement=2))
-    assert vx.vx_plot_kernel_mask(h) == ["key_setup", "hash_staged", "scatter2", "scan_counts",
-                                         "scan_pairs", "sortmatch", "pairhash"]
+    assert vx.vx_plot_kernel_mask(h) == slots
     vx.vx_plot_destroy(h)
+    # automatic: the pair slots while a partition's expected pairs fit them
+    # with a wide margin, the look-back otherwise (dense matching, the fused
+    # pair hash, partition chunks)
+    for K, kw, want in [(31, {}, slots), (22, {}, slots), (27, dict(match_scope=1), slots),
+                        (27, dict(match_distance=1 << 40), lookback),
+                        (24, dict(pipeline_chunks=2), lookback)]:
+        h = vx.vx_plot_create(K, bytes(32), vx.make_opts(**kw) if kw else None)
+        assert vx.vx_plot_kernel_mask(h) == want, (K, kw)
+        vx.vx_plot_destroy(h)
     h = vx.vx_plot_create(20, bytes(32), vx.make_opts(scatter_mode=2, fuse_pair_hash=1))
     assert vx.vx_plot_kernel_mask(h) == ["key_setup", "hash_direct", "scan_counts", "sortmatch"]
     vx.vx_plot_destroy(h)
@@ -158,7 +168,7 @@ def test_cross_bucket_scope_plans_a_halo(vx):
     assert t2g >= 16 * 2 ** 31  # E|T2| = N for the cross-bucket match
     h = vx.vx_plot_create(31, bytes(32), vx.make_opts(match_scope=1))
     assert vx.vx_plot_kernel_mask(h) == ["key_setup", "hash_staged", "scatter2", "scan_counts",
-                                         "sortmatch", "pairhash"]
+                                         "scan_pairs", "sortmatch", "pairhash"]
     vx.vx_plot_destroy(h)
 
 

@@ -39,7 +39,7 @@ def copy_table(vx, h, which):
     return host[: n * rb].numpy().reshape(n, rb)
 
 
-@pytest.mark.parametrize("placement", [0, 2], ids=["lookback", "slots"])
+@pytest.mark.parametrize("placement", [1, 2], ids=["lookback", "slots"])
 def test_batch_mixed_k_equals_oracle(vx, placement):
     mix = [(10, 101), (14, 102), (16, 103), (18, 104), (20, 105), (12, 106), (22, 107), (17, 108),
            (1, 109), (24, 110)]
@@ -108,7 +108,8 @@ def test_batch_mixed_scope_and_placement(vx):
     # halo-capable kernel instances run both kinds) and both Table-2
     # placements (a mixed launch places every plot by look-back): each plot
     # equals its own oracle.
-    mix = [(14, 120, dict(match_scope=1)), (16, 121, {}), (18, 122, dict(match_scope=1, t2_placement=2)),
+    mix = [(14, 120, dict(match_scope=1)), (16, 121, dict(t2_placement=1)),
+           (18, 122, dict(match_scope=1, t2_placement=2)),
            (12, 123, dict(t2_placement=2)), (20, 124, dict(match_scope=1)), (1, 125, dict(match_scope=1))]
     plots = [vx.Plot(K, plot_key(s), vx.make_opts(**kw)) for K, s, kw in mix]
     for rep in range(2):

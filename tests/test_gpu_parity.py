@@ -121,8 +121,11 @@ CASES = [
     (18, 14, dict(partition_log2=13)),                         # large partitions, 13-bit digits
     (19, 17, dict(partition_log2=9, slack_sigma=40)),          # roomy slots
     (20, 19, dict(partition_log2=6)),                          # 2^14 tiny partitions
-    # both Table-2 placements forced (automatic = look-back)
-    (1, 0, LOOKBACK), (12, 6, LOOKBACK), (20, 11, LOOKBACK), (22, 0, LOOKBACK),
+    # both Table-2 placements forced (automatic = the pair slots wherever a
+    # partition's pairs fit them with a wide margin, as at every K here)
+    (1, 0, LOOKBACK), (2, 1, LOOKBACK), (5, 3, LOOKBACK), (12, 6, LOOKBACK), (14, 8, LOOKBACK),
+    (16, 9, LOOKBACK), (18, 10, LOOKBACK), (20, 11, LOOKBACK), (22, 0, LOOKBACK),
+    (22, 0, dict(STAGED, t2_placement=1)), (20, 19, dict(partition_log2=6, t2_placement=1)),
     (17, 18, dict(DIRECT, t2_placement=1)), (19, 29, dict(partition_log2=13, t2_placement=1)),
     (1, 0, SLOTS), (5, 3, SLOTS), (14, 8, SLOTS), (22, 0, SLOTS),
     (20, 19, dict(partition_log2=6, t2_placement=2)),          # 2^14 groups of 8 partitions
@@ -228,8 +231,9 @@ def test_custom_match_distance_both_placements(vx, K, seed, D, placement):
 def test_pair_slot_overflow_is_reported(vx):
     # K=26 with every pair of a logical bucket matching: ~4096 pairs per
     # partition, more than a pair slot (1.5 x 2607) holds.  Forced slots
-    # must fail with VX_EOVERFLOW; the look-back placement (automatic)
-    # agrees with the split path, which places pairs by a plain scan.
+    # must fail with VX_EOVERFLOW; the look-back placement (automatic here:
+    # the slots would not hold the expected pairs) agrees with the split
+    # path, which places pairs by a plain scan.
     K, key, D = 26, plot_key(65), (1 << 64) - 1
     p = vx.Plot(K, key, vx.make_opts(match_distance=D, t2_placement=2))
     p.run()
@@ -310,7 +314,7 @@ def test_sync_reads_its_own_plot_when_buffers_are_reused(vx):
         vx.vx_plot_destroy(h)
 
 
-@pytest.mark.parametrize("K,s,placement", [(16, 8, 0), (20, 6, 2)], ids=["lookback", "slots"])
+@pytest.mark.parametrize("K,s,placement", [(16, 8, 1), (20, 6, 2)], ids=["lookback", "slots"])
 def test_lookback_wait_times_out(vx, K, s, placement):
     # Partition 0 (look-back placement) or chunk 0 of the pair-count scan
     # (slot placement: 2^14 partitions = 4 scan chunks) withholds its
@@ -385,7 +389,7 @@ def test_profile_trace(vx):
     assert ms["hash_staged"] > 0 and ms["sortmatch"] > 0 and ms["sort"] > 0 and ms["match"] > 0
     assert ms["pairhash"] > 0
     assert vx.vx_plot_kernel_mask(p.handle) == ["key_setup", "hash_staged", "scan_counts",
-                                                "sortmatch", "pairhash"]
+                                                "scan_pairs", "sortmatch", "pairhash"]
     assert vx.vx_plot_kernel_mask(p.handle, split=True) == [
         "key_setup", "hash_staged", "scan_counts", "sort", "scan_pairs", "match"]
     p.close()

@@ -49,6 +49,8 @@ WIN_CASES = [
     (20, 56, 3, DIRECT),
     (18, 57, 2, dict(fuse_pair_hash=1)),
     (18, 58, 2, dict(t2_placement=2)),
+    (18, 63, 2, dict(t2_placement=1)),
+    (22, 64, 3, dict(partition_log2=6, t2_placement=1)),
     (20, 59, 1, dict(pipeline_chunks=4, partition_log2=8)),    # 4 nonce chunks, two levels
     (22, 60, 4, {}),
     (17, 61, 2, dict(match_distance=1 << 45)),
