@@ -174,26 +174,61 @@ __device__ __forceinline__ void sort_pingpong(const Part &A, uint64_t *XK, uint3
         YN[pos] = XN[i];
     }
     __syncthreads();
-    // DC[g] is now the end of run g: run g is [DC[g-1], DC[g])
+    // DC[g] is now the end of run g: run g is [DC[g-1], DC[g]).  A record's
+    // place is its run's start plus the run's records before it.  A run's
+    // records sit in neighbouring lanes of a chunk of 32 positions, so each
+    // lane compares with the lanes up to the longest run's length away
+    // (shuffles, every lane in step), on a 32-bit compare key: the key bits
+    // below the digit, or their top 32 -- records of a run agree above
+    // them.  A lane whose run leaves its chunk, or that meets an equal
+    // compare key, ranks itself again from shared memory on full keys and
+    // nonces.  Two chunks per step so that their work overlaps.
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const uint32_t nch = (n + 31u) >> 5;
-    for (uint32_t c = warp; c < nch; c += NW) {
-        const uint32_t p = 32u * c + lane;
-        if (p < n) {
-            const uint64_t k = YK[p];
-            const uint32_t nn = YN[p];
-            const uint32_t g = (uint32_t)(k >> shift) & dmask;
-            const uint32_t s = g ? A.DC[g - 1] : 0u;
-            const uint32_t e = A.DC[g];
-            uint32_t dst = s;
-            if (e - s == 2) {  // the most common run of more than one record
-                const uint32_t q = p == s ? s + 1 : s;
-                dst += rec_less(YK[q], YN[q], k, nn) ? 1u : 0u;
-            } else if (e - s > 2) {
-                for (uint32_t q = s; q < e; ++q) dst += rec_less(YK[q], YN[q], k, nn) ? 1u : 0u;
+    const int cs = shift > 32 ? shift - 32 : 0;
+    for (uint32_t c = warp; c < nch; c += 2 * NW) {
+        const uint32_t pa = 32u * c + lane, pb = pa + 32u * NW;
+        const bool va = pa < n, vb = pb < n;
+        const uint32_t xa = va ? pa : 0u, xb = vb ? pb : 0u;
+        const uint64_t ka = YK[xa], kb = YK[xb];
+        const uint32_t na = YN[xa], nb = YN[xb];
+        const uint32_t ga = (uint32_t)(ka >> shift) & dmask, gb = (uint32_t)(kb >> shift) & dmask;
+        const uint32_t sa = ga ? A.DC[ga - 1] : 0u, sb = gb ? A.DC[gb - 1] : 0u;
+        const uint32_t ea = va ? A.DC[ga] : 0u, eb = vb ? A.DC[gb] : 0u;
+        const uint32_t lmax = __reduce_max_sync(0xffffffffu, max(va ? ea - sa : 0u, vb ? eb - sb : 0u));
+        uint32_t da = sa, db = sb;
+        if (lmax > 1) {
+            const uint32_t qa = (uint32_t)(ka >> cs), qb = (uint32_t)(kb >> cs);
+            // the chunk's positions are [32 c, 32 c + 32): a run inside it
+            // is seen whole by the shuffles
+            bool slow_a = va && (sa < 32u * c || ea > 32u * c + 32u);
+            bool slow_b = vb && (sb < 32u * (c + NW) || eb > 32u * (c + NW) + 32u);
+            for (uint32_t t = 1; t < lmax; ++t) {
+                const uint32_t da_ = __shfl_down_sync(0xffffffffu, qa, t), ua = __shfl_up_sync(0xffffffffu, qa, t);
+                const uint32_t db_ = __shfl_down_sync(0xffffffffu, qb, t), ub = __shfl_up_sync(0xffffffffu, qb, t);
+                const bool ina_d = pa + t < ea, ina_u = lane >= t && pa - t >= sa;
+                const bool inb_d = pb + t < eb, inb_u = lane >= t && pb - t >= sb;
+                da += (ina_d && da_ < qa ? 1u : 0u) + (ina_u && ua < qa ? 1u : 0u);
+                db += (inb_d && db_ < qb ? 1u : 0u) + (inb_u && ub < qb ? 1u : 0u);
+                slow_a = slow_a || (ina_d && da_ == qa) || (ina_u && ua == qa);
+                slow_b = slow_b || (inb_d && db_ == qb) || (inb_u && ub == qb);
             }
-            XK[dst] = k;
-            XN[dst] = nn;
+            if (va && slow_a) {
+                da = sa;
+                for (uint32_t q = sa; q < ea; ++q) da += rec_less(YK[q], YN[q], ka, na) ? 1u : 0u;
+            }
+            if (vb && slow_b) {
+                db = sb;
+                for (uint32_t q = sb; q < eb; ++q) db += rec_less(YK[q], YN[q], kb, nb) ? 1u : 0u;
+            }
+        }
+        if (va) {
+            XK[da] = ka;
+            XN[da] = na;
+        }
+        if (vb) {
+            XK[db] = kb;
+            XN[db] = nb;
         }
     }
     __syncthreads();
@@ -291,48 +326,72 @@ __device__ __forceinline__ void match_and_write(const Desc &d, uint32_t f, uint3
         nt = n + hc;
     }
     // 2. per chunk of 32 sorted records (one per lane; warp w takes chunks
-    //    [c0, c1)): the pairs starting at each record r, i.e. the later
-    //    records up to lim = min(last key of r's logical bucket,
-    //    key_r + D - 1), or key_r + D - 1 for the cross-bucket match, four
-    //    probes per step; and the lane's Table-1 record {nonce, BE key64},
-    //    three 4-byte stores (a warp's stores cover its chunk's 384 bytes).
+    //    [c0, c1), two at a time so that their loads overlap): the pairs
+    //    starting at each record r, i.e. the later records up to
+    //    lim = min(last key of r's logical bucket, key_r + D - 1), or
+    //    key_r + D - 1 for the cross-bucket match (four probes, then one by
+    //    one while all four match); the pair offsets inside the warp's
+    //    chunks (warp scans); and the lane's Table-1 record {nonce, BE
+    //    key64}, three 4-byte stores (a warp's stores cover its chunk's 384
+    //    bytes).  Probes may read up to three entries past the records; they
+    //    lie inside the shared allocation and are masked.
     const uint32_t nch = (n + 31u) >> 5;
     const uint32_t c0 = warp * nch / NW, c1 = (warp + 1) * nch / NW;
+    const uint32_t rend = min(32u * c1, n);  // the warp's records end here
     const uint64_t D = d.D;
     const bool global = HALO && d.scope != 0;
     uint32_t *__restrict__ t1w = reinterpret_cast<uint32_t *>(d.t1) + 3 * off;
-    uint32_t wsum = 0;
-    for (uint32_t c = c0; c < c1; ++c) {
-        const uint32_t r = 32u * c + lane;
-        uint32_t cnt = 0;
-        if (r < n) {
-            const uint64_t k = SK[r];
-            t1w[3u * r] = SN[r];
-            t1w[3u * r + 1] = bswap32((uint32_t)(k >> 32));
-            t1w[3u * r + 2] = bswap32((uint32_t)k);
-            const uint64_t last_in_bucket = global ? ~0ull : (k | ((1ull << 40) - 1));
-            uint64_t reach = k + (D - 1);
-            if (reach < k) reach = ~0ull;  // saturate
-            const uint64_t lim = reach < last_in_bucket ? reach : last_in_bucket;
-            for (uint32_t q = r + 1; q < nt; q += 4) {
-                const bool m0 = SK[q] <= lim;
-                const bool m1 = m0 && q + 1 < nt && SK[q + 1] <= lim;
-                const bool m2 = m1 && q + 2 < nt && SK[q + 2] <= lim;
-                const bool m3 = m2 && q + 3 < nt && SK[q + 3] <= lim;
-                cnt += (uint32_t)m0 + (uint32_t)m1 + (uint32_t)m2 + (uint32_t)m3;
-                if (!m3) break;
-            }
-            ST[r] = cnt;
+    auto limit_of = [&](uint64_t k) -> uint64_t {
+        const uint64_t last_in_bucket = global ? ~0ull : (k | ((1ull << 40) - 1));
+        uint64_t reach = k + (D - 1);
+        if (reach < k) reach = ~0ull;  // saturate
+        return reach < last_in_bucket ? reach : last_in_bucket;
+    };
+    auto count_from = [&](uint32_t r, uint64_t lim, uint64_t k1, uint64_t k2, uint64_t k3,
+                          uint64_t k4) -> uint32_t {
+        const bool m1 = r + 1 < nt && k1 <= lim;
+        const bool m2 = m1 && r + 2 < nt && k2 <= lim;
+        const bool m3 = m2 && r + 3 < nt && k3 <= lim;
+        const bool m4 = m3 && r + 4 < nt && k4 <= lim;
+        uint32_t cnt = (uint32_t)m1 + (uint32_t)m2 + (uint32_t)m3 + (uint32_t)m4;
+        if (m4)
+            for (uint32_t q = r + 5; q < nt && SK[q] <= lim; ++q) ++cnt;
+        return cnt;
+    };
+    uint32_t carry = 0;  // pairs of the warp's chunks before the current one
+    for (uint32_t c = c0; c < c1; c += 2) {
+        const uint32_t ra = 32u * c + lane, rb = ra + 32u;
+        const bool va = ra < n, vb = c + 1 < c1 && rb < n;
+        const uint32_t xa = va ? ra : 0u, xb = vb ? rb : 0u;
+        const uint64_t ka = SK[xa], kb = SK[xb];
+        const uint64_t a1 = SK[xa + 1], a2 = SK[xa + 2], a3 = SK[xa + 3], a4 = SK[xa + 4];
+        const uint64_t b1 = SK[xb + 1], b2 = SK[xb + 2], b3 = SK[xb + 3], b4 = SK[xb + 4];
+        const uint32_t na = SN[xa], nb = SN[xb];
+        if (va) {
+            t1w[3u * ra] = na;
+            t1w[3u * ra + 1] = bswap32((uint32_t)(ka >> 32));
+            t1w[3u * ra + 2] = bswap32((uint32_t)ka);
         }
-        wsum += __reduce_add_sync(0xffffffffu, cnt);
+        if (vb) {
+            t1w[3u * rb] = nb;
+            t1w[3u * rb + 1] = bswap32((uint32_t)(kb >> 32));
+            t1w[3u * rb + 2] = bswap32((uint32_t)kb);
+        }
+        const uint32_t cA = va ? count_from(ra, limit_of(ka), a1, a2, a3, a4) : 0u;
+        const uint32_t cB = vb ? count_from(rb, limit_of(kb), b1, b2, b3, b4) : 0u;
+        const uint32_t iA = warp_incl_scan(cA), iB = warp_incl_scan(cB);
+        const uint32_t tA = __shfl_sync(0xffffffffu, iA, 31);
+        if (va) ST[ra] = carry + iA - cA;
+        if (vb) ST[rb] = carry + tA + iB - cB;
+        carry += tA + __shfl_sync(0xffffffffu, iB, 31);
     }
-    if (lane == 0) A.WS[warp] = wsum;
+    if (lane == 0) A.WS[warp] = carry;
     __syncthreads();
-    uint32_t P = 0, carry = 0;  // the partition's pairs; those before this warp's chunks
+    uint32_t P = 0, wbase = 0;  // the partition's pairs; those before this warp's chunks
 #pragma unroll
     for (uint32_t w = 0; w < NW; ++w) {
         const uint32_t t = A.WS[w];
-        carry += w < warp ? t : 0u;
+        wbase += w < warp ? t : 0u;
         P += t;
     }
     const bool withhold = (d.test_flags & 1u) != 0;
@@ -372,39 +431,58 @@ __device__ __forceinline__ void match_and_write(const Desc &d, uint32_t f, uint3
         if (threadIdx.x == 0) atomicOr(d.status, kStPairSlot);
         ok = false;
     }
-    // 4. the pairs, in (i, j) order: chunk by chunk, a lane's record r
-    //    starts its cnt pairs (r, r + 1 + j) at its scanned offset.  Slot
-    //    placement: when the pairs fit the key array of shared memory (dead
-    //    since step 2) they are listed there and leave in one bulk copy
-    //    (thread 0's bulk group; the caller waits for its read before the
-    //    buffer is written again), else they go straight to the slot.
+    // 4. the pairs, in (i, j) order: chunk by chunk (two at a time), a
+    //    lane's record r starts its pairs (r, r + 1 + j) at its offset.
+    //    Slot placement: when the pairs fit the key array of shared memory
+    //    (dead since step 2) they are listed there and leave in one bulk
+    //    copy (thread 0's bulk group; the caller waits for its read before
+    //    the buffer is written again), else they go straight to the slot.
     uint4 *__restrict__ out = reinterpret_cast<uint4 *>(d.t2) + base;
     uint2 *__restrict__ pa = reinterpret_cast<uint2 *>(d.b_keys + (uint64_t)f * d.cap2);
     uint2 *__restrict__ pb = reinterpret_cast<uint2 *>(d.b_nonces + (uint64_t)f * d.cap2);
     const uint32_t capA = d.cap2;
     const bool staged = SLOTS && P < capA;
     uint2 *SP = reinterpret_cast<uint2 *>(SK);
+    auto emit = [&](uint32_t x, uint32_t a, uint32_t b) {
+        if (SLOTS)
+            *(staged ? SP + x : x < capA ? pa + x : pb + (x - capA)) = make_uint2(a, b);
+        else
+            out[x] = make_uint4(a, b, 0u, 0u);
+    };
     if (ok) {
-        for (uint32_t c = c0; c < c1; ++c) {
-            const uint32_t r = 32u * c + lane;
-            const uint32_t cnt = r < n ? ST[r] : 0u;
-            const uint32_t incl = warp_incl_scan(cnt);
-            const uint32_t at = carry + incl - cnt;
-            carry += __shfl_sync(0xffffffffu, incl, 31);
+        for (uint32_t c = c0; c < c1; c += 2) {
+            const uint32_t ra = 32u * c + lane, rb = ra + 32u;
+            const bool va = ra < n, vb = c + 1 < c1 && rb < n;
+            // offsets inside the warp's pairs; a record's count is the gap
+            // to the next record's offset (the warp's total after its last)
+            const uint32_t sa = va ? ST[ra] : 0u, sb = vb ? ST[rb] : 0u;
+            const uint32_t ea = va ? (ra + 1 < rend ? ST[ra + 1] : carry) : 0u;
+            const uint32_t eb = vb ? (rb + 1 < rend ? ST[rb + 1] : carry) : 0u;
+            const uint32_t aa = va ? SN[ra] : 0u, ab = vb ? SN[rb] : 0u;
+            const uint32_t cA = ea - sa, cB = eb - sb;
+            // the first four partners of each record, read together (the
+            // reads past the records stay inside the shared allocation)
+            const uint32_t xa = va ? ra : 0u, xb = vb ? rb : 0u;
+            const uint32_t a1 = SN[xa + 1], a2 = SN[xa + 2], a3 = SN[xa + 3], a4 = SN[xa + 4];
+            const uint32_t b1 = SN[xb + 1], b2 = SN[xb + 2], b3 = SN[xb + 3], b4 = SN[xb + 4];
             if (MODE == kSortHash) {
-                if (r < n) ST[r] = at;  // offsets for the listing below
+                __syncwarp();  // every lane has read its neighbour's offset
+                if (va) ST[ra] = wbase + sa;  // offsets for the listing below
+                if (vb) ST[rb] = wbase + sb;
                 continue;
             }
-            const uint32_t a = r < n ? SN[r] : 0u;
-            for (uint32_t j = 0; __any_sync(0xffffffffu, j < cnt); ++j) {
-                if (j < cnt) {
-                    const uint32_t b = SN[r + 1 + j];
-                    const uint32_t x = at + j;
-                    if (SLOTS)
-                        *(staged ? SP + x : x < capA ? pa + x : pb + (x - capA)) = make_uint2(a, b);
-                    else
-                        out[x] = make_uint4(a, b, 0u, 0u);
-                }
+            const uint32_t oa = wbase + sa, ob = wbase + sb;
+            if (cA > 0) emit(oa, aa, a1);
+            if (cA > 1) emit(oa + 1, aa, a2);
+            if (cA > 2) emit(oa + 2, aa, a3);
+            if (cA > 3) emit(oa + 3, aa, a4);
+            if (cB > 0) emit(ob, ab, b1);
+            if (cB > 1) emit(ob + 1, ab, b2);
+            if (cB > 2) emit(ob + 2, ab, b3);
+            if (cB > 3) emit(ob + 3, ab, b4);
+            for (uint32_t j = 4; __any_sync(0xffffffffu, j < cA || j < cB); ++j) {
+                if (j < cA) emit(oa + j, aa, SN[ra + 1 + j]);
+                if (j < cB) emit(ob + j, ab, SN[rb + 1 + j]);
             }
         }
         if (staged) {
