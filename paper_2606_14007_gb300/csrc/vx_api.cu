@@ -34,6 +34,7 @@ using vx::LaunchSet;
 namespace vx {
 static_assert(kPlanHashTile == (uint64_t)kHashTile, "planner and hash kernel tiles differ");
 static_assert(kPlanScanChunk == (uint64_t)kScanChunk, "planner and scan kernel chunks differ");
+static_assert(kPlanScatterTile == (uint64_t)kScatterTile, "planner and scatter kernel tiles differ");
 static_assert(kPlanT2HashTile == kT2HashTile, "planner and pair-hash kernel tiles differ");
 static_assert(kPlanT2SlotGroup == (uint64_t)kT2SlotGroup, "planner and slot pair-hash groups differ");
 static_assert(kHashThreads == 256 && kHashNoncesPerThread == 8, "hash shape the planner accepts");

@@ -28,6 +28,7 @@ constexpr uint64_t kWriteStageBytes = 256ull << 20;  // Sec. III-B: 256 MB pinne
 constexpr uint64_t kWriteChunkBytes = 4ull << 20;    // Sec. III-A: 4 MB sequential chunks
 constexpr uint64_t kPlanHashTile = 2048;   // nonces per hash CTA (threads x nonces/thread)
 constexpr uint64_t kPlanScanChunk = 4096;  // counters per Table-1 offset-scan CTA
+constexpr uint64_t kPlanScatterTile = 4096; // records per second-level scatter CTA
 constexpr uint64_t kPlanT2HashTile = 2048; // Table-2 records per pair-hash CTA
 constexpr uint64_t kPlanT2SlotGroup = 8;   // partitions per pair-hash CTA reading pair slots
 
@@ -216,7 +217,7 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
             return VX_EINVAL;
         }
         P.cap1 = (uint32_t)cap1;
-        P.chunks1 = (uint32_t)((cap1 + 4095) / 4096);
+        P.chunks1 = (uint32_t)((cap1 + kPlanScatterTile - 1) / kPlanScatterTile);
     }
     int db = K - P.pk;
     if (db < 1) db = 1;
