@@ -299,6 +299,8 @@ def main():
                          "times and kernel split for K=22 and 27..31 beside the oracle")
     ap.add_argument("--partition-log2", type=int, default=0)
     ap.add_argument("--scatter-mode", type=int, default=0)
+    ap.add_argument("--nonces-per-thread", type=int, default=0,
+                    help="Table-1 hash: 0 (= 8), 4, 8 or 16 nonces per thread")
     ap.add_argument("--fuse-pair-hash", type=int, default=0)
     ap.add_argument("--pipeline-chunks", type=int, default=0)
     ap.add_argument("--t2-placement", type=int, default=0,
@@ -580,7 +582,8 @@ def main():
 def plot_opts(vx, args):
     return vx.make_opts(partition_log2=args.partition_log2, scatter_mode=args.scatter_mode,
                         fuse_pair_hash=args.fuse_pair_hash, pipeline_chunks=args.pipeline_chunks,
-                        t2_placement=args.t2_placement, match_scope=args.match_scope)
+                        t2_placement=args.t2_placement, match_scope=args.match_scope,
+                        nonces_per_thread=args.nonces_per_thread)
 
 
 def _timed(fn, stream):

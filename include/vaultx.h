@@ -85,8 +85,10 @@ typedef struct vx_opts {
                                    Poisson count; 0 = default (12)                   */
     uint32_t hash_block;        /* threads per block of the hash kernels: 0 or 256
                                    (the one shape built; others are VX_EINVAL)      */
-    uint32_t nonces_per_thread; /* nonces each hash thread handles: 0 or 8 (the one
-                                   shape built; others are VX_EINVAL)               */
+    uint32_t nonces_per_thread; /* nonces each Table-1 hash thread handles: 0 (= 8),
+                                   4, 8 or 16 with the staged bucketing of a whole
+                                   plot; 8 with the direct bucketing or a window;
+                                   others VX_EINVAL.  Same tables for every value. */
     uint32_t scatter_mode;      /* bucketing of hashed records: 0 = automatic
                                    (staged), 1 = staged (shared-memory histogram per CTA, one
                                    claim per (CTA, bin), two levels), 2 = direct
@@ -238,12 +240,13 @@ int vx_table_info(const vx_plot *plot, int which, const void **dptr, uint64_t *n
 
 /* Autotuner: times every distinct plan for K that the candidate options give
  * (partition size 2^9 .. 2^13 records, i.e. the physical partition count and
- * the sort tile, and the staged or direct bucketing strategy; the hash
- * kernels' threads x nonces shape is compiled in and not a candidate) on
- * this device.  Each candidate runs one warm-up and three timed plots with a
- * fixed synthetic key in library-owned memory on stream (CUDA events).
- * *best gets base (defaults if null) with the fastest candidate's
- * partition_log2 and scatter_mode, *best_ms its mean plot time.
+ * the sort tile; the staged bucketing with 4, 8 or 16 nonces per hash
+ * thread, i.e. threads per nonce 1/4, 1/8, 1/16; the direct bucketing with
+ * 8) on this device.  Each candidate runs one warm-up and three timed plots
+ * with a fixed synthetic key in library-owned memory on stream (CUDA
+ * events).  *best gets base (defaults if null) with the fastest candidate's
+ * partition_log2, scatter_mode and nonces_per_thread, *best_ms its mean
+ * plot time.
  * Synchronous; a candidate that cannot be planned or allocated is skipped
  * (VX_ENOMEM if none ran).  The Python binding keeps an on-disk cache of the
  * result keyed by device and K.  The paper has no counterpart (its kernels

@@ -265,27 +265,43 @@ static cudaError_t launch_hs(const Desc *descs, int nplots, const uint32_t *tile
 // HALO instances carry the cross-bucket halo code and window instances the
 // window filter or the nonce list; plain launches carry neither.  A list
 // launch holds one windowed plot (never cross-bucket).
-template <bool HALO, int WM>
-static cudaError_t launch_hs_agg(const Desc *descs, int nplots, const uint32_t *tile_start,
+// Whole plots may take 4 or 16 nonces per thread instead of 8 (a tuning
+// choice: more nonces per thread, more independent hashes in flight per
+// thread but fewer resident CTAs); windows always take 8.
+template <bool HALO, int WM, int P>
+static cudaError_t launch_hs_npt(const Desc *descs, int nplots, const uint32_t *tile_start,
                                  uint32_t total_tiles, bool agg, int chunk, cudaStream_t s)
 {
-    constexpr int T = kHashThreads, P = kHashNoncesPerThread;
+    constexpr int T = kHashThreads;
     return agg ? launch_hs<T, P, true, HALO, WM>(descs, nplots, tile_start, total_tiles, chunk, s)
                : launch_hs<T, P, false, HALO, WM>(descs, nplots, tile_start, total_tiles, chunk, s);
+}
+
+template <bool HALO, int WM>
+static cudaError_t launch_hs_agg(const Desc *descs, int nplots, const uint32_t *tile_start,
+                                 uint32_t total_tiles, bool agg, int chunk, cudaStream_t s, int npt)
+{
+    if (WM == kWinNone && npt == 4)
+        return launch_hs_npt<HALO, kWinNone, 4>(descs, nplots, tile_start, total_tiles, agg, chunk, s);
+    if (WM == kWinNone && npt == 16)
+        return launch_hs_npt<HALO, kWinNone, 16>(descs, nplots, tile_start, total_tiles, agg, chunk, s);
+    if (npt != kHashNoncesPerThread) return cudaErrorInvalidValue;
+    return launch_hs_npt<HALO, WM, kHashNoncesPerThread>(descs, nplots, tile_start, total_tiles, agg, chunk, s);
 }
 
 cudaError_t launch_hash_scatter(const Desc *descs, int nplots, const uint32_t *tile_start,
                                 uint32_t total_tiles, HashCfg cfg, int chunk, cudaStream_t s)
 {
     if (total_tiles == 0) return cudaSuccess;
+    const int npt = cfg.npt;
     if (cfg.list)
         return cfg.halo ? cudaErrorInvalidValue
-                        : launch_hs_agg<false, kWinList>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s);
+                        : launch_hs_agg<false, kWinList>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s, npt);
     if (cfg.win)
-        return cfg.halo ? launch_hs_agg<true, kWinFilter>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s)
-                        : launch_hs_agg<false, kWinFilter>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s);
-    return cfg.halo ? launch_hs_agg<true, kWinNone>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s)
-                    : launch_hs_agg<false, kWinNone>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s);
+        return cfg.halo ? launch_hs_agg<true, kWinFilter>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s, npt)
+                        : launch_hs_agg<false, kWinFilter>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s, npt);
+    return cfg.halo ? launch_hs_agg<true, kWinNone>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s, npt)
+                    : launch_hs_agg<false, kWinNone>(descs, nplots, tile_start, total_tiles, cfg.agg, chunk, s, npt);
 }
 
 // ------------------------------------------------- hash + direct scatter

@@ -37,7 +37,8 @@ static_assert(kPlanScanChunk == (uint64_t)kScanChunk, "planner and scan kernel c
 static_assert(kPlanScatterTile == (uint64_t)kScatterTile, "planner and scatter kernel tiles differ");
 static_assert(kPlanT2HashTile == kT2HashTile, "planner and pair-hash kernel tiles differ");
 static_assert(kPlanT2SlotGroup == (uint64_t)kT2SlotGroup, "planner and slot pair-hash groups differ");
-static_assert(kHashThreads == 256 && kHashNoncesPerThread == 8, "hash shape the planner accepts");
+static_assert(kHashThreads == kPlanHashThreads && kHashNoncesPerThread == kPlanNoncesPerThread,
+              "hash shape the planner accepts");
 static_assert(kMatchThreads >= 256, "k_match loads a halo (<= 256 records) one per thread");
 static_assert(sizeof(Desc) + 64 <= kStageTilesOffset, "descriptor overlaps staged tiles");
 static_assert(kStageTilesOffset + kTileArrays * 2 * sizeof(uint32_t) <= kStageResultOffset &&
@@ -197,6 +198,11 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
     L->max_dbits = 1;
     L->max_p2 = 0;
     int min_bits = 64;
+    // One staged hash launch takes one shape: the plots' common nonces per
+    // thread, else the default (any shape gives the same records).
+    int npt = n > 0 && plots[0] ? plots[0]->plan.npt : kPlanNoncesPerThread;
+    for (int i = 0; i < n; ++i)
+        if (plots[i] && plots[i]->plan.npt != npt) npt = kPlanNoncesPerThread;
     for (int i = 0; i < n; ++i) {
         if (!plots[i] || !plots[i]->d_t1) return VX_EINVAL;
         const Plan &pl = plots[i]->plan;
@@ -223,7 +229,8 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
         uint64_t cnt[vx::kTileArrays] = {};
         const bool staged = pl.mode == kScatterStaged;
         for (int g = 0; g < vx::kMaxChunks && g < pl.hchunks; ++g) {
-            cnt[(staged ? A_STG : A_DIR) + g] = list ? pl.tiles_list : pl.tiles_hash;
+            cnt[(staged ? A_STG : A_DIR) + g] =
+                list ? pl.tiles_list : staged ? vx::hash_tiles(pl.N / pl.hchunks, npt) : pl.tiles_hash;
             if (staged && pl.p2 > 0) cnt[A_S2 + g] = pl.tiles_s2;
         }
         const uint64_t np = 1ull << pl.p;
@@ -246,6 +253,7 @@ int build_tiles(vx_plot *const *plots, int n, uint32_t *h, const uint32_t *d, La
     }
     L->n = n;
     L->agg = min_bits <= kAggMaxBits;
+    L->npt = npt;
     L->fuse_pair_hash = fuse;
     L->pair_slots = slots;
     L->halo = halo;
@@ -381,10 +389,10 @@ cudaError_t launch_front(const LaunchSet &L, const vx::Lanes &ln, const vx::Trac
     for (int g = 0; g < L.G; ++g) {
         if (L.n_staged[g])
             VX_LAUNCH(KID_STAGED, A, vx::launch_hash_scatter(L.descs, L.n, L.t_staged[g], L.n_staged[g],
-                                                             vx::HashCfg{L.agg, L.halo, L.win, L.list}, g, A));
+                                                             vx::HashCfg{L.agg, L.halo, L.win, L.list, L.npt}, g, A));
         if (L.n_direct[g])
             VX_LAUNCH(KID_DIRECT, A, vx::launch_hash_direct(L.descs, L.n, L.t_direct[g], L.n_direct[g], g, A,
-                                                            vx::HashCfg{L.agg, L.halo, L.win, L.list}));
+                                                            vx::HashCfg{L.agg, L.halo, L.win, L.list, L.npt}));
         if (L.n_s2[g]) {
             if (ov) {
                 cudaEventRecord(ln.sync[g], A);
@@ -822,7 +830,7 @@ int vx_autotune(int K, const vx_opts *base, vx_opts *best, double *best_ms, void
     cudaStream_t s = (cudaStream_t)stream;
     uint8_t key[32];
     for (int i = 0; i < 32; ++i) key[i] = (uint8_t)(0xA5 ^ (i * 7));
-    struct Seen { int p, p1, p2, mode; uint32_t cap2; int dbits; };
+    struct Seen { int p, p1, p2, mode, npt; uint32_t cap2; int dbits; };
     std::vector<Seen> seen;
     double best_t = 0;
     bool found = false;
@@ -831,19 +839,23 @@ int vx_autotune(int K, const vx_opts *base, vx_opts *best, double *best_ms, void
         if (e0) cudaEventDestroy(e0);
         return VX_ECUDA;
     }
+    // candidates: partition size x bucketing strategy x nonces per hash
+    // thread (4, 8, 16 for the staged hash; the direct one takes 8)
     for (int part = 9; part <= 13; ++part) {
-        for (uint32_t mode : {(uint32_t)vx::kScatterStaged, (uint32_t)vx::kScatterDirect}) {
+        for (int cand = 0; cand < 4; ++cand) {
+            const uint32_t mode = cand < 3 ? (uint32_t)vx::kScatterStaged : (uint32_t)vx::kScatterDirect;
             vx_opts o = b0;
             o.partition_log2 = part;
             o.scatter_mode = mode;
+            o.nonces_per_thread = cand == 0 ? 4u : cand == 2 ? 16u : 8u;
             vx::Plan pl;
             const char *why = nullptr;
             if (make_plan(K, &o, &pl, &why) != VX_OK) continue;
-            const Seen me{pl.p, pl.p1, pl.p2, pl.mode, pl.cap2, pl.dbits};
+            const Seen me{pl.p, pl.p1, pl.p2, pl.mode, pl.npt, pl.cap2, pl.dbits};
             bool dup = false;
             for (const Seen &x : seen)
                 dup = dup || (x.p == me.p && x.p1 == me.p1 && x.p2 == me.p2 && x.mode == me.mode &&
-                              x.cap2 == me.cap2 && x.dbits == me.dbits);
+                              x.npt == me.npt && x.cap2 == me.cap2 && x.dbits == me.dbits);
             if (dup) continue;  // the planner clamped it to a plan already timed
             seen.push_back(me);
             vx_plot *p = nullptr;

@@ -36,6 +36,7 @@ struct LaunchSet {
     uint32_t n_pchunk[kMaxChunks], n_t2h[kMaxChunks];
     uint32_t n_scan, n_part;          // total CTAs
     bool agg;
+    int npt;                 // nonces per thread of the staged Table-1 hash launch
     bool fuse_pair_hash;
     bool pair_slots;   // every plot uses the slot placement (t_t2h[0] = slot pair-hash grid)
     bool halo;         // some plot matches across buckets: kernels with the halo code

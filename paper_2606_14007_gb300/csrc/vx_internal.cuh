@@ -524,6 +524,7 @@ struct HashCfg {
     bool halo;    // some plot of the launch matches across buckets (halo code)
     bool win;     // some plot of the launch is a window (window filter)
     bool list;    // the launch's one plot hashes its window's nonce list
+    int npt;      // nonces per thread of the staged Table-1 hash (4, 8, 16; 8 with a window)
 };
 cudaError_t launch_key_setup(Desc *descs, int nplots, cudaStream_t s);
 // Hash kernels and the second scatter level take one nonce chunk (of

@@ -27,6 +27,15 @@ constexpr size_t kStageResultOffset = 4064;  // status u32 at +0, Table-2 count 
 constexpr uint64_t kWriteStageBytes = 256ull << 20;  // Sec. III-B: 256 MB pinned staging
 constexpr uint64_t kWriteChunkBytes = 4ull << 20;    // Sec. III-A: 4 MB sequential chunks
 constexpr uint64_t kPlanHashTile = 2048;   // nonces per hash CTA (threads x nonces/thread)
+constexpr int kPlanHashThreads = 256;      // threads per hash CTA
+constexpr int kPlanNoncesPerThread = 8;    // default nonces per hash thread
+
+// Table-1 hash CTAs over n nonces with npt nonces per thread.
+inline uint32_t hash_tiles(uint64_t n, int npt)
+{
+    const uint64_t tile = (uint64_t)kPlanHashThreads * (uint64_t)npt;
+    return (uint32_t)((n + tile - 1) / tile);
+}
 constexpr uint64_t kPlanScanChunk = 4096;  // counters per Table-1 offset-scan CTA
 constexpr uint64_t kPlanScatterTile = 4096; // records per second-level scatter CTA
 constexpr uint64_t kPlanT2HashTile = 2048; // Table-2 records per pair-hash CTA
@@ -40,6 +49,7 @@ struct Plan {
     int pk;                                // partition bits in key space: p + wbits
     uint32_t wbits, win;                   // window: top wbits of key64 == win (wbits 0: whole plot)
     int mode;                              // kScatterStaged or kScatterDirect
+    int npt;                               // nonces per thread of the Table-1 hash (4, 8, 16)
     uint32_t test_flags, spin_limit;
     bool fuse_pair_hash;
     bool pair_slots;                       // pairs staged in the partition slots (t2_placement 2)
@@ -131,12 +141,15 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
             *why = "reserved vx_opts fields must be zero";
             return VX_EINVAL;
         }
-    // The hash kernels are compiled for one shape (256 threads x 8 nonces).
+    // The hash kernels run 256 threads per CTA with 8 nonces per thread;
+    // the plain staged Table-1 hash is also compiled for 4 and 16.
     if ((opts.hash_block != 0 && opts.hash_block != 256) ||
-        (opts.nonces_per_thread != 0 && opts.nonces_per_thread != 8)) {
-        *why = "hash_block must be 0 or 256 and nonces_per_thread 0 or 8";
+        (opts.nonces_per_thread != 0 && opts.nonces_per_thread != 4 && opts.nonces_per_thread != 8 &&
+         opts.nonces_per_thread != 16)) {
+        *why = "hash_block must be 0 or 256 and nonces_per_thread 0, 4, 8 or 16";
         return VX_EINVAL;
     }
+    P.npt = opts.nonces_per_thread ? (int)opts.nonces_per_thread : kPlanNoncesPerThread;
     P.fuse_pair_hash = opts.fuse_pair_hash != 0;
     const uint32_t pc = opts.pipeline_chunks;
     if (pc != 0 && pc != 1 && pc != 2 && pc != 4 && pc != 8) {
@@ -174,6 +187,10 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     // Automatic = staged: on GB300 the per-record slot claims of the direct
     // strategy cost more L2 atomic throughput than the second scatter pass.
     P.mode = opts.scatter_mode == kScatterDirect ? kScatterDirect : kScatterStaged;
+    if (P.npt != kPlanNoncesPerThread && (P.mode != kScatterStaged || P.wbits)) {
+        *why = "nonces_per_thread 4 or 16 needs the staged bucketing and a whole plot (no window)";
+        return VX_EINVAL;
+    }
     if (P.mode == kScatterDirect) {
         P.p1 = P.p;  // one level: the hash kernel claims final-partition slots
     } else if (opts.coarse_bits >= 0) {
@@ -280,7 +297,7 @@ inline int make_plan_sized(int K, const vx_opts *o, Plan *pl, const char **why, 
     }
     // Grids (tile sizes are the kernels' compile-time tiles).
     // Grids per chunk (a chunk of the hash covers 2^K / hchunks nonces).
-    P.tiles_hash = (uint32_t)((P.N / P.hchunks + kPlanHashTile - 1) / kPlanHashTile);
+    P.tiles_hash = hash_tiles(P.N / P.hchunks, P.npt);
     P.tiles_staged = P.mode == kScatterStaged ? P.tiles_hash : 0u;
     P.tiles_direct = P.mode == kScatterDirect ? P.tiles_hash : 0u;
     P.tiles_s2 = P.p2 > 0 ? (uint32_t)(((uint64_t)1 << P.p1) * P.chunks1) : 0u;

@@ -247,7 +247,7 @@ def vx_autotune(K: int, opts: vx_opts | None = None, stream=None) -> tuple[vx_op
     return best, ms.value
 
 
-_TUNED = ("partition_log2", "scatter_mode")
+_TUNED = ("partition_log2", "scatter_mode", "nonces_per_thread")
 
 
 def autotune(K: int, opts: vx_opts | None = None, cache_path: str | None = None,
@@ -264,7 +264,7 @@ def autotune(K: int, opts: vx_opts | None = None, cache_path: str | None = None,
     base = opts if opts is not None else vx_opts_default()
     prop = torch.cuda.get_device_properties(torch.cuda.current_device())
     fields = {n: getattr(base, n) for n, _ in vx_opts._fields_
-              if n not in ("size", "reserved", "partition_log2", "scatter_mode")}
+              if n not in ("size", "reserved") + _TUNED}
     key = json.dumps([prop.name, prop.multi_processor_count, K, fields], sort_keys=True)
     try:
         with open(path) as f:
@@ -275,7 +275,7 @@ def autotune(K: int, opts: vx_opts | None = None, cache_path: str | None = None,
     ctypes.memmove(ctypes.byref(out), ctypes.byref(base), ctypes.sizeof(vx_opts))
     if key in cache:
         for n in _TUNED:
-            setattr(out, n, int(cache[key][n]))
+            setattr(out, n, int(cache[key].get(n, 0)))
         return out
     best, ms = vx_autotune(K, base, stream)
     entry = {n: int(getattr(best, n)) for n in _TUNED}

@@ -85,12 +85,17 @@ def test_required_bytes_rejects_bad_arguments(vx):
                dict(coarse_bits=11, scatter_mode=1), dict(scatter_mode=3),
                dict(slack_sigma=400, partition_log2=12), dict(t2_placement=3),
                dict(t2_placement=2, pipeline_chunks=2), dict(t2_placement=2, fuse_pair_hash=1),
-               dict(hash_block=128), dict(nonces_per_thread=4), dict(match_scope=2),
+               dict(hash_block=128), dict(nonces_per_thread=6), dict(nonces_per_thread=32),
+               dict(nonces_per_thread=4, scatter_mode=2),           # direct: 8 only
+               dict(nonces_per_thread=16, window_bits=2, window=1),  # windows: 8 only
+               dict(match_scope=2),
                dict(match_scope=1, match_distance=1 << 60),        # wider than a partition
                dict(match_scope=1, match_distance=1 << 43)]:       # halo of ~1024 records
         with pytest.raises(vx.VxError):
             vx.vx_plot_required_bytes(31, vx.make_opts(**kw))
     vx.vx_plot_required_bytes(31, vx.make_opts(hash_block=256, nonces_per_thread=8))
+    for npt in (4, 16):  # the staged Table-1 hash's other shapes
+        vx.vx_plot_required_bytes(31, vx.make_opts(nonces_per_thread=npt, scatter_mode=1))
     bad = vx.make_opts()
     bad.size = 8
     with pytest.raises(vx.VxError):

@@ -25,10 +25,12 @@ def test_autotune_plan_plots_correctly_and_caches(vx, tmp_path):
     K = 18
     o = vx.autotune(K, cache_path=path)
     assert 9 <= o.partition_log2 <= 13 and o.scatter_mode in (1, 2)
+    assert o.nonces_per_thread in ((4, 8, 16) if o.scatter_mode == 1 else (8,))
     cache = json.load(open(path))
     assert len(cache) == 1
     (k, entry), = cache.items()
     assert entry["ms"] > 0 and entry["partition_log2"] == o.partition_log2
+    assert entry["nonces_per_thread"] == o.nonces_per_thread
     key = plot_key(130)
     p = vx.Plot(K, key, o)
     p.run()

@@ -108,7 +108,7 @@ def test_batch_mixed_scope_and_placement(vx):
     # halo-capable kernel instances run both kinds) and both Table-2
     # placements (a mixed launch places every plot by look-back): each plot
     # equals its own oracle.
-    mix = [(14, 120, dict(match_scope=1)), (16, 121, dict(t2_placement=1)),
+    mix = [(14, 120, dict(match_scope=1)), (16, 121, dict(t2_placement=1, nonces_per_thread=16)),
            (18, 122, dict(match_scope=1, t2_placement=2)),
            (12, 123, dict(t2_placement=2)), (20, 124, dict(match_scope=1)), (1, 125, dict(match_scope=1))]
     plots = [vx.Plot(K, plot_key(s), vx.make_opts(**kw)) for K, s, kw in mix]

@@ -121,6 +121,11 @@ CASES = [
     (18, 14, dict(partition_log2=13)),                         # large partitions, 13-bit digits
     (19, 17, dict(partition_log2=9, slack_sigma=40)),          # roomy slots
     (20, 19, dict(partition_log2=6)),                          # 2^14 tiny partitions
+    # the Table-1 hash with 4 and 16 nonces per thread (tiles of 1024 and
+    # 4096 nonces; K=11 and 13 end in or fit one ragged tile)
+    (11, 40, dict(nonces_per_thread=16)), (13, 41, dict(nonces_per_thread=16)),
+    (22, 42, dict(nonces_per_thread=16)), (9, 43, dict(nonces_per_thread=4)),
+    (21, 44, dict(nonces_per_thread=4)), (20, 45, dict(nonces_per_thread=16, pipeline_chunks=4)),
     # both Table-2 placements forced (automatic = the pair slots wherever a
     # partition's pairs fit them with a wide margin, as at every K here)
     (1, 0, LOOKBACK), (2, 1, LOOKBACK), (5, 3, LOOKBACK), (12, 6, LOOKBACK), (14, 8, LOOKBACK),
