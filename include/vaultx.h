@@ -50,8 +50,10 @@ enum {
     VX_ETIMEDOUT = -4,  /* a bounded device-side wait gave up                      */
     VX_EBUSY = -5,      /* server full / resource in use                           */
     VX_ENOTREADY = -6,  /* result not produced yet (call order, or still running)  */
-    VX_EOVERFLOW = -7   /* a partition slot overflowed its capacity: the tables are
+    VX_EOVERFLOW = -7,  /* a partition slot overflowed its capacity: the tables are
                            incomplete; re-run with a larger opts.slack_sigma       */
+    VX_EIO = -8         /* a plot file could not be opened, written or closed (the
+                           system's reason, errno text, in vx_last_error)          */
 };
 
 /* Table selectors. */
@@ -286,7 +288,10 @@ int vx_sort_table2(vx_plot *plot, void *d_work, uint64_t work_bytes, void *strea
  * write of the other.  Waits for the plot's own work first (vx_sync), so it
  * may run on a host thread while later plots compute.  Returns after the
  * data is handed to the file system (no fsync); seconds_d2h = time spent
- * waiting for device copies, seconds_total = the whole call.  Synchronous. */
+ * waiting for device copies, seconds_total = the whole call.  Synchronous.
+ * VX_EIO when the file cannot be opened, a write fails or the close reports
+ * a deferred write error (errno text in vx_last_error); VX_ECUDA when a
+ * device copy fails. */
 int vx_plot_write(vx_plot *plot, const char *path, double *seconds_d2h, double *seconds_total);
 
 /* ------------------------------------------- chunked device-memory tiling */
@@ -303,10 +308,29 @@ int vx_plot_write(vx_plot *plot, const char *path, double *seconds_d2h, double *
 int vx_plot_tiled_bytes(int K, const vx_opts *opts, int window_bits, uint64_t *device_bytes,
                         uint64_t *host_t1_bytes, uint64_t *host_t2_bytes);
 
+/* How many times vx_plot_tiled hashes every nonce at window_bits c, into
+ * *passes: 1 for c = 0 (the whole plot), 2 for 1 <= c <= 8 without nonce
+ * chunks (a first pass stores one window-id byte per nonce, then each window
+ * hashes only its own nonces), else 2^c (each window hashes every nonce and
+ * keeps its share: at K=31 a hash pass takes ~51 ms, so c = 9 costs ~26 s).
+ * The cost to weigh against vx_plot_tiled_bytes' footprint: above 8 bits
+ * the id bytes are gone (K=31: 2.93 GB at c = 8, 0.39 GB at c = 9) but the
+ * hashing grows 256-fold.  VX_EINVAL as vx_plot_tiled_bytes.  Host only.
+ * The paper has no counterpart. */
+int vx_plot_tiled_hash_passes(int K, const vx_opts *opts, int window_bits, uint32_t *passes);
+
 /* The fewest window bits (0 .. 16) whose vx_plot_tiled_bytes device_bytes
- * fit budget_bytes, into *window_bits.  VX_ENOMEM if none does (the
+ * fit budget_bytes and whose vx_plot_tiled_hash_passes are at most
+ * max_hash_passes (>= 1), into *window_bits.  VX_ENOMEM if none does (the
  * partition bits bound the window bits), VX_EINVAL for bad arguments.  Host
- * only. */
+ * only.  The paper has no counterpart. */
+int vx_plot_tiled_window_bits_capped(int K, const vx_opts *opts, uint64_t budget_bytes,
+                                     uint32_t max_hash_passes, int *window_bits);
+
+/* vx_plot_tiled_window_bits_capped with at most 2 hash passes: the window-id
+ * path only, never the window counts above 8 bits that hash the whole plot
+ * once per window (a budget below that path's footprint gets VX_ENOMEM; a
+ * caller who accepts 2^c passes asks the capped call).  Host only. */
 int vx_plot_tiled_window_bits(int K, const vx_opts *opts, uint64_t budget_bytes, int *window_bits);
 
 /* A whole plot in device memory of about 2^(1 - window_bits) of its
@@ -349,8 +373,9 @@ int vx_plot_tiled(int K, const uint8_t key[32], const vx_opts *opts, int window_
  * the table's size is needed.  d_work and host_t1 as in vx_plot_tiled (both
  * may be NULL).
  * *seconds (may be NULL) gets the call's wall time.  On an error the file
- * holds the windows written so far.  Synchronous.  VX_EINVAL also when the
- * file cannot be opened; VX_ECUDA when a write fails. */
+ * holds the windows written so far.  Synchronous.  VX_EIO when the file
+ * cannot be opened, a write fails or the close reports a deferred write
+ * error; VX_ECUDA when a device step fails. */
 int vx_plot_tiled_write(int K, const uint8_t key[32], const vx_opts *opts, int window_bits,
                         void *d_work, uint64_t work_bytes, const char *path, void *host_t1,
                         uint64_t host_t1_bytes, uint64_t *t1_count, uint64_t *t2_count,

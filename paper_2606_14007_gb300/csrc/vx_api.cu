@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include <cerrno>
 #include <fcntl.h>
 #include <unistd.h>
 
@@ -526,6 +527,7 @@ const char *vx_strerror(int st)
     case VX_EBUSY: return "busy";
     case VX_ENOTREADY: return "not ready";
     case VX_EOVERFLOW: return "partition slot overflow";
+    case VX_EIO: return "plot file I/O error";
     default: return "unknown status";
     }
 }
@@ -1305,7 +1307,8 @@ namespace vx {
 // Appends plot p's Table 2 (synced) to the open file fd through the pinned
 // staging buffer: double-buffered half-buffer copies on the library's copy
 // stream, each written as sequential 4 MB chunks.  *d2h (may be null) gets
-// the seconds spent waiting for copies.  VX_OK or VX_ECUDA (detail on p).
+// the seconds spent waiting for copies.  VX_OK, VX_ECUDA or VX_EIO (a
+// failed write, errno text on p).
 int write_table2_fd(vx_plot *p, int fd, double *d2h_out)
 {
     const void *src = nullptr;
@@ -1336,6 +1339,7 @@ int write_table2_fd(vx_plot *p, int fd, double *d2h_out)
         return e;
     };
     bool ok = true;
+    int werr = 0;  // errno of a failed write
     if (total > 0) {
         if (issue(0, 0) != cudaSuccess) ok = false;
         uint64_t next = std::min(half, total);
@@ -1352,7 +1356,11 @@ int write_table2_fd(vx_plot *p, int fd, double *d2h_out)
             while (left > 0 && ok) {   // sequential 4 MB writes
                 const size_t chunk = (size_t)std::min<uint64_t>(left, vx::kWriteChunkBytes);
                 ssize_t w = ::write(fd, buf, chunk);
-                if (w <= 0) { ok = false; break; }
+                if (w <= 0) {
+                    werr = w < 0 ? errno : ENOSPC;
+                    ok = false;
+                    break;
+                }
                 buf += w;
                 left -= (uint64_t)w;
             }
@@ -1362,7 +1370,11 @@ int write_table2_fd(vx_plot *p, int fd, double *d2h_out)
     }
     cudaStreamSynchronize(g_copy_stream);
     if (!ok) {
-        set_err(p, "Table-2 write failed");
+        if (werr) {
+            set_err(p, std::string("Table-2 write failed: ") + strerror(werr));
+            return VX_EIO;
+        }
+        set_err(p, "Table-2 copy to the staging buffer failed");
         return VX_ECUDA;
     }
     if (d2h_out) *d2h_out = d2h;
@@ -1379,14 +1391,14 @@ extern "C" int vx_plot_write(vx_plot *p, const char *path, double *sec_d2h, doub
     const auto t0 = std::chrono::steady_clock::now();
     int fd = open(path, O_WRONLY | O_CREAT | O_TRUNC, 0644);
     if (fd < 0) {
-        set_err(p, std::string("cannot open ") + path);
-        return VX_EINVAL;
+        set_err(p, std::string("cannot open ") + path + ": " + strerror(errno));
+        return VX_EIO;
     }
     double d2h = 0;
     rc = vx::write_table2_fd(p, fd, &d2h);
-    if (close(fd) != 0 && rc == VX_OK) {
-        set_err(p, "Table-2 write failed");
-        rc = VX_ECUDA;
+    if (close(fd) != 0 && rc == VX_OK) {  // deferred write-back errors surface here
+        set_err(p, std::string("closing ") + path + ": " + strerror(errno));
+        rc = VX_EIO;
     }
     if (rc != VX_OK) return rc;
     if (sec_d2h) *sec_d2h = d2h;

@@ -206,22 +206,46 @@ extern "C" int vx_plot_tiled_bytes(int K, const vx_opts *opts, int window_bits,
     return VX_OK;
 }
 
-extern "C" int vx_plot_tiled_window_bits(int K, const vx_opts *opts, uint64_t budget_bytes,
-                                         int *window_bits)
+extern "C" int vx_plot_tiled_hash_passes(int K, const vx_opts *opts, int window_bits, uint32_t *passes)
 {
-    if (!window_bits) return VX_EINVAL;
+    if (!passes) return VX_EINVAL;
+    vx_opts o;
+    if (window_opts(opts, window_bits, &o) != VX_OK) return VX_EINVAL;
+    vx::Plan pl;
+    const char *why = nullptr;
+    if (vx::make_plan(K, &o, &pl, &why) != VX_OK) return VX_EINVAL;
+    // whole plot: once; window ids: the id pass and the window's own list;
+    // else every window hashes every nonce and keeps its share
+    *passes = window_bits == 0 ? 1u : use_ids(pl) ? 2u : (1u << window_bits);
+    return VX_OK;
+}
+
+extern "C" int vx_plot_tiled_window_bits_capped(int K, const vx_opts *opts, uint64_t budget_bytes,
+                                                uint32_t max_hash_passes, int *window_bits)
+{
+    if (!window_bits || max_hash_passes == 0) return VX_EINVAL;
     // Fewest windows first: the device footprint falls with every extra bit
     // (one bit is the exception: two half-plot buffers are no smaller than one
     // whole plot), and each extra window costs a little time.
     for (int c = 0; c <= 16; ++c) {
         uint64_t dev = 0;
+        uint32_t passes = 0;
         if (vx_plot_tiled_bytes(K, opts, c, &dev, nullptr, nullptr) != VX_OK) break;
-        if (dev <= budget_bytes) {
+        if (vx_plot_tiled_hash_passes(K, opts, c, &passes) != VX_OK) break;
+        if (dev <= budget_bytes && passes <= max_hash_passes) {
             *window_bits = c;
             return VX_OK;
         }
     }
     return VX_ENOMEM;
+}
+
+extern "C" int vx_plot_tiled_window_bits(int K, const vx_opts *opts, uint64_t budget_bytes,
+                                         int *window_bits)
+{
+    // At most two hashes of every nonce (the window-id path): above 8 window
+    // bits each window would hash the whole plot again.
+    return vx_plot_tiled_window_bits_capped(K, opts, budget_bytes, 2, window_bits);
 }
 
 extern "C" int vx_plot_tiled(int K, const uint8_t key[32], const vx_opts *opts, int window_bits,
@@ -249,10 +273,10 @@ extern "C" int vx_plot_tiled_write(int K, const uint8_t key[32], const vx_opts *
     const auto t0 = std::chrono::steady_clock::now();
     Sink sink;
     sink.fd = open(path, O_WRONLY | O_CREAT | O_TRUNC, 0644);
-    if (sink.fd < 0) return VX_EINVAL;
+    if (sink.fd < 0) return VX_EIO;
     int rc = tiled_run(K, key, opts, window_bits, d_work, work_bytes, host_t1, host_t1_bytes, sink,
                        t1_count, t2_count, stream);
-    if (close(sink.fd) != 0 && rc == VX_OK) rc = VX_ECUDA;
+    if (close(sink.fd) != 0 && rc == VX_OK) rc = VX_EIO;  // deferred write-back errors
     if (seconds)
         *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return rc;

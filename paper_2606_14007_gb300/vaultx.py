@@ -18,8 +18,8 @@ import threading
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libvaultx.so")
 
-VX_OK, VX_EINVAL, VX_ENOMEM, VX_ECUDA, VX_ETIMEDOUT, VX_EBUSY, VX_ENOTREADY, VX_EOVERFLOW = (
-    0, -1, -2, -3, -4, -5, -6, -7)
+VX_OK, VX_EINVAL, VX_ENOMEM, VX_ECUDA, VX_ETIMEDOUT, VX_EBUSY, VX_ENOTREADY, VX_EOVERFLOW, VX_EIO = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
 VX_TABLE1, VX_TABLE2 = 1, 2
 VX_TEST_WITHHOLD_PREFIX = 1
 VX_QUEUED, VX_RUNNING, VX_DONE, VX_FAILED = 0, 1, 2, 3
@@ -108,6 +108,8 @@ def lib():
             "vx_plot_batch": (c_int, [P(vp), c_int, vp]),
             "vx_plot_tiled_bytes": (c_int, [c_int, P(vx_opts), c_int, P(u64), P(u64), P(u64)]),
             "vx_plot_tiled_window_bits": (c_int, [c_int, P(vx_opts), u64, P(c_int)]),
+            "vx_plot_tiled_window_bits_capped": (c_int, [c_int, P(vx_opts), u64, u32, P(c_int)]),
+            "vx_plot_tiled_hash_passes": (c_int, [c_int, P(vx_opts), c_int, P(u32)]),
             "vx_plot_tiled": (c_int, [c_int, u8p, P(vx_opts), c_int, vp, u64, vp, u64, vp, u64, P(u64),
                                       P(u64), vp]),
             "vx_plot_tiled_write": (c_int, [c_int, u8p, P(vx_opts), c_int, vp, u64, ctypes.c_char_p, vp,
@@ -331,12 +333,28 @@ def vx_plot_tiled_bytes(K: int, window_bits: int, opts: vx_opts | None = None) -
     return a.value, b.value, c.value
 
 
-def vx_plot_tiled_window_bits(K: int, budget_bytes: int, opts: vx_opts | None = None) -> int:
-    """The fewest window bits whose tiled device footprint fits budget_bytes."""
+def vx_plot_tiled_window_bits(K: int, budget_bytes: int, opts: vx_opts | None = None,
+                              max_hash_passes: int | None = None) -> int:
+    """The fewest window bits whose tiled device footprint fits budget_bytes
+    (with at most max_hash_passes hashes of every nonce; default 2, the
+    window-id path)."""
     c = ctypes.c_int()
-    _check(lib().vx_plot_tiled_window_bits(K, ctypes.byref(opts) if opts else None, budget_bytes,
-                                           ctypes.byref(c)), "vx_plot_tiled_window_bits")
+    o = ctypes.byref(opts) if opts else None
+    if max_hash_passes is None:
+        _check(lib().vx_plot_tiled_window_bits(K, o, budget_bytes, ctypes.byref(c)),
+               "vx_plot_tiled_window_bits")
+    else:
+        _check(lib().vx_plot_tiled_window_bits_capped(K, o, budget_bytes, max_hash_passes, ctypes.byref(c)),
+               "vx_plot_tiled_window_bits_capped")
     return c.value
+
+
+def vx_plot_tiled_hash_passes(K: int, window_bits: int, opts: vx_opts | None = None) -> int:
+    """How many times a tiled plot hashes every nonce at window_bits."""
+    n = ctypes.c_uint32()
+    _check(lib().vx_plot_tiled_hash_passes(K, ctypes.byref(opts) if opts else None, window_bits,
+                                           ctypes.byref(n)), "vx_plot_tiled_hash_passes")
+    return n.value
 
 
 def vx_plot_tiled(K: int, key: bytes, window_bits: int, host_t1: int, host_t1_bytes: int,

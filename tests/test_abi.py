@@ -56,6 +56,7 @@ def test_library_is_sm103a_only():
 def test_strerror_and_version(vx):
     assert vx.strerror(0) == "ok"
     assert "overflow" in vx.strerror(vx.VX_EOVERFLOW)
+    assert "I/O" in vx.strerror(vx.VX_EIO)
     assert vx.lib().vx_version() >> 16 == 1
 
 
@@ -289,6 +290,32 @@ def test_tiled_window_bits_fit_a_budget(vx):
     assert ei.value.code == vx.VX_ENOMEM
 
 
+def test_tiled_hash_passes_and_the_capped_choice(vx):
+    # Whole plot: one hash of every nonce; 1..8 window bits: the id pass and
+    # each window's list, two; above 8 bits every window hashes every nonce.
+    assert vx.vx_plot_tiled_hash_passes(31, 0) == 1
+    for c in range(1, 9):
+        assert vx.vx_plot_tiled_hash_passes(31, c) == 2, c
+    assert vx.vx_plot_tiled_hash_passes(31, 9) == 512
+    assert vx.vx_plot_tiled_hash_passes(31, 10) == 1024
+    # nonce chunks turn the id pass off
+    assert vx.vx_plot_tiled_hash_passes(31, 3, vx.make_opts(pipeline_chunks=2)) == 8
+    # A budget between the 9-bit and the 8-bit footprints: the default choice
+    # refuses (it would hash the plot 512 times), the capped one takes 9 bits
+    # only when told that 512 passes are acceptable.
+    f8 = vx.vx_plot_tiled_bytes(31, 8)[0]
+    f9 = vx.vx_plot_tiled_bytes(31, 9)[0]
+    assert f9 < f8
+    budget = (f8 + f9) // 2
+    with pytest.raises(vx.VxError) as ei:
+        vx.vx_plot_tiled_window_bits(31, budget)
+    assert ei.value.code == vx.VX_ENOMEM
+    with pytest.raises(vx.VxError):
+        vx.vx_plot_tiled_window_bits(31, budget, max_hash_passes=511)
+    assert vx.vx_plot_tiled_window_bits(31, budget, max_hash_passes=512) == 9
+    assert vx.vx_plot_tiled_window_bits(31, f8, max_hash_passes=512) == 8
+
+
 def test_window_planner_sweep(vx):
     # Every K and every window count the planner accepts: a window's buffers
     # hold its share of the tables (Table 1 at least 12 B per expected record,
@@ -316,3 +343,13 @@ def test_window_planner_sweep(vx):
             if prev is not None and c >= 3:
                 assert dev < prev, (K, c, dev, prev)
             prev = dev
+
+
+def test_plot_file_that_cannot_be_opened_is_an_io_error(vx, tmp_path):
+    # The file is opened before any device work: a path in a missing
+    # directory gives VX_EIO, not VX_EINVAL (bad arguments) or VX_ECUDA.
+    path = str(tmp_path / "no_such_dir" / "plot.bin")
+    rc, _, _, _ = vx.vx_plot_tiled_write(12, bytes(32), 0, path, check=False, stream=0)
+    assert rc == vx.VX_EIO
+    rc, _, _, _ = vx.vx_plot_tiled_write(12, bytes(32), 40, path, check=False, stream=0)
+    assert rc == vx.VX_EINVAL  # bad window bits are still refused first
