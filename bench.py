@@ -312,6 +312,8 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="batch / large: every K plotted with the autotuner's plan (cached on disk)")
     ap.add_argument("--serve-streams", type=int, default=0, help="serve: concurrent waves (0 = library default)")
+    ap.add_argument("--serve-no-plain", action="store_true",
+                    help="serve: skip the one-at-a-time leg (a long latency run at a rate far below capacity)")
     ap.add_argument("--serve-max-wave", type=int, default=0, help="serve: plots per wave (0 = library default)")
     ap.add_argument("--serve-max-inflight", type=int, default=0,
                     help="serve: plots on the device at once (0 = library default)")
@@ -801,6 +803,15 @@ def run_serve(vx, args):
             time.sleep(max(0.0, min(0.002, arrivals[i][0] - (time.perf_counter() - t0))))
     served_s = time.perf_counter() - t0
     vx.vx_serve_destroy(srv)
+
+    if args.serve_no_plain:
+        return {"mode": "serve", "metric": "plot-request latency and aggregate nonces/s",
+                "unit": "nonces/s", "rate_per_s": args.rate, "duration_s": args.duration,
+                "requests": len(arrivals), "K_range": [22, 29],
+                "served": {"value": done_nonces / served_s, "p50_s": pct(lat, 50), "p99_s": pct(lat, 99),
+                           "completed": len(lat), "failed": failed, "wall_s": served_s,
+                           "how": "vx_serve_submit/poll: admission by HBM footprint"},
+                "one_at_a_time": None, "data": "synthetic"}
 
     # -- one at a time, first come first served, on one buffer set sized for K=29
     t1b, t2b, sb = vx.vx_plot_required_bytes(29)

@@ -210,14 +210,18 @@ int vx_match(vx_plot *plot, void *stream);
 /* Table 1 and Table 2 in one pass (Sec. III-A pipeline): key setup, keyed
  * BLAKE3 of every nonce fused with the first bucketing scatter level, the
  * second level, then the fused partition sort + match kernel.  That kernel
- * sorts each partition in shared memory, writes it to Table 1, and writes
- * its pairs {a, b} into Table 2 at the offset a decoupled look-back over the
- * earlier partitions gives.  A streaming pass then hashes the pairs in
- * place (vx_opts: fuse_pair_hash hashes inside the sort kernel instead,
- * t2_placement=2 stages the pairs in the partition slots).  Same tables as
- * vx_table1 + vx_match.  Ends with a 12-byte copy of the status and the
- * Table-2 count to pinned host memory and an event that vx_sync waits on.
- * Allocates if nothing is bound.  Asynchronous. */
+ * sorts each partition in shared memory and writes it to Table 1; its pairs
+ * {a, b} go either into Table 2 at the offset a decoupled look-back over
+ * the earlier partitions gives (t2_placement 1; a streaming pass then
+ * hashes them in place) or into the partition's own slot (t2_placement 2,
+ * the automatic choice when they fit; a scan of the pair counts and the
+ * slot pair hash then write Table 2).  fuse_pair_hash hashes inside the
+ * sort kernel instead.  Same tables as vx_table1 + vx_match.  Ends with a
+ * 12-byte copy of the status and the Table-2 count to pinned host memory
+ * and an event that vx_sync waits on.  Allocates if nothing is bound.
+ * Asynchronous.  One plot's runs must not overlap on the GPU (two runs of
+ * the same plot on different streams race on its buffers): different plots
+ * may run concurrently. */
 int vx_plot_run(vx_plot *plot, void *stream);
 
 /* Waits for the plot's work, reads its status word and Table-2 count, and

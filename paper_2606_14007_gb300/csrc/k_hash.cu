@@ -487,6 +487,7 @@ __global__ void __launch_bounds__(kT2HashThreads) k_t2_hash_slots(const Desc *__
     __syncthreads();
     const uint32_t total = s_rel[ng];
     const uint32_t cap = d.cap2;
+    if (s_base + total > d.t2cap) return;  // the scan flags this; never write past Table 2
     uint32_t g[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) g[i] = d.pre2[i];
@@ -499,6 +500,7 @@ __global__ void __launch_bounds__(kT2HashThreads) k_t2_hash_slots(const Desc *__
         t += s_rel[t + 1] <= q ? 1u : 0u;
         const uint32_t k = q - s_rel[t];
         const uint64_t f = fa + t;
+        if (k >= cap + cap / 2u) break;  // past the pair slot (the sort flags this)
         const uint2 ab = k < cap ? reinterpret_cast<const uint2 *>(d.b_keys + f * cap)[k]
                                  : reinterpret_cast<const uint2 *>(d.b_nonces + f * cap)[k - cap];
         uint32_t h0, h1;
