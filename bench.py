@@ -755,7 +755,8 @@ def run_batch_compare(vx, mix, steps, warmup, name, label, tune=False):
             "batched": {"value": nonces / (ms_batch / 1e3), "ms_per_step": ms_batch,
                         "how": "vx_plot_batch: grouped launches recorded into a CUDA graph"},
             "batched_over_plain": ms_plain / ms_batch, "equal_output": bool(equal),
-            "autotuned": {str(K): {"partition_log2": o.partition_log2, "scatter_mode": o.scatter_mode}
+            "autotuned": {str(K): {"partition_log2": o.partition_log2, "scatter_mode": o.scatter_mode,
+                                   "nonces_per_thread": o.nonces_per_thread}
                           for K, o in tuned.items()} or None,
             "steps": steps, "warmup": warmup, "data": "synthetic"}
 

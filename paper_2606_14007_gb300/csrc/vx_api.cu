@@ -1112,6 +1112,10 @@ struct BatchEntry {
     cudaStream_t cap_stream = nullptr;
     cudaStream_t aux = nullptr, aux_lo = nullptr;  // other branches of the recorded graph
     cudaEvent_t sync[vx::kSyncEvents] = {};
+    // the second lane: its own stream and branches, and the fork / join
+    cudaStream_t lane2 = nullptr, aux2 = nullptr, aux_lo2 = nullptr;
+    cudaEvent_t sync2[vx::kSyncEvents] = {};
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 std::mutex g_batch_mu;
@@ -1134,6 +1138,10 @@ void drop_batch(BatchEntry *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     vx::free_lanes(b->aux, b->aux_lo, b->sync);
+    if (b->lane2) cudaStreamDestroy(b->lane2);
+    vx::free_lanes(b->aux2, b->aux_lo2, b->sync2);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
     cudaFree(b->d_ws);
     cudaFreeHost(b->h_ws);
     delete b;
@@ -1230,27 +1238,63 @@ extern "C" int vx_plot_batch(vx_plot *const *plots, int n, void *stream)
         b = new BatchEntry();
         b->plots.assign(plots, plots + n);
         for (int i = 0; i < n; ++i) b->bufs.push_back(plots[i]->d_scratch);
-        b->ws_bytes = vx::batch_ws_bytes(n);
+        // Two lanes of grouped launches, balanced by nonces (largest plots
+        // first, each to the lighter lane), recorded on two branches of the
+        // graph so that one lane's kernels can run beside the other's.
+        std::vector<int> order(n);
+        for (int i = 0; i < n; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return plots[x]->plan.N > plots[y]->plan.N; });
+        std::vector<vx_plot *> lane[2];
+        uint64_t load[2] = {0, 0};
+        for (int i : order) {
+            const int l = n >= 2 && load[1] < load[0] ? 1 : 0;
+            lane[l].push_back(plots[i]);
+            load[l] += plots[i]->plan.N;
+        }
+        const int nl = lane[1].empty() ? 1 : 2;
+        const size_t ws0 = (vx::batch_ws_bytes((int)lane[0].size()) + 255) & ~(size_t)255;
+        b->ws_bytes = ws0 + (nl == 2 ? vx::batch_ws_bytes((int)lane[1].size()) : 0);
         if (cudaMallocHost((void **)&b->h_ws, b->ws_bytes) != cudaSuccess ||
             dev_alloc((void **)&b->d_ws, b->ws_bytes) != cudaSuccess) {
             cudaGetLastError();
             drop_batch(b);
             return VX_ENOMEM;
         }
-        LaunchSet L;
-        if (vx::batch_prepare(plots, n, b->h_ws, b->d_ws, &L) != VX_OK) {
-            drop_batch(b);
-            return VX_EINVAL;
+        LaunchSet L[2];
+        for (int l = 0; l < nl; ++l) {
+            const size_t at = l ? ws0 : 0;
+            if (vx::batch_prepare(lane[l].data(), (int)lane[l].size(), b->h_ws + at, b->d_ws + at, &L[l]) !=
+                VX_OK) {
+                drop_batch(b);
+                return VX_EINVAL;
+            }
         }
         // The workspace is uploaded once; replays of the graph reuse it.
         cudaError_t e = cudaMemcpy(b->d_ws, b->h_ws, b->ws_bytes, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = vx::make_lanes(&b->aux, &b->aux_lo, b->sync);
+        if (e == cudaSuccess && nl == 2) {
+            e = cudaStreamCreateWithFlags(&b->lane2, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = vx::make_lanes(&b->aux2, &b->aux_lo2, b->sync2);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+        }
         cudaGraph_t g = nullptr;
         if (e == cudaSuccess) e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            const vx::Lanes ln{b->cap_stream, b->aux, b->aux_lo, b->sync};
-            cudaError_t e1 = vx::launch_plot_seq(L, ln);
+            cudaError_t e1 = cudaSuccess;
+            if (nl == 2) {
+                e1 = cudaEventRecord(b->fork, b->cap_stream);
+                if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(b->lane2, b->fork, 0);
+            }
+            if (e1 == cudaSuccess)
+                e1 = vx::launch_plot_seq(L[0], vx::Lanes{b->cap_stream, b->aux, b->aux_lo, b->sync});
+            if (e1 == cudaSuccess && nl == 2) {
+                e1 = vx::launch_plot_seq(L[1], vx::Lanes{b->lane2, b->aux2, b->aux_lo2, b->sync2});
+                if (e1 == cudaSuccess) e1 = cudaEventRecord(b->join, b->lane2);
+                if (e1 == cudaSuccess) e1 = cudaStreamWaitEvent(b->cap_stream, b->join, 0);
+            }
             e = cudaStreamEndCapture(b->cap_stream, &g);
             if (e == cudaSuccess) e = e1;
         }

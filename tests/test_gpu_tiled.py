@@ -225,7 +225,7 @@ def test_tiled_plot_file_equals_whole_plot_file(vx, tmp_path):
 def test_tiled_plot_file_bad_path(vx, tmp_path):
     rc, _, _, _ = vx.vx_plot_tiled_write(16, plot_key(90), 2, str(tmp_path / "no" / "such" / "dir.bin"),
                                          check=False)
-    assert rc == vx.VX_EINVAL
+    assert rc == vx.VX_EIO  # the file cannot be opened: an I/O error, before any device work
 
 
 def test_tiled_plots_in_a_caller_work_buffer(vx, tmp_path):
