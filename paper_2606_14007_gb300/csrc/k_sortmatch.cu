@@ -150,26 +150,106 @@ __device__ __forceinline__ void counts_to_starts(uint32_t *DC, uint32_t M, uint3
     __syncthreads();
 }
 
+// True when the M counter words fill whole rows of 32 per warp, at most R
+// rows each: the shape in which counts_to_starts needs no general block
+// scan, and the one counts_to_starts_packed requires.
+template <int NT, int R>
+__host__ __device__ __forceinline__ bool rows_shape(uint32_t M)
+{
+    constexpr uint32_t NW = NT / 32;
+    return M >= 32u * NW && M <= 32u * NW * R && M % (32u * NW) == 0;
+}
+
+// counts_to_starts for 2M digit counters of 16 bits, two to a word (digit
+// 2w in the low half of word w, 2w + 1 in the high half; every count and
+// start below 2^16).  The words must have rows_shape<NT, R>.  Each word's
+// two counts become their run starts: the exclusive prefix P of the
+// word sums, and P plus the low count.  Ends with a barrier.
+template <int NT, int R>
+__device__ __forceinline__ void counts_to_starts_packed(uint32_t *DC, uint32_t M, uint32_t *WS)
+{
+    constexpr uint32_t NW = NT / 32;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t rows = M / (32u * NW);
+    uint32_t *row0 = DC + warp * rows * 32u + lane;
+    uint32_t lo[R], v[R], incl[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const uint32_t w = (uint32_t)j < rows ? row0[32 * j] : 0u;
+        lo[j] = w & 0xFFFFu;
+        v[j] = lo[j] + (w >> 16);
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) incl[j] = warp_incl_scan(v[j]);
+    uint32_t run = 0;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const uint32_t t = __shfl_sync(0xffffffffu, incl[j], 31);
+        incl[j] += run - v[j];
+        run += t;
+    }
+    if (lane == 0) WS[warp] = run;
+    __syncthreads();
+    uint32_t carry = 0;
+#pragma unroll
+    for (uint32_t w = 0; w < NW; ++w) carry += w < warp ? WS[w] : 0u;
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+        if ((uint32_t)j < rows) {
+            const uint32_t P = carry + incl[j];
+            row0[32 * j] = P | ((P + lo[j]) << 16);
+        }
+    __syncthreads();
+}
+
 // Ping-pong sort of the n records in buffer X (keys XK, nonces XN):
 // digit histogram, scan, then each record placed by digit into buffer Y (a
 // digit's run in arrival order); then every position of Y, 32 per warp
 // step, finds its record's rank inside its run (runs hold about one
 // record; a run of L compares L records) and writes the record to that
 // place of X.  X ends sorted, Y is free.
-template <int NT>
+//
+// PACK: 16-bit digit counters, two to a word, so that the same counter
+// words hold twice the digits (ndig digits in ndig / 2 words, which must
+// have rows_shape; n < 2^16).  Runs then hold about half a record, and
+// fewer of them need ranking.
+//
+// DRAIN: buffer Y may still be the source of thread 0's bulk stores (the
+// previous item's staged pairs); their reads must end before the records
+// are placed into it, so thread 0 waits for them after the histogram and
+// the scan, which overlap the stores.
+template <int NT, bool PACK, bool DRAIN>
 __device__ __forceinline__ void sort_pingpong(const Part &A, uint64_t *XK, uint32_t *XN, uint64_t *YK,
                                               uint32_t *YN, uint32_t n, int shift, uint32_t ndig)
 {
     constexpr uint32_t NW = NT / 32;
     const uint32_t dmask = ndig - 1u;
+    // digit g's counter: word g (PACK: word g / 2, the half g & 1)
+    auto bump = [&](uint32_t g) -> uint32_t {
+        if (PACK) {
+            const uint32_t h = (g & 1u) << 4;
+            return (atomicAdd(&A.DC[g >> 1], 1u << h) >> h) & 0xFFFFu;
+        }
+        return atomicAdd(&A.DC[g], 1u);
+    };
+    const uint16_t *DC16 = reinterpret_cast<const uint16_t *>(A.DC);
+    // end of run g once the records are placed (little-endian halves)
+    auto run_end = [&](uint32_t g) -> uint32_t { return PACK ? (uint32_t)DC16[g] : A.DC[g]; };
 #pragma unroll 4
-    for (uint32_t i = threadIdx.x; i < n; i += NT) atomicAdd(&A.DC[(uint32_t)(XK[i] >> shift) & dmask], 1u);
+    for (uint32_t i = threadIdx.x; i < n; i += NT) bump((uint32_t)(XK[i] >> shift) & dmask);
     __syncthreads();
-    counts_to_starts<NT, 8>(A.DC, ndig, A.WS);
+    if (PACK)
+        counts_to_starts_packed<NT, 8>(A.DC, ndig >> 1, A.WS);
+    else
+        counts_to_starts<NT, 8>(A.DC, ndig, A.WS);
+    if (DRAIN) {
+        if (threadIdx.x == 0) bulk_wait_all<true>();
+        __syncthreads();
+    }
 #pragma unroll 4
     for (uint32_t i = threadIdx.x; i < n; i += NT) {
         const uint64_t k = XK[i];
-        const uint32_t pos = atomicAdd(&A.DC[(uint32_t)(k >> shift) & dmask], 1u);
+        const uint32_t pos = bump((uint32_t)(k >> shift) & dmask);
         YK[pos] = k;
         YN[pos] = XN[i];
     }
@@ -193,8 +273,8 @@ __device__ __forceinline__ void sort_pingpong(const Part &A, uint64_t *XK, uint3
         const uint64_t ka = YK[xa], kb = YK[xb];
         const uint32_t na = YN[xa], nb = YN[xb];
         const uint32_t ga = (uint32_t)(ka >> shift) & dmask, gb = (uint32_t)(kb >> shift) & dmask;
-        const uint32_t sa = ga ? A.DC[ga - 1] : 0u, sb = gb ? A.DC[gb - 1] : 0u;
-        const uint32_t ea = va ? A.DC[ga] : 0u, eb = vb ? A.DC[gb] : 0u;
+        const uint32_t sa = ga ? run_end(ga - 1) : 0u, sb = gb ? run_end(gb - 1) : 0u;
+        const uint32_t ea = va ? run_end(ga) : 0u, eb = vb ? run_end(gb) : 0u;
         const uint32_t lmax = __reduce_max_sync(0xffffffffu, max(va ? ea - sa : 0u, vb ? eb - sb : 0u));
         uint32_t da = sa, db = sb;
         if (lmax > 1) {
@@ -557,6 +637,23 @@ struct Item {
     bool ok;
 };
 
+// Starts an L2 prefetch of the filled part of partition f's slot (f below
+// 2^p), so that the reads that come for it later hit L2.  (Two items ahead
+// in the persistent front end it measured 1% slower: its bulk copies do not
+// wait on DRAM latency.)
+__device__ __forceinline__ void prefetch_slot_l2(const Desc &d, uint32_t f)
+{
+    const uint32_t nf = min(d.cnt2[f], d.cap2);
+    if (!nf) return;
+    const uint32_t nk = (nf + 1u) & ~1u, nn = (nf + 3u) & ~3u;  // 16-byte multiples
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_keys + (uint64_t)f * d.cap2),
+                 "r"(nk * 8u)
+                 : "memory");
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_nonces + (uint64_t)f * d.cap2),
+                 "r"(nn * 4u)
+                 : "memory");
+}
+
 template <bool EMIT>
 __device__ __forceinline__ Item take_item(const Desc *__restrict__ descs, int nplots,
                                           const uint32_t *__restrict__ tile_start, uint32_t t)
@@ -651,9 +748,6 @@ __global__ void __launch_bounds__(kPipeThreads, MODE == kSortHash ? 2 : 3)
             for (uint32_t i = threadIdx.x; i < ndig; i += NT) A.DC[i] = 0u;
         }
         const uint64_t off = valid ? d.t1off[f] : 0ull;
-        // The previous item's staged pairs must have left the buffer this
-        // item places its records into.
-        if (SLOTS_MODE(MODE) && threadIdx.x == 0) bulk_wait_all<true>();
         // The slot copy was started during the previous item (or above).
         if (!__syncthreads_and(mbar_wait(bar, phase, d.spin_limit))) {
             if (threadIdx.x == 0) atomicOr(d.status, kStTimeout);
@@ -662,9 +756,19 @@ __global__ void __launch_bounds__(kPipeThreads, MODE == kSortHash ? 2 : 3)
         }
         A.SK = rb ? YK : XK;
         A.SN = rb ? YN : XN;
-        if (valid) sort_pingpong<NT>(A, A.SK, A.SN, rb ? XK : YK, rb ? XN : YN, n, 64 - d.pk - d.dbits, ndig);
-        // The other buffer is free: start the next item's copy into it.
+        // One more digit bit in the same counter words where they allow it.
+        const int shift = 64 - d.pk - d.dbits;
+        // The previous item's staged pairs leave the buffer this item
+        // places its records into while the sort counts its digits.
+        constexpr bool DR = SLOTS_MODE(MODE);
+        if (valid && n < 0x10000u && rows_shape<NT, 8>(ndig))
+            sort_pingpong<NT, true, DR>(A, A.SK, A.SN, rb ? XK : YK, rb ? XN : YN, n, shift - 1, ndig << 1);
+        else if (valid)
+            sort_pingpong<NT, false, DR>(A, A.SK, A.SN, rb ? XK : YK, rb ? XN : YN, n, shift, ndig);
+        // The other buffer is free: start the next item's copy into it
+        // (after the staged pairs' reads, already over unless no sort ran).
         if (threadIdx.x == 0) {
+            if (DR) bulk_wait_all<true>();
             if (nx.ok) launch_copy(nx, nx_n, rb ^ 1);
             nx = nn;
             nn.ok = false;
@@ -708,18 +812,7 @@ __global__ void __launch_bounds__(kGlThreads, MODE == kSortHash ? 2 : 3)
     // Warm L2 with the filled part of the slot kSlotPrefetchAhead tickets
     // ahead, so that its CTA's reads hit L2.
     const uint64_t fa = (uint64_t)f + kSlotPrefetchAhead;
-    if (threadIdx.x == 0 && fa < (1ull << d.p)) {
-        const uint32_t nfa = min(d.cnt2[fa], cap);
-        if (nfa) {
-            const uint32_t nk = (nfa + 1u) & ~1u, nn = (nfa + 3u) & ~3u;  // 16-byte multiples
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_keys + fa * cap),
-                         "r"(nk * 8u)
-                         : "memory");
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_nonces + fa * cap),
-                         "r"(nn * 4u)
-                         : "memory");
-        }
-    }
+    if (threadIdx.x == 0 && fa < (1ull << d.p)) prefetch_slot_l2(d, (uint32_t)fa);
     const uint32_t n = min(d.cnt2[f], cap);
     const uint64_t off = d.t1off[f];
     __syncthreads();
