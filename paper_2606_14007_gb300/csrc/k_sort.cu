@@ -123,7 +123,12 @@ __global__ void __launch_bounds__(kScatterThreads) k_scatter2(const Desc *__rest
     __syncthreads();
     const uint32_t cap = d.cap2;
     bool overflow = false, hover = false;
-    for (uint32_t i = threadIdx.x; i < count; i += NT) {
+    // unrolled over the thread's PER records so that their dependent
+    // shared-memory reads (key, then its bin's bases) overlap
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const uint32_t i = (uint32_t)j * NT + threadIdx.x;
+        if (i >= count) break;
         const uint64_t k = sm.keys[i];
         const uint32_t bin = (uint32_t)(k >> shift) & bin_mask;
         const uint32_t g = sm.gbase[bin] + (i - sm.loff[bin]);
