@@ -7,13 +7,17 @@
 // fusion (a partition never leaves shared memory between sort and match).
 // Changed: a physical partition (a run of whole logical buckets, ~2048
 // records) per work item, a counting sort on the key bits below the
-// partition prefix (about one record per digit) whose digit runs are then
-// ordered by (key64, nonce), and the partition's Table-2 base found by a
-// decoupled look-back over the partitions before it (partition order comes
-// from a ticket counter, so every partition an item waits on is held by a
-// running CTA; every wait is bounded and a timeout poisons the chain
-// instead of hanging).  With the cross-bucket match (HALO instances) the
-// next partition's halo is sorted in behind the partition's records.
+// partition prefix (about one record per digit, half a record with the
+// 16-bit counters of the persistent front end) whose digit runs are then
+// ordered by (key64, nonce).  A partition's pairs either go to its own slot
+// (kSortSlots, the default wherever the plan shows the pair slot safe: no
+// partition waits on another, a scan and the slot pair hash place them) or
+// straight to Table 2 at a base found by a decoupled look-back over the
+// partitions before it (partition order comes from a ticket counter, so
+// every partition an item waits on is held by a running CTA; every wait is
+// bounded and a timeout poisons the chain instead of hanging).  With the
+// cross-bucket match (HALO instances) the next partition's halo is sorted
+// in behind the partition's records.
 //
 // After the sort every step walks the sorted records in chunks of 32, one
 // record per lane, each warp over its own run of chunks: the pair counts
