@@ -309,6 +309,10 @@ def main():
                     help="0 pairs inside a logical bucket, 1 cross-bucket")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: requests per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serve: seconds of arrivals")
+    ap.add_argument("--sweep-oracle-max-k", type=int, default=27,
+                    help="sweep: largest K of the all-core oracle timed (larger K extrapolated)")
+    ap.add_argument("--sweep-oracle-1t-max-k", type=int, default=23,
+                    help="sweep: largest K of the single-thread oracle timed")
     ap.add_argument("--autotune", action="store_true",
                     help="batch / large: every K plotted with the autotuner's plan (cached on disk)")
     ap.add_argument("--serve-streams", type=int, default=0, help="serve: concurrent waves (0 = library default)")
@@ -644,9 +648,10 @@ def run_sweep(vx, args):
     from seed K), device ms per plot (CUDA events on the launching stream,
     `steps` timed after `warmup`), nonces/s, the per-kernel split, and
     T(k+1)/T(k); beside them the oracle on the host cores: single-thread
-    (plain oracle) measured at K = 20 .. 23, all cores (its all-core
-    variant) measured at K = 20 .. 27, larger K extrapolated as N log N from
-    the largest measured K and labelled so."""
+    (plain oracle) measured at K = 20 .. --sweep-oracle-1t-max-k, all cores
+    (its all-core variant) at K = 20 .. --sweep-oracle-max-k, each only
+    while its tables fit the free host memory; larger K extrapolated as
+    N log N from the largest measured K and labelled so."""
     import torch
     from oracle import oracle as orc
     from paper_2606_14007_gb300.inputs import plot_key
@@ -675,11 +680,25 @@ def run_sweep(vx, args):
     orc.build()
     threads = os.cpu_count() or 1
     single, allc = {}, {}
-    for K in (20, 21, 22, 23):
+
+    def fits(K):
+        # Table 1 and its sort scratch, then Table 1 and Table 2: at most
+        # about 30 bytes per nonce at once, with a quarter of the memory spare
+        try:
+            free = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        except (ValueError, OSError):
+            return K <= 27
+        return 30 * (1 << K) <= 0.75 * free
+
+    for K in range(20, args.sweep_oracle_1t_max_k + 1):
+        if not fits(K):
+            break
         t0 = time.perf_counter()
         orc.plot(K, plot_key(K))
         single[K] = time.perf_counter() - t0
-    for K in range(20, 28):
+    for K in range(20, args.sweep_oracle_max_k + 1):
+        if not fits(K):
+            break
         t0 = time.perf_counter()
         orc.plot_allcores(K, plot_key(K), threads)
         allc[K] = time.perf_counter() - t0
