@@ -309,11 +309,12 @@ __global__ void __launch_bounds__(256) k_s2_scan(const Sort2Desc *__restrict__ d
 
 // ------------------------------------------------------- partition sort
 // One CTA per partition: counting sort on the dbits key bits below the
-// partition prefix, insertion sort of each digit run by (key2, a, b), and
-// the records {a, b, hash2} written at the partition's offset.  Shared
-// memory holds each record's key and its index in the slot (12 B with the
-// digit rank), five CTAs per SM; the packed pair is read from the slot (L2)
-// when the record is written out, or when two keys tie.
+// partition prefix, then each record ranked inside its digit run by
+// (key2, a, b) with warp shuffles and written straight to its place at the
+// partition's offset as {a, b, hash2}.  Shared memory holds each record's
+// key and its index in the slot (12 B with the digit rank); the packed pair
+// is read from the slot (L2) when the record is written out, or when two
+// keys tie.
 constexpr uint32_t kS2PrefetchAhead = 384;  // partitions ahead: ~half the resident CTAs
 
 struct S2SortLayout {
@@ -374,31 +375,86 @@ __global__ void __launch_bounds__(kS2SortThreads, 5) k_s2_sort(const Sort2Desc *
         SI[pos] = (uint16_t)i;
     }
     __syncthreads();
-    for (uint32_t dg = threadIdx.x; dg < ndig; dg += NT) {
-        const uint32_t s0 = DC[dg];
-        const uint32_t s1 = dg + 1 < ndig ? DC[dg + 1] : n;
-        for (uint32_t a = s0 + 1; a < s1; ++a) {
-            const uint64_t kx = SK[a];
-            const uint16_t ix = SI[a];
-            uint32_t b = a;
-            while (b > s0) {
-                const uint64_t ky = SK[b - 1];
-                // equal keys (rare): order by the packed pair (a << 32 | b)
-                if (ky < kx || (ky == kx && __ldg(iv + SI[b - 1]) < __ldg(iv + ix))) break;
-                SK[b] = ky;
-                SI[b] = SI[b - 1];
-                --b;
-            }
-            SK[b] = kx;
-            SI[b] = ix;
-        }
-    }
-    __syncthreads();
+    // DC[g] is the start of run g (records of digit g in arrival order);
+    // the run ends at DC[g + 1] (n for the last digit).  Every position, 32
+    // per warp step and one per lane, finds its record's rank inside its run
+    // and the record goes straight to its place in the sorted table.  A
+    // run's records sit in neighbouring lanes, so each lane compares with
+    // the lanes up to the longest run's length away (shuffles, every lane
+    // in step) on a 32-bit compare key: the key bits below the digit, or
+    // their top 32 (records of a run agree above them).  A lane whose run
+    // leaves its chunk, or that meets an equal compare key, ranks itself
+    // from shared memory on full keys, then on the packed pairs (a << 32 |
+    // b) for equal keys.  Two chunks per step so that their work overlaps.
     uint4 *__restrict__ out = d.t2 + o;
-    for (uint32_t r = threadIdx.x; r < n; r += NT) {
-        const uint64_t k = SK[r], v = __ldg(iv + SI[r]);
-        out[r] = make_uint4((uint32_t)(v >> 32), (uint32_t)v, bswap32((uint32_t)(k >> 32)),
-                            bswap32((uint32_t)k));
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    constexpr uint32_t NW = NT / 32;
+    const uint32_t nch = (n + 31u) >> 5;
+    const int cs = shift > 32 ? shift - 32 : 0;
+    auto run_bounds = [&](uint64_t k, uint32_t &s0, uint32_t &s1) {
+        const uint32_t g = (uint32_t)(k >> shift) & dmask;
+        s0 = DC[g];
+        s1 = g + 1 < ndig ? DC[g + 1] : n;
+    };
+    // place of the record (k, slot index ix) among the run [s0, s1)
+    auto rank_slow = [&](uint64_t k, uint16_t ix, uint32_t s0, uint32_t s1) -> uint32_t {
+        uint32_t r = s0;
+        uint64_t v = 0;
+        bool have_v = false;
+        for (uint32_t q = s0; q < s1; ++q) {
+            const uint64_t kq = SK[q];
+            if (kq < k) {
+                ++r;
+            } else if (kq == k && SI[q] != ix) {
+                if (!have_v) {
+                    v = __ldg(iv + ix);
+                    have_v = true;
+                }
+                r += __ldg(iv + SI[q]) < v ? 1u : 0u;
+            }
+        }
+        return r;
+    };
+    for (uint32_t c = warp; c < nch; c += 2 * NW) {
+        const uint32_t pa = 32u * c + lane, pb = pa + 32u * NW;
+        const bool va = pa < n, vb = pb < n;
+        const uint32_t xa = va ? pa : 0u, xb = vb ? pb : 0u;
+        const uint64_t ka = SK[xa], kb = SK[xb];
+        const uint16_t ia = SI[xa], ib = SI[xb];
+        uint32_t sa, ea, sb, eb;
+        run_bounds(ka, sa, ea);
+        run_bounds(kb, sb, eb);
+        if (!va) sa = ea = 0u;
+        if (!vb) sb = eb = 0u;
+        const uint32_t lmax = __reduce_max_sync(0xffffffffu, max(ea - sa, eb - sb));
+        uint32_t da = sa, db = sb;
+        if (lmax > 1) {
+            const uint32_t qa = (uint32_t)(ka >> cs), qb = (uint32_t)(kb >> cs);
+            bool slow_a = va && (sa < 32u * c || ea > 32u * c + 32u);
+            bool slow_b = vb && (sb < 32u * (c + NW) || eb > 32u * (c + NW) + 32u);
+            for (uint32_t t = 1; t < lmax; ++t) {
+                const uint32_t da_ = __shfl_down_sync(0xffffffffu, qa, t), ua = __shfl_up_sync(0xffffffffu, qa, t);
+                const uint32_t db_ = __shfl_down_sync(0xffffffffu, qb, t), ub = __shfl_up_sync(0xffffffffu, qb, t);
+                const bool ina_d = pa + t < ea, ina_u = lane >= t && pa - t >= sa;
+                const bool inb_d = pb + t < eb, inb_u = lane >= t && pb - t >= sb;
+                da += (ina_d && da_ < qa ? 1u : 0u) + (ina_u && ua < qa ? 1u : 0u);
+                db += (inb_d && db_ < qb ? 1u : 0u) + (inb_u && ub < qb ? 1u : 0u);
+                slow_a = slow_a || (ina_d && da_ == qa) || (ina_u && ua == qa);
+                slow_b = slow_b || (inb_d && db_ == qb) || (inb_u && ub == qb);
+            }
+            if (va && slow_a) da = rank_slow(ka, ia, sa, ea);
+            if (vb && slow_b) db = rank_slow(kb, ib, sb, eb);
+        }
+        if (va) {
+            const uint64_t v = __ldg(iv + ia);
+            out[da] = make_uint4((uint32_t)(v >> 32), (uint32_t)v, bswap32((uint32_t)(ka >> 32)),
+                                 bswap32((uint32_t)ka));
+        }
+        if (vb) {
+            const uint64_t v = __ldg(iv + ib);
+            out[db] = make_uint4((uint32_t)(v >> 32), (uint32_t)v, bswap32((uint32_t)(kb >> 32)),
+                                 bswap32((uint32_t)kb));
+        }
     }
 }
 
