@@ -307,6 +307,43 @@ __global__ void __launch_bounds__(256) k_s2_scan(const Sort2Desc *__restrict__ d
     }
 }
 
+// In-place exclusive scan of 2M digit counters of 16 bits, two to a word
+// (digit 2w in the low half of word w, 2w + 1 in the high half; every
+// count and start below 2^16), by a CTA of NT threads: each word's two
+// counts become their starts.  Warp w takes a contiguous run of the words,
+// 32 at a time; `ws` holds NT/32 words.  Ends with a __syncthreads.
+template <int NT>
+__device__ __forceinline__ void block_scan_packed16(uint32_t *A, uint32_t M, uint32_t *ws)
+{
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t chunk = (M + NW - 1) / NW;
+    const uint32_t lo = min(M, (uint32_t)warp * chunk), hi = min(M, lo + chunk);
+    uint32_t sum = 0;
+    for (uint32_t i = lo + lane; i < hi; i += 32) sum += (A[i] & 0xFFFFu) + (A[i] >> 16);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) ws[warp] = sum;
+    __syncthreads();
+    uint32_t carry = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) carry += w < warp ? ws[w] : 0u;
+    for (uint32_t base = lo; base < hi; base += 32) {
+        const uint32_t i = base + lane;
+        const uint32_t a = i < hi ? A[i] : 0u, l = a & 0xFFFFu, v = l + (a >> 16);
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t P = carry + incl - v;
+        if (i < hi) A[i] = P | ((P + l) << 16);
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    __syncthreads();
+}
+
 // ------------------------------------------------------- partition sort
 // One CTA per partition: counting sort on the dbits key bits below the
 // partition prefix, then each record ranked inside its digit run by
@@ -349,16 +386,21 @@ __global__ void __launch_bounds__(kS2SortThreads, 5) k_s2_sort(const Sort2Desc *
     const uint64_t o = d.off[f];
     const uint64_t *__restrict__ ik = d.b_keys + (uint64_t)f * cap;
     const uint64_t *__restrict__ iv = d.b_vals + (uint64_t)f * cap;
-    const int shift = 64 - d.p - dbits;
-    const uint32_t dmask = ndig - 1u;
+    // one more digit bit than the plan's in the same counter words: 16-bit
+    // counters, two to a word (n < 2^16), runs of about half the records
+    const int shift = 64 - d.p - dbits - 1;
+    const uint32_t pdig = ndig << 1, dmask = pdig - 1u;
+    const uint16_t *DC16 = reinterpret_cast<const uint16_t *>(DC);
     // the filled part of the slot kS2PrefetchAhead partitions ahead goes to
     // L2 after step 1 (its fill count is read now)
     const uint64_t fa = (uint64_t)f + kS2PrefetchAhead;
     const uint32_t nfa = (threadIdx.x == 0 && fa < (1ull << d.p)) ? min(d.cnt2[fa], cap) : 0u;
     for (uint32_t i = threadIdx.x; i < ndig; i += NT) DC[i] = 0u;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n; i += NT)
-        RK[i] = (uint16_t)atomicAdd(&DC[(uint32_t)(__ldg(ik + i) >> shift) & dmask], 1u);
+    for (uint32_t i = threadIdx.x; i < n; i += NT) {
+        const uint32_t g = (uint32_t)(__ldg(ik + i) >> shift) & dmask, h = (g & 1u) << 4;
+        RK[i] = (uint16_t)(atomicAdd(&DC[g >> 1], 1u << h) >> h);
+    }
     if (nfa) {
         const uint32_t nb = ((nfa + 1u) & ~1u) * 8u;  // 16-byte multiple (cap is even)
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(d.b_keys + fa * cap), "r"(nb)
@@ -367,16 +409,16 @@ __global__ void __launch_bounds__(kS2SortThreads, 5) k_s2_sort(const Sort2Desc *
                      : "memory");
     }
     __syncthreads();
-    block_scan_inplace_u32<NT>(DC, ndig, WS);
+    block_scan_packed16<NT>(DC, ndig, WS);
     for (uint32_t i = threadIdx.x; i < n; i += NT) {
         const uint64_t k = __ldg(ik + i);
-        const uint32_t pos = DC[(uint32_t)(k >> shift) & dmask] + RK[i];
+        const uint32_t pos = DC16[(uint32_t)(k >> shift) & dmask] + RK[i];
         SK[pos] = k;
         SI[pos] = (uint16_t)i;
     }
     __syncthreads();
-    // DC[g] is the start of run g (records of digit g in arrival order);
-    // the run ends at DC[g + 1] (n for the last digit).  Every position, 32
+    // DC16[g] is the start of run g (records of digit g in arrival order);
+    // the run ends at DC16[g + 1] (n for the last digit).  Every position, 32
     // per warp step and one per lane, finds its record's rank inside its run
     // and the record goes straight to its place in the sorted table.  A
     // run's records sit in neighbouring lanes, so each lane compares with
@@ -393,8 +435,8 @@ __global__ void __launch_bounds__(kS2SortThreads, 5) k_s2_sort(const Sort2Desc *
     const int cs = shift > 32 ? shift - 32 : 0;
     auto run_bounds = [&](uint64_t k, uint32_t &s0, uint32_t &s1) {
         const uint32_t g = (uint32_t)(k >> shift) & dmask;
-        s0 = DC[g];
-        s1 = g + 1 < ndig ? DC[g + 1] : n;
+        s0 = DC16[g];
+        s1 = g + 1 < pdig ? DC16[g + 1] : n;
     };
     // place of the record (k, slot index ix) among the run [s0, s1)
     auto rank_slow = [&](uint64_t k, uint16_t ix, uint32_t s0, uint32_t s1) -> uint32_t {
