@@ -125,7 +125,12 @@ __global__ void __launch_bounds__(kS2Threads) k_s2_scatter1(const Sort2Desc *__r
     __syncthreads();
     const uint32_t count = (uint32_t)(n - base < kS2Tile1 ? n - base : kS2Tile1);
     bool overflow = false;
-    for (uint32_t i = threadIdx.x; i < count; i += NT) {
+    // unrolled over the thread's PER records so that their dependent
+    // shared-memory reads (key, then its bin's bases) overlap
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const uint32_t i = (uint32_t)j * NT + threadIdx.x;
+        if (i >= count) break;
         const uint64_t k = sm.keys[i];
         const uint32_t bin = bits ? (uint32_t)(k >> (64 - bits)) : 0u;
         const uint32_t g = sm.gbase[bin] + (i - sm.loff[bin]);
@@ -237,7 +242,10 @@ __global__ void __launch_bounds__(kS2BThreads) k_s2_scatter2(const Sort2Desc *__
     __syncthreads();
     const uint32_t cap = d.cap2;
     bool overflow = false;
-    for (uint32_t i = threadIdx.x; i < count; i += NT) {
+#pragma unroll
+    for (int j = 0; j < (int)(kS2Tile2 / kS2BThreads); ++j) {
+        const uint32_t i = (uint32_t)j * NT + threadIdx.x;
+        if (i >= count) break;
         const uint64_t k = sm.keys[i];
         const uint32_t bin = (uint32_t)(k >> shift) & bin_mask;
         const uint32_t g = sm.gbase[bin] + (i - sm.loff[bin]);
