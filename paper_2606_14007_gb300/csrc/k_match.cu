@@ -88,33 +88,58 @@ __global__ void __launch_bounds__(kMatchThreads) k_match(const Desc *__restrict_
     }
     __syncthreads();
 
-    // Per-record pair counts over a contiguous chunk of records per thread.
+    // Per-record pair counts, chunks of 32 sorted records (one per lane),
+    // warp w over chunks [c0, c1): the later records up to lim =
+    // min(last key of r's logical bucket, key_r + D - 1), or key_r + D - 1
+    // for the cross-bucket match (four probes, then one by one while all
+    // four match), and their warp scans.  Probes may read up to four
+    // entries past the records: inside the shared allocation, and masked.
     const bool global = d.scope != 0;
-    const uint32_t per = (n + NT - 1) / NT;
-    const uint32_t r0 = min(n, threadIdx.x * per), r1 = min(n, r0 + per);
-    uint32_t mine = 0;
-    for (uint32_t r = r0; r < r1; ++r) {
-        const uint64_t k = keys[r];
-        const uint64_t bucket = k >> 40;
-        uint32_t c = 0;
-        for (uint32_t r2 = r + 1; r2 < nt; ++r2) {
-            const uint64_t k2 = keys[r2];
-            if ((!global && (k2 >> 40) != bucket) || k2 - k >= D) break;
-            ++c;
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    constexpr uint32_t NW = NT / 32;
+    const uint32_t nch = (n + 31u) >> 5;
+    const uint32_t c0 = warp * nch / NW, c1 = (warp + 1) * nch / NW;
+    uint32_t carry = 0;  // the warp's pairs before the current chunk
+    for (uint32_t c = c0; c < c1; ++c) {
+        const uint32_t r = 32u * c + lane;
+        uint32_t cnt = 0;
+        if (r < n) {
+            const uint64_t k = keys[r];
+            const uint64_t last = global ? ~0ull : (k | ((1ull << 40) - 1));
+            uint64_t lim = k + (D - 1);
+            if (lim < k) lim = ~0ull;  // saturate
+            if (lim > last) lim = last;
+            const uint64_t k1 = keys[r + 1], k2 = keys[r + 2], k3 = keys[r + 3], k4 = keys[r + 4];
+            const bool m1 = r + 1 < nt && k1 <= lim;
+            const bool m2 = m1 && r + 2 < nt && k2 <= lim;
+            const bool m3 = m2 && r + 3 < nt && k3 <= lim;
+            const bool m4 = m3 && r + 4 < nt && k4 <= lim;
+            cnt = (uint32_t)m1 + (uint32_t)m2 + (uint32_t)m3 + (uint32_t)m4;
+            if (m4)
+                for (uint32_t q = r + 5; q < nt && keys[q] <= lim; ++q) ++cnt;
         }
-        start[r] = c;
-        mine += c;
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        if (r < n) start[r] = carry + incl - cnt;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
-    uint32_t total;
-    uint32_t run = block_exclusive_scan_u32<NT>(mine, ws, &total);
-    for (uint32_t r = r0; r < r1; ++r) {
-        const uint32_t c = start[r];
-        start[r] = run;
-        run += c;
+    if (lane == 0) ws[warp] = carry;
+    __syncthreads();
+    uint32_t wbase = 0, total = 0;
+#pragma unroll
+    for (uint32_t w = 0; w < NW; ++w) {
+        const uint32_t t = ws[w];
+        wbase += w < warp ? t : 0u;
+        total += t;
     }
     if (total != P && threadIdx.x == 0) atomicOr(d.status, kStCountMismatch);
-    __syncthreads();
-
+    // the warp's pairs end here (a record's count is the gap to the next
+    // record's offset; the warp's total after its last record)
+    const uint32_t rend = min(32u * c1, n);
     uint32_t g[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) g[i] = d.pre2[i];
@@ -122,12 +147,17 @@ __global__ void __launch_bounds__(kMatchThreads) k_match(const Desc *__restrict_
     const uint32_t limit = min(total, P);
     for (uint32_t w0 = 0; w0 < limit; w0 += kPairList) {
         const uint32_t w1 = min(limit, w0 + kPairList);
-        // List the pairs whose Table-2 position falls in [w0, w1).
-        for (uint32_t r = r0; r < r1; ++r) {
-            const uint32_t s = start[r];
-            const uint32_t e = r + 1 < n ? start[r + 1] : total;
-            const uint32_t lo = max(s, w0), hi = min(e, w1);
-            for (uint32_t k = lo; k < hi; ++k) list[k - w0] = r | ((r + 1 + (k - s)) << 16);
+        // List the pairs whose Table-2 position falls in [w0, w1): each lane
+        // its records' pairs (r, r + 1 + j) at the warp base plus the
+        // record's offset.
+        for (uint32_t c = c0; c < c1; ++c) {
+            const uint32_t r = 32u * c + lane;
+            if (r < n) {
+                const uint32_t s = wbase + start[r];
+                const uint32_t e = wbase + (r + 1 < rend ? start[r + 1] : carry);
+                const uint32_t lo = max(s, w0), hi = min(e, w1);
+                for (uint32_t k = lo; k < hi; ++k) list[k - w0] = r | ((r + 1 + (k - s)) << 16);
+            }
         }
         __syncthreads();
         for (uint32_t q = threadIdx.x; q < w1 - w0; q += NT) {
