@@ -15,16 +15,17 @@
 
 namespace vx {
 
-constexpr uint32_t kPairList = 4096;  // pair-list window (entries of 2 x u16)
-
+// Shared layout for slots of at most `cap` records (with the halo): key64
+// [cap] | nonce [cap] | pair offset [cap] | scan workspace.  Once the pairs
+// are counted the keys are dead and their space holds the pair list, in
+// windows of 2 * cap entries (2 x u16 each).
 struct MatchLayout {
-    size_t nonces, start, list, ws, bytes;
+    size_t nonces, start, ws, bytes;
     __host__ __device__ MatchLayout(uint32_t cap)
     {
         nonces = (size_t)cap * 8;
         start = nonces + (size_t)cap * 4;
-        list = start + (size_t)cap * 4;
-        ws = list + (size_t)kPairList * 4;
+        ws = start + (size_t)cap * 4;
         bytes = ws + (kMatchThreads / 32 + 1) * 4;
     }
 };
@@ -48,7 +49,8 @@ __global__ void __launch_bounds__(kMatchThreads) k_match(const Desc *__restrict_
     uint64_t *keys = reinterpret_cast<uint64_t *>(smem_raw);
     uint32_t *nonces = reinterpret_cast<uint32_t *>(smem_raw + L.nonces);
     uint32_t *start = reinterpret_cast<uint32_t *>(smem_raw + L.start);
-    uint32_t *list = reinterpret_cast<uint32_t *>(smem_raw + L.list);
+    uint32_t *list = reinterpret_cast<uint32_t *>(smem_raw);  // over the keys, after the counts
+    const uint32_t kPairList = 2u * (d.cap2 + d.hcap);
     uint32_t *ws = reinterpret_cast<uint32_t *>(smem_raw + L.ws);
 
     // Table-1 words {nonce, h0, h1} -> nonce[], key64[] (key64 = BE of h).
