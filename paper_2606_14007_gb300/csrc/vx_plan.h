@@ -18,6 +18,7 @@
 namespace vx {
 
 constexpr int kDefaultPartLog2 = 11;       // mean records per physical partition: 2048
+constexpr int kSort2PartLog2 = 10;         // the same for the sort of Table 2 by hash2
 constexpr uint32_t kDefaultSlackSigma = 12;
 constexpr int kMaxPartBits = 21;           // scatter levels of <= 10 and <= 11 bits
 constexpr int kAggMaxBits = 6;             // warp-aggregate ranks up to 64 bins
@@ -378,7 +379,7 @@ inline int make_sort2_plan(uint64_t n, Sort2Plan *out, size_t desc_bytes)
     memset(&S, 0, sizeof(S));
     int lg = 0;
     while (lg < 63 && (2ull << lg) <= n) ++lg;  // floor(log2(n)), 0 for n <= 1
-    S.p = lg - kDefaultPartLog2;
+    S.p = lg - kSort2PartLog2;
     if (S.p < 0) S.p = 0;
     if (S.p > 20) S.p = 20;  // its second level keeps to <= 10 bits
     S.p1 = S.p <= 10 ? S.p : S.p / 2;
