@@ -274,51 +274,61 @@ constexpr int kScanThreads = 1024;
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_pairs(const Desc *__restrict__ descs)
 {
-    __shared__ uint64_t ws[kScanThreads / 32 + 1];
-    __shared__ uint64_t carry_s;
+    constexpr int NT = kScanThreads, NW = NT / 32, PER = 4;
+    __shared__ uint64_t ws[NW];
+    __shared__ uint64_t s_tile;
     const Desc &d = descs[blockIdx.x];
     const uint64_t n = 1ull << d.p;
     uint64_t *out = d.t2off;
-    const uint64_t per = (n + kScanThreads - 1) / kScanThreads;
-    const uint64_t b0 = (uint64_t)threadIdx.x * per;
-    const uint64_t b1 = min(n, b0 + per);
-    auto val = [&](uint64_t i) -> uint64_t { return d.pairs[i]; };
-    uint64_t local = 0;
-    for (uint64_t i = b0; i < b1; ++i) local += val(i);
-    // block exclusive scan of `local` (u64)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint64_t incl = local;
+    // tiles of NT * PER consecutive counts, PER per thread (coalesced),
+    // block-scanned one after the other with the running total carried
+    uint64_t carry = 0;
+    for (uint64_t t0 = 0; t0 < n; t0 += (uint64_t)NT * PER) {
+        const uint64_t b0 = t0 + (uint64_t)threadIdx.x * PER;
+        uint64_t v[PER], local = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) ws[warp] = incl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint64_t run = 0;
-        for (int w = 0; w < kScanThreads / 32; ++w) {
-            uint64_t t = ws[w];
-            ws[w] = run;
-            run += t;
+        for (int k = 0; k < PER; ++k) {
+            v[k] = b0 + k < n ? d.pairs[b0 + k] : 0ull;
+            local += v[k];
         }
-        carry_s = run;
-    }
-    __syncthreads();
-    uint64_t run = ws[warp] + incl - local;
-    for (uint64_t i = b0; i < b1; ++i) {
-        out[i] = run;
-        run += val(i);
+        uint64_t incl = local;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) ws[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint64_t x = lane < NW ? ws[lane] : 0ull;
+            uint64_t wi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            if (lane < NW) ws[lane] = wi - x;  // exclusive warp prefixes
+            if (lane == NW - 1) s_tile = wi;
+        }
+        __syncthreads();
+        uint64_t at = carry + ws[warp] + incl - local;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            if (b0 + k < n) out[b0 + k] = at;
+            at += v[k];
+        }
+        carry += s_tile;
+        __syncthreads();  // ws and s_tile are reused by the next tile
     }
     if (threadIdx.x == 0) {
-        out[n] = carry_s;
+        out[n] = carry;
         // A re-run of the match (e.g. after a larger Table-2 buffer was
         // bound) re-decides the capacity bit.
-        if (carry_s > d.t2cap) atomicOr(d.status, kStT2Capacity);
+        if (carry > d.t2cap) atomicOr(d.status, kStT2Capacity);
         else atomicAnd(d.status, ~kStT2Capacity);
     }
 }
-
 
 cudaError_t launch_scan_pairs(const Desc *descs, int nplots, cudaStream_t s)
 {
