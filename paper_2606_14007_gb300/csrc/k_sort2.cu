@@ -11,12 +11,14 @@
 // back into the Table-2 buffer at its offset.  Table 2 is read completely by
 // the first level before anything writes it.
 #include "vx_internal.cuh"
+#include "vx_plan.h"
 
 namespace vx {
 
-constexpr int kS2Threads = 256;              // first level: 256 threads x 8 records
+constexpr int kS2Threads = 512;              // first level: 512 threads x 8 records
 constexpr int kS2PerThread = 8;
 constexpr uint32_t kS2Tile1 = kS2Threads * kS2PerThread;
+static_assert(kS2Tile1 == kPlanS2Tile1, "planner and first-level sort tiles differ");
 constexpr int kS2BThreads = 512;             // second level: 512 threads x 8 records
 constexpr uint32_t kS2Tile2 = 4096;
 constexpr int kS2SortThreads = 256;
@@ -43,7 +45,7 @@ __global__ void k_s2_setup(Sort2Desc *dp)
 }
 
 // ---------------------------------------------------- first scatter level
-// A CTA takes 2048 consecutive Table-2 records, ranks them in shared memory
+// A CTA takes kS2Tile1 consecutive Table-2 records, ranks them in shared memory
 // by their level bin, claims one run per (CTA, bin) with a global atomic,
 // and writes them bin by bin (key2 and the packed pair (a << 32 | b)).
 struct S2Smem1 {

@@ -40,6 +40,7 @@ inline uint32_t hash_tiles(uint64_t n, int npt)
 constexpr uint64_t kPlanScanChunk = 4096;  // counters per Table-1 offset-scan CTA
 constexpr uint64_t kPlanScatterTile = 4096; // records per second-level scatter CTA
 constexpr uint64_t kPlanT2HashTile = 2048; // Table-2 records per pair-hash CTA
+constexpr uint64_t kPlanS2Tile1 = 4096;    // Table-2 records per first-level CTA of the sort by hash2
 constexpr uint64_t kPlanT2SlotGroup = 8;   // partitions per pair-hash CTA reading pair slots
 
 enum { kScatterAuto = 0, kScatterStaged = 1, kScatterDirect = 2 };
@@ -400,7 +401,7 @@ inline int make_sort2_plan(uint64_t n, Sort2Plan *out, size_t desc_bytes)
         S.chunks1 = (uint32_t)((cap1 + 4095) / 4096);
         S.tiles2 = (uint32_t)((1u << S.p1) * S.chunks1);
     }
-    S.tiles1 = (uint32_t)((n + 2047) / 2048);
+    S.tiles1 = (uint32_t)((n + kPlanS2Tile1 - 1) / kPlanS2Tile1);
     S.parts = 1u << S.p;
     S.tiles_scan = (uint32_t)((S.parts + kPlanScanChunk - 1) / kPlanScanChunk);
     const uint64_t np = S.parts, n1 = S.p2 > 0 ? (1ull << S.p1) : 0ull;
