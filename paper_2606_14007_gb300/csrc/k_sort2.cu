@@ -6,9 +6,10 @@
 // with the Table-1 machinery applied to 16-byte records: a first scatter
 // level by the top p1 bits of key2, a second level by the next p2 bits into
 // 2^p Poisson-sized partitions, a scan of the partition counts, and a
-// shared-memory sort of every partition (counting sort on the next dbits
-// key bits, insertion sort inside a digit) that writes its records straight
-// back into the Table-2 buffer at its offset.  Table 2 is read completely by
+// shared-memory sort of every partition (counting sort on the next
+// dbits + 1 key bits, each record ranked inside its digit run by warp
+// shuffles) that writes its records straight back into the Table-2 buffer
+// at their places.  Table 2 is read completely by
 // the first level before anything writes it.
 #include "vx_internal.cuh"
 #include "vx_plan.h"
