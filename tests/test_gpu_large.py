@@ -204,6 +204,49 @@ def test_plot_equals_oracle_elementwise(vx, K):
     assert np.array_equal(off.astype(np.uint64), orc.bucket_offsets(r1))
 
 
+@pytest.mark.parametrize("K", [24, 25])
+def test_split_path_equals_oracle_elementwise(vx, K):
+    # vx_table1 then vx_match (the sort's count mode, the pair-offset scan
+    # and the match kernel) at sizes past the small-K parity test.
+    key = plot_key(K + 300)
+    p = vx.Plot(K, key)
+    p.run_split()
+    n2 = p.sync()
+    g1 = p.t1.cpu().numpy()
+    g2 = p.t2.cpu().numpy()
+    p.close()
+    torch.cuda.empty_cache()
+    r1, r2 = orc.plot_allcores(K, key, THREADS)
+    d = first_diff(g1, r1)
+    assert d < 0, "Table 1 differs from the oracle at record %d" % d
+    assert n2 == r2.shape[0], (n2, r2.shape[0])
+    d = first_diff(g2, r2)
+    assert d < 0, "Table 2 differs from the oracle at record %d" % d
+
+
+@pytest.mark.parametrize("K", [24, 25])
+def test_sorted_table2_equals_oracle_elementwise(vx, K):
+    # vx_sort_table2 at sizes past its small-K test: the oracle's Table 2
+    # in (key2, a, b) order, byte for byte.
+    key = plot_key(K + 400)
+    p = vx.Plot(K, key)
+    p.run()
+    n2 = p.sync()
+    wb = vx.vx_sort_table2_work_bytes(p.handle)
+    work = torch.empty(max(wb, 256), dtype=torch.uint8, device="cuda")
+    vx.vx_sort_table2(p.handle, work.data_ptr(), wb)
+    assert vx.vx_sync(p.handle) == vx.VX_OK
+    got = p.t2.cpu().numpy()
+    p.close()
+    del work
+    torch.cuda.empty_cache()
+    _, r2 = orc.plot_allcores(K, key, THREADS)
+    assert n2 == r2.shape[0], (n2, r2.shape[0])
+    ref = orc.sort_table2(r2)
+    d = first_diff(got, ref)
+    assert d < 0, "sorted Table 2 differs from the oracle at record %d" % d
+
+
 @pytest.mark.parametrize("K", [27, 28, 29, 30, 31])
 def test_plot_bit_exact_by_properties(vx, K):
     check_plot(vx, K, K)
